@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""D2Q9 + NSBC throughput on one GB300: MLUPS and the HBM roofline.
+
+One "step" is one lattice-Boltzmann time step of the whole domain: the fused
+pull-stream + BGK collide kernel over the interior and the NSBC kernel over
+the perimeter.  Default workload: 8192 x 8192 nodes, tau 0.55, four Gaussian
+acoustic pulses (amplitude 1e-3, half-width 64) at seeded centres, NSBC on
+all four edges, FP32 shifted storage.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(the reference for this method) on the host cores instead.
+Under torchrun with N > 1 every rank runs an independent replica (a single
+domain does not shard without a halo exchange); value = sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D2Q9+NSBC MLUPS"
+UNIT = "MLUPS"
+BYTES_PER_CELL = {"f64": 144, "f32": 72, "f16": 36, "bf16": 36}
+CPU_SAMPLE_N = 2048
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="pulse-8192")
+    p.add_argument("--storage", default="f32", choices=list(BYTES_PER_CELL))
+    p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--launch", default="", help="bulk launch shape 'threads_x,rows' instead of autotuning")
+    return p.parse_args()
+
+
+def workload(name: str):
+    from paper_2005_08674_gb300 import inputs
+    m = re.fullmatch(r"pulse-(\d+)", name)
+    if not m:
+        raise SystemExit(f"unknown workload {name}")
+    n = int(m.group(1))
+    if n == 8192:
+        return inputs.pulse_8192()
+    return inputs.pulse_square(n, margin=max(8, min(256, n // 4)), half_width=min(64.0, n / 16))
+
+
+def describe(w, storage):
+    p = w.params
+    return (f"{w.name}: {w.nx}x{w.ny} D2Q9 BGK tau={w.tau}, {len(p['centres'])} Gaussian pulses "
+            f"A={p['amplitude']} HWHM={p['half_width']} at seeded centres, NSBC (gamma 0.6, beta 0) "
+            f"on all edges, {storage} shifted storage")
+
+
+# --- clocks -------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.sel = []
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(device_index).uuid)
+            if u:
+                self.sel = ["-i", u if u.startswith("GPU-") else "GPU-" + u]
+        except Exception:
+            self.sel = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", *self.sel,
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+                power.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        srt = sorted(sm)
+        busy = [s for s in srt if s > 0.5 * max(srt)] or srt
+        return {"sm_mhz": busy[len(busy) // 2], "sm_max_mhz": max(smax), "power_w_max": max(power),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --- roofline inputs ------------------------------------------------------------
+
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for name in ("lbm_kernels.cuh", "lbm_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2005_08674_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(storage: str, interior_cells: int):
+    """DRAM bytes per bulk launch from the committed ncu summary, scaled by the
+    cells one launch processes, if the kernel source is unchanged since then."""
+    path = os.path.join(ROOT, "profiles", f"bulk_kernel_traffic_{storage}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"dram_bytes_per_interior_cell:\s*([0-9.]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != kernel_source_sha():
+        return None
+    return float(m_b.group(1)) * interior_cells
+
+
+# --- CPU oracle (baseline / reference arm) --------------------------------------
+
+def oracle_sample_workload():
+    from paper_2005_08674_gb300 import inputs
+    return inputs.pulse_square(CPU_SAMPLE_N, steps=0)
+
+
+def cpu_threads() -> int:
+    v = os.environ.get("OMP_NUM_THREADS")
+    return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
+
+
+def time_oracle(seconds: float, warmup: int = 1, fixed_steps: int | None = None):
+    import oracle
+    w = oracle_sample_workload()
+    o = oracle.Oracle(w.nx, w.ny, w.tau, openmp=True).init(*w.fields())
+    o.step(warmup)
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        o.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if (fixed_steps is not None and steps >= fixed_steps) or (fixed_steps is None and el >= seconds):
+            break
+    mlups = w.cells * steps / el / 1e6
+    sample = (f"FP64 C oracle (OpenMP over rows) on the same pulse recipe at {w.nx}x{w.ny} "
+              f"(4 pulses, tau 0.55), {steps} steps after {warmup} warm-up, host cores")
+    return mlups, steps, el, sample
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    mlups, steps, el, sample = time_oracle(0.0, warmup=args.warmup, fixed_steps=args.steps)
+    cores = cpu_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": describe(w, args.storage), "sample": f"{CPU_SAMPLE_N}x{CPU_SAMPLE_N}"},
+        "cpu_baseline": {"value": mlups, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": mlups, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --- GPU arm ------------------------------------------------------------------
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2005_08674_gb300 import build
+    build.build()
+    from paper_2005_08674_gb300 import lbm
+
+    torch.cuda.set_device(local_rank)
+    dist = world > 1
+    if dist:
+        import torch.distributed as td
+
+    w = workload(args.workload)
+    cells = w.cells
+    interior = (w.nx - 2) * (w.ny - 2)
+    fields = w.fields()
+
+    sim = lbm.Simulation(w.nx, w.ny, w.tau, w.farfield_rho, w.farfield_u, storage=args.storage)
+    sim.init(*fields)
+    if args.launch:
+        bx, rows = (int(v) for v in args.launch.split(","))
+        sim.set_launch(bx, rows)
+    else:
+        bx, rows, _ = sim.autotune()
+    stream = sim.stream
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            td.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (also captures the step graphs)
+    sim.step(args.warmup)
+    barrier()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        td.all_reduce(t, op=td.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = world * cells * args.steps / (ms_max * 1e-3) / 1e6
+    out = sim.reduce(allow_unstable=True)
+    stable = out[3] == 0
+
+    # kernel-timing region: same step, per-launch CUDA events on the launching stream
+    kprof = min(args.steps, 400)
+    lbm.lbm_profile(sim.h, True)
+    sim.step(kprof)
+    bulk_ms, nb, nsbc_ms, nn = lbm.lbm_profile_read(sim.h)
+    lbm.lbm_profile(sim.h, False)
+    bulk_avg = bulk_ms / max(nb, 1)
+    nsbc_avg = nsbc_ms / max(nn, 1)
+    peak, peak_kind = measured_peak_gbs()
+    alg_bytes = BYTES_PER_CELL[args.storage] * interior
+    achieved = alg_bytes / (bulk_avg * 1e-3) / 1e9
+    traffic = profiled_traffic(args.storage, interior)
+
+    line = None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": describe(w, args.storage), "nx": w.nx, "ny": w.ny,
+                       "bulk_launch": {"threads_x": bx, "rows": rows},
+                       "l2": f"inputs larger than L2: {lbm.lbm_buffer_bytes(sim.h) / 1e9:.2f} GB per population buffer",
+                       "parallelism": "replicas" if world > 1 else "single-gpu",
+                       "stable": bool(stable)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "bulk_kernel (fused pull-stream + BGK collide)",
+                         "bytes_per_cell": BYTES_PER_CELL[args.storage], "cells_per_launch": interior,
+                         "avg_launch_ms": bulk_avg, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "nsbc_avg_launch_ms": nsbc_avg,
+                         "timing": f"per-launch CUDA events over {kprof} steps after the timed region"},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clk,
+        }
+
+    # end to end through the C ABI with host buffers (pinned)
+    if not args.no_e2e:
+        pinned = [torch.empty((w.ny, w.nx), dtype=torch.float64, pin_memory=True) for _ in range(6)]
+        for t, a in zip(pinned[:3], fields):
+            t.numpy()[...] = a
+        host_in = [t.numpy() for t in pinned[:3]]
+        host_out = [t.numpy() for t in pinned[3:]]
+        barrier()
+        t0 = time.perf_counter()
+        lbm.lbm_init(sim.h, *host_in)
+        lbm.lbm_step(sim.h, args.steps)
+        lbm.lbm_get_macros(sim.h, *host_out)
+        t1 = time.perf_counter()
+        barrier()
+        e2e_s = t1 - t0
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            td.all_reduce(t, op=td.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        if line is not None:
+            nbytes = 3 * cells * 8
+            line["e2e"] = {"value": world * cells * args.steps / e2e_s / 1e6, "unit": UNIT,
+                           "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
+                           "what": "lbm_init (host fields) + lbm_step(steps) + lbm_get_macros (host), wall clock",
+                           "seconds": e2e_s}
+        del pinned, host_in, host_out
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    # other storage types on the same workload
+    if not args.no_variants:
+        variants = {}
+        vsteps = min(args.steps, 1000)
+        for st in ("f32", "f16", "bf16", "f64"):
+            if st == args.storage:
+                continue
+            s2 = lbm.Simulation(w.nx, w.ny, w.tau, w.farfield_rho, w.farfield_u, storage=st)
+            s2.init(*fields)
+            vb, vr, _ = s2.autotune()
+            s2.step(args.warmup)
+            torch.cuda.synchronize()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(s2.stream)
+            s2.step(vsteps)
+            a1.record(s2.stream)
+            torch.cuda.synchronize()
+            vms = a0.elapsed_time(a1)
+            lbm.lbm_profile(s2.h, True)
+            s2.step(min(vsteps, 200))
+            bms, bn, _, _ = lbm.lbm_profile_read(s2.h)
+            bavg = bms / max(bn, 1)
+            gbs = BYTES_PER_CELL[st] * interior / (bavg * 1e-3) / 1e9
+            variants[st] = {"mlups": world * cells * vsteps / (vms * 1e-3) / 1e6, "steps": vsteps,
+                            "bulk_gbs": gbs, "bulk_frac": gbs / peak, "bulk_launch": [vb, vr]}
+            s2.close()
+            del s2
+            torch.cuda.empty_cache()
+        if line is not None:
+            line["variants"] = variants
+
+    if line is not None and not args.no_cpu:
+        mlups, steps, el, sample = time_oracle(args.cpu_seconds)
+        line["cpu_baseline"] = {"value": mlups, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+                                "sample": sample, "seconds": el}
+    return line
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as td
+        torch.cuda.set_device(local_rank)
+        td.init_process_group("nccl")
+    line = run_ours(args, rank, world, local_rank)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as td
+        td.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) D2Q9 lattice-Boltzmann library with
+ * the Non-equilibrium Symmetry Boundary Condition (NSBC) of Euser & Vuik,
+ * "A non-reflective boundary condition for LBM based on the assumption of
+ * non-equilibrium symmetry" (arXiv 2005.08674).
+ *
+ * Conventions shared by every entry point:
+ *   - Lattice: D2Q9 numbered as in the paper's Fig. 1 (Sec. 3):
+ *     c_0=(0,0), c_1=(1,0), c_2=(-1,0), c_3=(0,1), c_4=(0,-1), c_5=(1,1),
+ *     c_6=(-1,-1), c_7=(-1,1), c_8=(1,-1); weights 4/9, 1/9, 1/36.
+ *   - Node (i, j) sits at x = i, y = j.  Host and device macroscopic fields
+ *     are row-major [ny][nx] arrays of double, x fastest.
+ *   - The stored state is the post-collision population set of step n.  Its
+ *     moments equal the fluid state at step n (collision conserves rho and
+ *     rho u), and that is what the macro getters return.
+ *   - A step is: pull streaming (Eq. lbe_0), NSBC on every edge node
+ *     (Sec. 5: Eqs. nes_0..nes_4), then BGK collision at every node
+ *     (Eqs. lbe_1, feq_1), boundary nodes included.
+ *   - Status codes: LBM_OK (0) or a negative LBM_E* value; lbm_last_error()
+ *     returns a message for the calling thread's last failure.
+ *   - Device work is asynchronous on the handle's stream unless an entry
+ *     point says it synchronises.  Entry points are not thread-safe on one
+ *     handle; distinct handles are independent.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBM_OK 0
+#define LBM_EINVAL (-1)    /* bad argument: NULL, nx or ny < 3, tau <= 0.5, unknown mode */
+#define LBM_ENOMEM (-2)    /* device allocation failed */
+#define LBM_ECUDA (-3)     /* a CUDA runtime call failed (message has the CUDA error) */
+#define LBM_EUNSTABLE (-4) /* non-finite or non-positive density found by lbm_reduce */
+#define LBM_ESTATE (-5)    /* call out of order (e.g. step before init) */
+
+/* Storage of the populations in device memory.  Every type stores the
+ * deviation f_i - w_i from the rest-state weights (a shift that keeps the
+ * stored magnitudes small, so rounding is relative to the perturbation).
+ * Arithmetic: LBM_F64 computes in double everywhere; the other three
+ * collide and apply the NSBC in float, with the NSBC gradient extrapolation
+ * and far-field blend (Eqs. nes_2, nes_3) in double. */
+#define LBM_F64 0
+#define LBM_F32 1
+#define LBM_F16 2  /* IEEE binary16, round-to-nearest-even */
+#define LBM_BF16 3 /* bfloat16, round-to-nearest-even */
+
+typedef struct lbm lbm_t;
+
+/* Create a simulation of nx x ny nodes with BGK relaxation time tau
+ * (Eq. lbe_1, dt = 1) and far-field reference vector
+ * m_0 = (farfield_rho, farfield_u[0], farfield_u[1]) (Eq. nes_3).
+ * NSBC defaults: gamma = 0.6 (the paper's best value for D2Q9, Sec. 5),
+ * beta = 0 (the paper's experiments), kappa = 3, first-order gradient.
+ * Storage defaults to LBM_F32.  Host-only: no device memory is touched
+ * until lbm_bind or the first lbm_init*.  Returns NULL on bad arguments
+ * (nx, ny < 3 or > 65536, tau <= 0.5 or not finite, farfield_rho <= 0,
+ * farfield_u NULL) with the reason in lbm_last_error(). */
+lbm_t* lbm_create(int32_t nx, int32_t ny, double tau, double farfield_rho,
+                  const double farfield_u[2]);
+
+/* Free the handle and any device memory the library allocated for it
+ * (never memory passed to lbm_bind).  Synchronises the stream.  NULL-safe. */
+void lbm_destroy(lbm_t* h);
+
+/* NSBC parameters (Sec. 5).  gamma: relaxation of the gradient prediction
+ * m_p = m - gamma d_n m (Eq. nes_2), d_n a one-sided difference along the
+ * outward unit normal with grad_order 1 or 2 points into the domain
+ * (corner normals are diagonal).  beta: far-field factor of Eq. nes_3.
+ * kappa: momentum factor of the correction of Eq. nes_4,
+ * f_i -= w_i (d_rho + kappa c_i . d(rho u)); kappa = 3 makes the corrected
+ * node carry exactly rho_c and rho_c u_c, kappa = 1 is the printed formula.
+ * Returns LBM_EINVAL for grad_order not in {1, 2} or non-finite values. */
+int lbm_set_nsbc(lbm_t* h, double gamma, double beta, double kappa, int32_t grad_order);
+
+/* Choose the storage type (LBM_F64 / LBM_F32 / LBM_F16 / LBM_BF16).
+ * Only allowed before the first lbm_bind / lbm_init* (LBM_ESTATE after). */
+int lbm_set_precision(lbm_t* h, int32_t storage);
+
+/* Use this CUDA stream (a cudaStream_t passed as void*; NULL = the legacy
+ * default stream) for all later device work of this handle. */
+int lbm_set_stream(lbm_t* h, void* cuda_stream);
+
+/* Bytes of ONE population buffer: 9 planes of ny rows of `pitch` elements
+ * of the storage type, pitch = nx rounded up to 64, each plane starting
+ * 256-byte aligned. */
+size_t lbm_buffer_bytes(const lbm_t* h);
+
+/* Bytes of the scratch area: three [ny][nx] double fields (macros) plus
+ * reduction partials, rounded to 256 bytes. */
+size_t lbm_scratch_bytes(const lbm_t* h);
+
+/* Hand the library caller-owned device memory (e.g. from PyTorch): two
+ * population buffers of lbm_buffer_bytes() each and one scratch area of
+ * lbm_scratch_bytes(), all 256-byte aligned and on the current device.
+ * The caller keeps ownership and must keep them alive until lbm_destroy.
+ * Must precede the first lbm_init*; otherwise the library allocates its own
+ * on first use. */
+int lbm_bind(lbm_t* h, void* dev_a, void* dev_b, void* dev_scratch);
+
+/* Initialise every node at equilibrium f_i = f_i^eq(rho, u) (Eq. feq_1) from
+ * HOST fields rho, ux, uy ([ny][nx] double).  Copies host->device through
+ * the scratch area on the stream and synchronises.  Resets the step count. */
+int lbm_init(lbm_t* h, const double* rho, const double* ux, const double* uy);
+
+/* As lbm_init, from DEVICE fields [ny][nx] double; asynchronous. */
+int lbm_init_device(lbm_t* h, const double* d_rho, const double* d_ux, const double* d_uy);
+
+/* Advance n >= 0 steps, asynchronously on the stream.  Steps are replayed
+ * from a CUDA graph of a fixed number of steps captured on first use (and
+ * recaptured after lbm_set_nsbc / lbm_set_stream); the remainder is
+ * launched directly. */
+int lbm_step(lbm_t* h, int32_t n);
+
+/* Number of steps taken since the last lbm_init* / lbm_set_populations. */
+int64_t lbm_steps_done(const lbm_t* h);
+
+/* Macroscopic fields rho, ux, uy (Eqs. cf_0, cf_1 as discrete sums) of the
+ * current state into HOST arrays [ny][nx] double; synchronises. */
+int lbm_get_macros(lbm_t* h, double* rho, double* ux, double* uy);
+
+/* As lbm_get_macros into DEVICE arrays [ny][nx] double; asynchronous. */
+int lbm_get_macros_device(lbm_t* h, double* d_rho, double* d_ux, double* d_uy);
+
+/* Absolute populations f_i (not shifted) as HOST [9][ny][nx] double, rounded
+ * to the storage type on the way in.  For checkpoints and tests.  Both
+ * synchronise.  set resets the step count. */
+int lbm_get_populations(lbm_t* h, double* f);
+int lbm_set_populations(lbm_t* h, const double* f);
+
+/* FP64 reductions over all nodes, used for the reflection measure and as an
+ * instability check.  If ref_rho is non-NULL, ref_* are DEVICE [.][ref_pitch]
+ * double fields whose element [0] is aligned with node (0, 0) of this
+ * handle (pass a pointer into a larger, padded reference domain).  Writes
+ * HOST out[4]:
+ *   out[0] = sum rho                               (mass)
+ *   out[1] = sum (cs^2 (rho - rho_r)^2 / rho_ff + rho_ff |u - u_r|^2) / 2
+ *            with (rho_r, u_r) the reference field, or the far field m_0
+ *   out[2] = sum rho |u|^2 / 2                     (kinetic energy)
+ *   out[3] = number of nodes with non-finite or non-positive rho
+ * Synchronises.  Returns LBM_EUNSTABLE when out[3] > 0 (out still filled). */
+int lbm_reduce(lbm_t* h, const double* ref_rho, const double* ref_ux, const double* ref_uy,
+               int32_t ref_pitch, double out[4]);
+
+/* Launch shape of the bulk stream-collide kernel: threads per block along x
+ * and rows per block.  0, 0 restores the built-in choice.  Returns
+ * LBM_EINVAL for shapes the kernel was not compiled for. */
+int lbm_set_launch(lbm_t* h, int32_t threads_x, int32_t rows);
+
+/* Time every compiled bulk launch shape on this handle's own buffers (a few
+ * steps each, CUDA events on the stream) and keep the fastest; the state is
+ * restored afterwards.  Writes the chosen shape and its time per step in
+ * milliseconds to the optional outputs. */
+int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, double* ms_per_step);
+
+/* Per-launch timing.  While enabled, lbm_step launches every step directly
+ * (no graph) on the handle's stream with CUDA events around the bulk
+ * stream-collide kernel and around the NSBC kernel, which then run one after
+ * the other.  lbm_profile resets the record. */
+int lbm_profile(lbm_t* h, int32_t enable);
+
+/* Read and reset the record (synchronises): out[0] = total bulk-kernel
+ * milliseconds, out[1] = bulk launches, out[2] = total NSBC-kernel
+ * milliseconds, out[3] = NSBC launches, since the last reset. */
+int lbm_profile_read(lbm_t* h, double out[4]);
+
+/* Message describing the calling thread's last failure ("" if none). */
+const char* lbm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -21,29 +21,32 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.c")
 _LIB = os.path.join(_HERE, "liblbm_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "liblbm_oracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/liblbm_oracle.so`` (gcc, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".tmp{os.getpid()}"
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle into ``oracle/liblbm_oracle.so`` (gcc, no FMA
+    contraction).  ``openmp=True`` builds ``liblbm_oracle_omp.so`` from the same
+    source with the row loop split over threads (bit-identical results)."""
+    out = _LIB_OMP if openmp else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".tmp{os.getpid()}"
         subprocess.check_call(
-            ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c99", "-fPIC",
-             "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+            ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=gnu99", "-fPIC",
+             *(["-fopenmp"] if openmp else []), "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
-def lib():
-    global _lib
+def lib(openmp: bool = False):
     with _lock:
-        if _lib is None:
-            L = ctypes.CDLL(build())
+        if openmp not in _libs:
+            L = ctypes.CDLL(build(openmp=openmp))
             L.or_create.restype = ctypes.c_void_p
             L.or_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_double]
@@ -62,8 +65,8 @@ def lib():
             L.or_steps.argtypes = [ctypes.c_void_p]
             L.or_equilibrium.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp]
             L.or_lattice.argtypes = [_ip, _ip, _dp, _ip]
-            _lib = L
-    return _lib
+            _libs[openmp] = L
+    return _libs[openmp]
 
 
 def _p(a: np.ndarray):
@@ -94,8 +97,8 @@ class Oracle:
     def __init__(self, nx: int, ny: int, tau: float, farfield_rho: float = 1.0,
                  farfield_u=(0.0, 0.0), gamma: float = 0.6, beta: float = 0.0,
                  kappa: float = 3.0, grad_order: int = 1, periodic=(False, False),
-                 collision: str = "bgk", mrt_rates=None):
-        self._L = lib()
+                 collision: str = "bgk", mrt_rates=None, openmp: bool = False):
+        self._L = lib(openmp)
         h = self._L.or_create(nx, ny, tau, farfield_rho, farfield_u[0], farfield_u[1])
         if not h:
             raise ValueError(f"oracle rejected nx={nx} ny={ny} tau={tau}")

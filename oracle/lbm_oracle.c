@@ -333,6 +333,9 @@ void or_macros(const or_sim* s, double* rho, double* ux, double* uy) {
 /* Eq. (lbe_0) streaming, Sec. 5 boundary, Eq. (lbe_1)/(mrt_lbe) collision */
 void or_step(or_sim* s, int n) {
   for (int k = 0; k < n; ++k) {
+    /* rows are independent within a step; the OpenMP build splits them over
+     * threads without changing any result bit */
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < s->ny; ++y)
       for (int x = 0; x < s->nx; ++x) {
         double g[9];

@@ -1,0 +1,247 @@
+// lbm_device.cuh -- device-side building blocks of the D2Q9 + NSBC update
+// for sm_103a: storage traits (shifted populations in f64/f32/f16/bf16 with
+// 16-byte vector access), the BGK cell update, and the NSBC node update.
+//
+// Populations are stored as h_i = f_i - w_i (deviation from the rest state),
+// so rho = 1 + sum h_i and rho u = sum c_i h_i (sum c_i w_i = 0).  The
+// equilibrium in the same shift is
+//   h_i^eq = f_i^eq - w_i = w_i (d_rho + rho (3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u))
+// which is Eq. (feq_1) with cs^2 = 1/3 minus w_i.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace lbmk {
+
+// ---------------------------------------------------------------------------
+// Lattice (Fig. 1): c_0=(0,0) c_1=(1,0) c_2=(-1,0) c_3=(0,1) c_4=(0,-1)
+// c_5=(1,1) c_6=(-1,-1) c_7=(-1,1) c_8=(1,-1); w = 4/9, 1/9, 1/36.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int cx(int i) {
+  return i == 1 || i == 5 || i == 8 ? 1 : (i == 2 || i == 6 || i == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int cy(int i) {
+  return i == 3 || i == 5 || i == 7 ? 1 : (i == 4 || i == 6 || i == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr int opp(int i) { return i == 0 ? 0 : (i % 2 == 1 ? i + 1 : i - 1); }
+template <typename C>
+__host__ __device__ constexpr C wt(int i) {
+  return i == 0 ? C(4) / C(9) : (i <= 4 ? C(1) / C(9) : C(1) / C(36));
+}
+
+// ---------------------------------------------------------------------------
+// Storage traits: compute type C, cells per 16-byte vector V, vector and
+// scalar loads (streaming: every population is read once per step) and
+// stores.  16-bit types round to nearest even on store.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Store;
+
+template <>
+struct Store<double> {
+  using C = double;
+  static constexpr int V = 2;
+  __device__ static void ld(const double* p, C (&o)[V]) {
+    const double2 t = __ldcs(reinterpret_cast<const double2*>(p));
+    o[0] = t.x;
+    o[1] = t.y;
+  }
+  __device__ static void st(double* p, const C (&o)[V]) {
+    __stcs(reinterpret_cast<double2*>(p), make_double2(o[0], o[1]));
+  }
+  __device__ static C ld1(const double* p) { return __ldcs(p); }
+  __device__ static C ldg1(const double* p) { return __ldg(p); }
+  __device__ static void st1(double* p, C v) { *p = v; }
+  __device__ static double cvt(C v) { return v; }
+};
+
+template <>
+struct Store<float> {
+  using C = float;
+  static constexpr int V = 4;
+  __device__ static void ld(const float* p, C (&o)[V]) {
+    const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+    o[0] = t.x;
+    o[1] = t.y;
+    o[2] = t.z;
+    o[3] = t.w;
+  }
+  __device__ static void st(float* p, const C (&o)[V]) {
+    __stcs(reinterpret_cast<float4*>(p), make_float4(o[0], o[1], o[2], o[3]));
+  }
+  __device__ static C ld1(const float* p) { return __ldcs(p); }
+  __device__ static C ldg1(const float* p) { return __ldg(p); }
+  __device__ static void st1(float* p, C v) { *p = v; }
+  __device__ static float cvt(C v) { return v; }
+};
+
+template <>
+struct Store<__half> {
+  using C = float;
+  static constexpr int V = 8;
+  __device__ static void ld(const __half* p, C (&o)[V]) {
+    const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
+    const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      __half2 h2;
+      memcpy(&h2, &w[k], 4);
+      const float2 f = __half22float2(h2);
+      o[2 * k] = f.x;
+      o[2 * k + 1] = f.y;
+    }
+  }
+  __device__ static void st(__half* p, const C (&o)[V]) {
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const __half2 h2 = __floats2half2_rn(o[2 * k], o[2 * k + 1]);
+      memcpy(&w[k], &h2, 4);
+    }
+    __stcs(reinterpret_cast<uint4*>(p), make_uint4(w[0], w[1], w[2], w[3]));
+  }
+  __device__ static C ld1(const __half* p) { return __half2float(*p); }
+  __device__ static C ldg1(const __half* p) { return __half2float(__ldg(p)); }
+  __device__ static void st1(__half* p, C v) { *p = __float2half_rn(v); }
+  __device__ static __half cvt(C v) { return __float2half_rn(v); }
+};
+
+template <>
+struct Store<__nv_bfloat16> {
+  using C = float;
+  static constexpr int V = 8;
+  __device__ static void ld(const __nv_bfloat16* p, C (&o)[V]) {
+    const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
+    const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      __nv_bfloat162 b2;
+      memcpy(&b2, &w[k], 4);
+      const float2 f = __bfloat1622float2(b2);
+      o[2 * k] = f.x;
+      o[2 * k + 1] = f.y;
+    }
+  }
+  __device__ static void st(__nv_bfloat16* p, const C (&o)[V]) {
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const __nv_bfloat162 b2 = __floats2bfloat162_rn(o[2 * k], o[2 * k + 1]);
+      memcpy(&w[k], &b2, 4);
+    }
+    __stcs(reinterpret_cast<uint4*>(p), make_uint4(w[0], w[1], w[2], w[3]));
+  }
+  __device__ static C ld1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  __device__ static C ldg1(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+  __device__ static void st1(__nv_bfloat16* p, C v) { *p = __float2bfloat16_rn(v); }
+  __device__ static __nv_bfloat16 cvt(C v) { return __float2bfloat16_rn(v); }
+};
+
+// ---------------------------------------------------------------------------
+// Moments of shifted populations (Eqs. cf_0, cf_1 as discrete sums).
+// ---------------------------------------------------------------------------
+template <typename C>
+__device__ __forceinline__ void moments(const C (&h)[9], C& drho, C& jx, C& jy) {
+  drho = ((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + (h[6] + h[7])) + h[8];
+  jx = (h[1] - h[2]) + (h[5] - h[6]) + (h[8] - h[7]);
+  jy = (h[3] - h[4]) + (h[5] - h[6]) + (h[7] - h[8]);
+}
+
+// Shifted equilibrium h^eq_i at (d_rho, u), Eq. (feq_1) minus w_i.
+template <typename C>
+__device__ __forceinline__ void equilibrium(C drho, C ux, C uy, C (&e)[9]) {
+  const C rho = C(1) + drho;
+  const C usq = C(1.5) * (ux * ux + uy * uy);
+  const C w0 = wt<C>(0), wa = wt<C>(1), wd = wt<C>(5);
+  e[0] = w0 * (drho - rho * usq);
+  // axis directions: c.u = +-ux, +-uy
+  {
+    const C a = C(4.5) * ux * ux - usq, b = C(3) * ux;
+    e[1] = wa * (drho + rho * (a + b));
+    e[2] = wa * (drho + rho * (a - b));
+  }
+  {
+    const C a = C(4.5) * uy * uy - usq, b = C(3) * uy;
+    e[3] = wa * (drho + rho * (a + b));
+    e[4] = wa * (drho + rho * (a - b));
+  }
+  {
+    const C s = ux + uy;  // c_5 = -c_6 = (1, 1)
+    const C a = C(4.5) * s * s - usq, b = C(3) * s;
+    e[5] = wd * (drho + rho * (a + b));
+    e[6] = wd * (drho + rho * (a - b));
+  }
+  {
+    const C d = uy - ux;  // c_7 = -c_8 = (-1, 1)
+    const C a = C(4.5) * d * d - usq, b = C(3) * d;
+    e[7] = wd * (drho + rho * (a + b));
+    e[8] = wd * (drho + rho * (a - b));
+  }
+}
+
+// BGK collision, Eq. (lbe_1) with dt = 1, on shifted populations.
+template <typename C>
+__device__ __forceinline__ void collide_bgk(C (&h)[9], C omega) {
+  C drho, jx, jy;
+  moments(h, drho, jx, jy);
+  const C inv = C(1) / (C(1) + drho);
+  C e[9];
+  equilibrium(drho, jx * inv, jy * inv, e);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) h[i] = h[i] + omega * (e[i] - h[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Geometry and NSBC parameters passed by value to the kernels.
+// ---------------------------------------------------------------------------
+struct Geom {
+  int nx, ny, pitch;
+  long long plane;  // elements between population planes
+};
+
+struct Nsbc {
+  double gamma, beta, kappa;
+  double m0[3];  // far-field (rho, ux, uy)
+  int order;     // 1 or 2
+};
+
+// Node k of the perimeter (k < 2 nx + 2 (ny - 2)) -> coordinates and outward
+// normal.  Order: bottom row, top row, left column, right column (corners
+// belong to the rows).
+__device__ __forceinline__ void perimeter_node(int k, int nx, int ny, int& x, int& y, int& nxn, int& nyn) {
+  if (k < 2 * nx) {
+    const bool top = k >= nx;
+    x = top ? k - nx : k;
+    y = top ? ny - 1 : 0;
+    nyn = top ? 1 : -1;
+    nxn = x == 0 ? -1 : (x == nx - 1 ? 1 : 0);
+  } else {
+    k -= 2 * nx;
+    const bool right = k >= ny - 2;
+    y = 1 + (right ? k - (ny - 2) : k);
+    x = right ? nx - 1 : 0;
+    nxn = right ? 1 : -1;
+    nyn = 0;
+  }
+}
+
+// Moments (rho, ux, uy) at node (x, y) in double, from the stored state.
+template <typename T>
+__device__ __forceinline__ void node_moments_f64(const T* __restrict__ A, const Geom& g, int x, int y,
+                                                 double (&m)[3]) {
+  using S = Store<T>;
+  const long long o = (long long)y * g.pitch + x;
+  double h[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) h[i] = (double)S::ldg1(A + i * g.plane + o);
+  double drho, jx, jy;
+  moments(h, drho, jx, jy);
+  const double rho = 1.0 + drho;
+  m[0] = rho;
+  m[1] = jx / rho;
+  m[2] = jy / rho;
+}
+
+}  // namespace lbmk

@@ -1,0 +1,318 @@
+// lbm_kernels.cuh -- the sm_103a kernels of one D2Q9 + NSBC time step and
+// their helpers (initialisation, macroscopic fields, FP64 reductions).
+//
+//   bulk_kernel  : fused pull-stream (Eq. lbe_0) + BGK collide (Eq. lbe_1)
+//                  over interior nodes, 16-byte vector loads/stores along x,
+//                  x-1 / x+1 neighbours exchanged with warp shuffles.
+//   nsbc_kernel  : the boundary of Sec. 5 on every edge and corner node:
+//                  gradient prediction (Eq. nes_2) with one-sided differences
+//                  whose points are loaded by neighbouring lanes and gathered
+//                  with warp shuffles, far-field blend (Eq. nes_3), mirror of
+//                  the outgoing non-equilibrium part (Eqs. nes_0, nes_1),
+//                  conservation correction (Eq. nes_4), then the ordinary
+//                  collision.
+// Both read buffer A (step n) and write disjoint nodes of buffer B (step
+// n+1), so they may run concurrently.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbmk {
+
+// ---------------------------------------------------------------------------
+// Bulk: interior rows 1..ny-2; each thread owns V consecutive cells of a row
+// segment (V = 16 bytes / sizeof(T)), blocks of BX threads cover BX*V cells
+// of `rows` consecutive rows.  Only nodes 1..nx-2 are stored.
+// ---------------------------------------------------------------------------
+template <typename T, int BX>
+__global__ void __launch_bounds__(BX) bulk_kernel(const T* __restrict__ A, T* __restrict__ B, Geom g,
+                                                  typename Store<T>::C omega, int rows) {
+  using S = Store<T>;
+  using C = typename S::C;
+  constexpr int V = S::V;
+  const int lane = threadIdx.x & 31;
+  const int x0 = (blockIdx.x * BX + threadIdx.x) * V;
+  const bool active = x0 < g.nx;
+  const long long P = g.plane;
+  const int y_begin = 1 + blockIdx.y * rows;
+  const int y_end = min(y_begin + rows, g.ny - 1);
+  for (int y = y_begin; y < y_end; ++y) {
+    const long long r0 = (long long)y * g.pitch + x0;
+    const long long rm = r0 - g.pitch, rp = r0 + g.pitch;
+    C v[9][V];
+    if (active) {
+      S::ld(A + 0 * P + r0, v[0]);
+      S::ld(A + 1 * P + r0, v[1]);
+      S::ld(A + 2 * P + r0, v[2]);
+      S::ld(A + 3 * P + rm, v[3]);
+      S::ld(A + 4 * P + rp, v[4]);
+      S::ld(A + 5 * P + rm, v[5]);
+      S::ld(A + 6 * P + rp, v[6]);
+      S::ld(A + 7 * P + rm, v[7]);
+      S::ld(A + 8 * P + rp, v[8]);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 9; ++i)
+#pragma unroll
+        for (int k = 0; k < V; ++k) v[i][k] = C(0);
+    }
+    // values at x0-1 for the directions pulled from the left (1, 5, 8) and
+    // at x0+V for those pulled from the right (2, 6, 7): from the
+    // neighbouring lane, or a scalar load at the warp's ends.
+    C l1 = __shfl_up_sync(0xffffffffu, v[1][V - 1], 1);
+    C l5 = __shfl_up_sync(0xffffffffu, v[5][V - 1], 1);
+    C l8 = __shfl_up_sync(0xffffffffu, v[8][V - 1], 1);
+    C r2 = __shfl_down_sync(0xffffffffu, v[2][0], 1);
+    C r6 = __shfl_down_sync(0xffffffffu, v[6][0], 1);
+    C r7 = __shfl_down_sync(0xffffffffu, v[7][0], 1);
+    if (lane == 0 && active && x0 > 0) {
+      l1 = S::ld1(A + 1 * P + r0 - 1);
+      l5 = S::ld1(A + 5 * P + rm - 1);
+      l8 = S::ld1(A + 8 * P + rp - 1);
+    }
+    if (lane == 31 && x0 + V < g.nx) {
+      r2 = S::ld1(A + 2 * P + r0 + V);
+      r6 = S::ld1(A + 6 * P + rp + V);
+      r7 = S::ld1(A + 7 * P + rm + V);
+    }
+    C o[9][V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      C h[9];
+      h[0] = v[0][k];
+      h[1] = k == 0 ? l1 : v[1][k - 1];
+      h[2] = k == V - 1 ? r2 : v[2][k + 1];
+      h[3] = v[3][k];
+      h[4] = v[4][k];
+      h[5] = k == 0 ? l5 : v[5][k - 1];
+      h[6] = k == V - 1 ? r6 : v[6][k + 1];
+      h[7] = k == V - 1 ? r7 : v[7][k + 1];
+      h[8] = k == 0 ? l8 : v[8][k - 1];
+      collide_bgk(h, omega);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) o[i][k] = h[i];
+    }
+    if (active) {
+      if (x0 >= 1 && x0 + V <= g.nx - 1) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) S::st(B + i * P + r0, o[i]);
+      } else {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+          const int x = x0 + k;
+          if (x >= 1 && x <= g.nx - 2) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) S::st1(B + i * P + r0 + k, o[i][k]);
+          }
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// NSBC: four lanes per perimeter node.  Lane q loads the node b - q n and
+// forms its moments in double (q = 0, 1, and 2 for the second-order
+// difference); lane 0 gathers them by shuffles within its quad, predicts
+// and blends m_c in double, then rebuilds, corrects and collides the node in
+// the compute type.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128) nsbc_kernel(const T* __restrict__ A, T* __restrict__ B, Geom g, Nsbc p,
+                                                   typename Store<T>::C omega) {
+  using S = Store<T>;
+  using C = typename S::C;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int node = t >> 2, q = t & 3;
+  const int perim = 2 * g.nx + 2 * (g.ny - 2);
+  if (node >= perim) return;  // a quad leaves together
+  const unsigned quad = 0xFu << ((threadIdx.x & 31) & ~3);
+  int x, y, nxn, nyn;
+  perimeter_node(node, g.nx, g.ny, x, y, nxn, nyn);
+
+  double m[3] = {0.0, 0.0, 0.0};
+  if (q <= p.order) node_moments_f64(A, g, x - q * nxn, y - q * nyn, m);
+  double m1[3], m2[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    m1[c] = __shfl_down_sync(quad, m[c], 1, 4);
+    m2[c] = __shfl_down_sync(quad, m[c], 2, 4);
+  }
+  if (q != 0) return;
+
+  // Eq. (nes_2): m_p = m_b - gamma d_n m along the outward unit normal;
+  // Eq. (nes_3): m_c = (1 - beta) m_p + beta m_0.
+  const double len = (nxn != 0 && nyn != 0) ? 1.4142135623730951 : 1.0;
+  double mc[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const double dn = p.order == 2 ? (3.0 * m[c] - 4.0 * m1[c] + m2[c]) / (2.0 * len) : (m[c] - m1[c]) / len;
+    const double mp = m[c] - p.gamma * dn;
+    mc[c] = (1.0 - p.beta) * mp + p.beta * p.m0[c];
+  }
+
+  // pulled populations; unknown where the source lies outside the domain
+  C h[9];
+  bool known[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int sx = x - cx(i), sy = y - cy(i);
+    known[i] = sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny;
+    h[i] = known[i] ? S::ldg1(A + i * g.plane + (long long)sy * g.pitch + sx) : C(0);
+  }
+
+  // Eqs. (nes_0), (nes_1): f_in = f_in^eq(m_c) + f_out - f_out^eq(m_c)
+  const C drho_c = C(mc[0] - 1.0);
+  C e[9];
+  equilibrium(drho_c, C(mc[1]), C(mc[2]), e);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const int o = opp(i);
+    if (!known[i]) h[i] = known[o] ? e[i] + (h[o] - e[o]) : e[i];
+  }
+
+  // Eq. (nes_4): f_i -= w_i (d_rho + kappa c_i . d(rho u))
+  C drho, jx, jy;
+  moments(h, drho, jx, jy);
+  const C d_rho = drho - drho_c;
+  const C d_jx = jx - C(mc[0] * mc[1]);
+  const C d_jy = jy - C(mc[0] * mc[2]);
+  const C kap = C(p.kappa);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) h[i] -= wt<C>(i) * (d_rho + kap * (C(cx(i)) * d_jx + C(cy(i)) * d_jy));
+
+  collide_bgk(h, omega);
+  const long long o = (long long)y * g.pitch + x;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) S::st1(B + i * g.plane + o, h[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Initialisation at equilibrium (Eq. feq_1) from double fields [ny][nx];
+// padding columns are zeroed.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void init_kernel(T* __restrict__ A, Geom g, const double* __restrict__ rho,
+                            const double* __restrict__ ux, const double* __restrict__ uy) {
+  using S = Store<T>;
+  const long long n = (long long)g.ny * g.pitch;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(idx / g.pitch), x = (int)(idx % g.pitch);
+    double e[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    if (x < g.nx) {
+      const long long k = (long long)y * g.nx + x;
+      equilibrium(rho[k] - 1.0, ux[k], uy[k], e);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) A[i * g.plane + idx] = S::cvt(typename S::C(e[i]));
+  }
+}
+
+// Macroscopic fields (double) of the stored state.
+template <typename T>
+__global__ void macros_kernel(const T* __restrict__ A, Geom g, double* __restrict__ rho, double* __restrict__ ux,
+                              double* __restrict__ uy) {
+  const long long n = (long long)g.ny * g.nx;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(k / g.nx), x = (int)(k % g.nx);
+    double m[3];
+    node_moments_f64(A, g, x, y, m);
+    rho[k] = m[0];
+    ux[k] = m[1];
+    uy[k] = m[2];
+  }
+}
+
+// One population plane <-> absolute double field [ny][nx].
+template <typename T>
+__global__ void plane_to_f64(const T* __restrict__ A, Geom g, int i, double* __restrict__ out) {
+  using S = Store<T>;
+  const long long n = (long long)g.ny * g.nx;
+  const double w = wt<double>(i);
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(k / g.nx), x = (int)(k % g.nx);
+    out[k] = (double)S::ldg1(A + i * g.plane + (long long)y * g.pitch + x) + w;
+  }
+}
+
+template <typename T>
+__global__ void f64_to_plane(T* __restrict__ A, Geom g, int i, const double* __restrict__ in) {
+  using S = Store<T>;
+  const long long n = (long long)g.ny * g.pitch;
+  const double w = wt<double>(i);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int y = (int)(idx / g.pitch), x = (int)(idx % g.pitch);
+    const double v = x < g.nx ? in[(long long)y * g.nx + x] - w : 0.0;
+    A[i * g.plane + idx] = S::cvt(typename S::C(v));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 reductions: per-block partial sums (4 doubles per block) into
+// `partials`, then one block sums the partials in a fixed order.
+// ---------------------------------------------------------------------------
+struct RefField {
+  const double *rho, *ux, *uy;
+  int pitch;
+};
+
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* smem) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) smem[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < NT / 32; ++k) s += smem[k];
+  return s;  // valid in thread 0
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) reduce_kernel(const T* __restrict__ A, Geom g, RefField ref, double rho_ff,
+                                                    double uxf, double uyf, double* __restrict__ partials) {
+  __shared__ double smem[NT / 32];
+  const double cs2 = 1.0 / 3.0;
+  double s[4] = {0.0, 0.0, 0.0, 0.0};
+  const long long n = (long long)g.ny * g.nx;
+  for (long long k = blockIdx.x * (long long)NT + threadIdx.x; k < n; k += (long long)gridDim.x * NT) {
+    const int y = (int)(k / g.nx), x = (int)(k % g.nx);
+    double m[3];
+    node_moments_f64(A, g, x, y, m);
+    double rr = rho_ff, ur = uxf, vr = uyf;
+    if (ref.rho) {
+      const long long r = (long long)y * ref.pitch + x;
+      rr = ref.rho[r];
+      ur = ref.ux[r];
+      vr = ref.uy[r];
+    }
+    const double dr = m[0] - rr, du = m[1] - ur, dv = m[2] - vr;
+    s[0] += m[0];
+    s[1] += 0.5 * (cs2 * dr * dr / rho_ff + rho_ff * (du * du + dv * dv));
+    s[2] += 0.5 * m[0] * (m[1] * m[1] + m[2] * m[2]);
+    s[3] += (isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]) && m[0] > 0.0) ? 0.0 : 1.0;
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const double t = block_sum<NT>(s[c], smem);
+    if (threadIdx.x == 0) partials[blockIdx.x * 4 + c] = t;
+  }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) reduce_finish(const double* __restrict__ partials, int nblocks,
+                                                    double* __restrict__ out) {
+  __shared__ double smem[NT / 32];
+  for (int c = 0; c < 4; ++c) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += NT) s += partials[b * 4 + c];
+    const double t = block_sum<NT>(s, smem);
+    if (threadIdx.x == 0) out[c] = t;
+  }
+}
+
+}  // namespace lbmk

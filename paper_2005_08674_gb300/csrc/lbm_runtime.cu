@@ -1,0 +1,607 @@
+// lbm_runtime.cu -- host runtime behind the C ABI of include/lbm.h: handle
+// state, device memory (library-owned or caller-bound), stream, CUDA-graph
+// replay of the step loop, launch-shape autotuning, and the entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_kernels.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+#define LBM_CUDA(call)                                                                          \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return fail(e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s (%s:%d)", #call, \
+                  cudaGetErrorString(e_), __FILE__, __LINE__);                                  \
+  } while (0)
+
+constexpr int kGraphSteps = 16;  // steps per captured graph (even: buffers return to their roles)
+constexpr int kReduceThreads = 256;
+constexpr int kReduceBlocks = 1216;  // 8 x 152 SMs
+constexpr int kNsbcThreads = 128;
+
+// launch shapes compiled for the bulk kernel: threads per block along x
+constexpr int kShapesBX[] = {64, 128, 256, 512};
+constexpr int kShapesRows[] = {1, 2, 4, 8};
+
+}  // namespace
+
+struct lbm {
+  int nx = 0, ny = 0, pitch = 0;
+  long long plane = 0;  // elements per population plane (256-byte multiple)
+  double tau = 0.0;
+  lbmk::Nsbc nsbc{};
+  int storage = LBM_F32;
+  size_t elt = 4;
+  void* buf[2] = {nullptr, nullptr};
+  void* scratch = nullptr;
+  bool owns_memory = false;
+  bool bound = false;
+  bool initialised = false;
+  int cur = 0;  // buffer holding the current state
+  long long steps = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr, side = nullptr;  // capture stream and NSBC branch
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by starting buffer
+  int bx = 128, rows = 1;
+  int device = 0;
+  // per-launch timing (lbm_profile): event pairs around every bulk and NSBC launch
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+};
+
+namespace {
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+lbmk::Geom geom(const lbm_t* h) { return lbmk::Geom{h->nx, h->ny, h->pitch, h->plane}; }
+
+size_t macro_bytes(const lbm_t* h) { return round_up((size_t)h->nx * h->ny * sizeof(double), 256); }
+
+// scratch layout: rho | ux | uy (each macro_bytes) | partials | out[4]
+double* scratch_field(lbm_t* h, int c) {
+  return reinterpret_cast<double*>(static_cast<char*>(h->scratch) + c * macro_bytes(h));
+}
+double* scratch_partials(lbm_t* h) { return scratch_field(h, 3); }
+double* scratch_out(lbm_t* h) { return scratch_partials(h) + kReduceBlocks * 4; }
+
+void drop_graphs(lbm_t* h) {
+  for (auto& g : h->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+int ensure_memory(lbm_t* h) {
+  if (h->bound) return LBM_OK;
+  const size_t bb = lbm_buffer_bytes(h), sb = lbm_scratch_bytes(h);
+  LBM_CUDA(cudaGetDevice(&h->device));
+  LBM_CUDA(cudaMalloc(&h->buf[0], bb));
+  LBM_CUDA(cudaMalloc(&h->buf[1], bb));
+  LBM_CUDA(cudaMalloc(&h->scratch, sb));
+  LBM_CUDA(cudaMemset(h->buf[0], 0, bb));
+  LBM_CUDA(cudaMemset(h->buf[1], 0, bb));
+  h->owns_memory = true;
+  h->bound = true;
+  return LBM_OK;
+}
+
+int ensure_streams(lbm_t* h) {
+  if (!h->cap) {
+    LBM_CUDA(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+    LBM_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+    LBM_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+    LBM_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+  }
+  return LBM_OK;
+}
+
+int grid_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  return (int)(b < 1 ? 1 : (b > 152LL * 32 ? 152LL * 32 : b));
+}
+
+// ---- typed launchers ------------------------------------------------------
+
+template <typename T, int BX>
+void launch_bulk_bx(const lbm_t* h, const void* a, void* b, int rows, cudaStream_t s) {
+  using C = typename lbmk::Store<T>::C;
+  constexpr int V = lbmk::Store<T>::V;
+  const int nvec = (h->nx + V - 1) / V;
+  dim3 grid((nvec + BX - 1) / BX, (h->ny - 2 + rows - 1) / rows);
+  lbmk::bulk_kernel<T, BX><<<grid, BX, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
+                                              C(1.0 / h->tau), rows);
+}
+
+template <typename T>
+void launch_bulk(const lbm_t* h, const void* a, void* b, int bx, int rows, cudaStream_t s) {
+  switch (bx) {
+    case 64: launch_bulk_bx<T, 64>(h, a, b, rows, s); break;
+    case 256: launch_bulk_bx<T, 256>(h, a, b, rows, s); break;
+    case 512: launch_bulk_bx<T, 512>(h, a, b, rows, s); break;
+    default: launch_bulk_bx<T, 128>(h, a, b, rows, s); break;
+  }
+}
+
+template <typename T>
+void launch_nsbc(const lbm_t* h, const void* a, void* b, cudaStream_t s) {
+  using C = typename lbmk::Store<T>::C;
+  const long long perim = 2LL * h->nx + 2LL * (h->ny - 2);
+  const int blocks = (int)((perim * 4 + kNsbcThreads - 1) / kNsbcThreads);
+  lbmk::nsbc_kernel<T><<<blocks, kNsbcThreads, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
+                                                       h->nsbc, C(1.0 / h->tau));
+}
+
+template <typename F>
+void dispatch(int storage, F&& f) {
+  switch (storage) {
+    case LBM_F64: f(double{}); break;
+    case LBM_F16: f(__half{}); break;
+    case LBM_BF16: f(__nv_bfloat16{}); break;
+    default: f(float{}); break;
+  }
+}
+
+// One step from buffer `from` to 1 - from.  With `fork`, the NSBC kernel runs
+// on the side stream concurrently with the bulk kernel (both only read
+// buffer `from` and write disjoint nodes of the other buffer).
+void enqueue_step(const lbm_t* h, int from, cudaStream_t s, bool fork) {
+  const void* a = h->buf[from];
+  void* b = h->buf[1 - from];
+  dispatch(h->storage, [&](auto tag) {
+    using T = decltype(tag);
+    if (fork) {
+      cudaEventRecord(h->ev_fork, s);
+      cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+      launch_nsbc<T>(h, a, b, h->side);
+      launch_bulk<T>(h, a, b, h->bx, h->rows, s);
+      cudaEventRecord(h->ev_join, h->side);
+      cudaStreamWaitEvent(s, h->ev_join, 0);
+    } else {
+      launch_bulk<T>(h, a, b, h->bx, h->rows, s);
+      launch_nsbc<T>(h, a, b, s);
+    }
+  });
+}
+
+int capture_graph(lbm_t* h, int from) {
+  cudaGraph_t g = nullptr;
+  LBM_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+  for (int k = 0; k < kGraphSteps; ++k) enqueue_step(h, (from + k) & 1, h->cap, true);
+  cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+  if (e != cudaSuccess) return fail(LBM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&h->graph[from], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(LBM_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+int profiled_event(lbm_t* h, cudaEvent_t* out) {
+  if (h->ev_used == h->ev_pool.size()) {
+    cudaEvent_t e;
+    LBM_CUDA(cudaEventCreate(&e));
+    h->ev_pool.push_back(e);
+  }
+  *out = h->ev_pool[h->ev_used++];
+  return LBM_OK;
+}
+
+// One step with an event pair around each kernel, both on the handle's stream.
+int enqueue_step_profiled(lbm_t* h, int from) {
+  const void* a = h->buf[from];
+  void* b = h->buf[1 - from];
+  cudaEvent_t e[4];
+  for (auto& x : e) {
+    int rc = profiled_event(h, &x);
+    if (rc) return rc;
+  }
+  dispatch(h->storage, [&](auto tag) {
+    using T = decltype(tag);
+    cudaEventRecord(e[0], h->stream);
+    launch_bulk<T>(h, a, b, h->bx, h->rows, h->stream);
+    cudaEventRecord(e[1], h->stream);
+    cudaEventRecord(e[2], h->stream);
+    launch_nsbc<T>(h, a, b, h->stream);
+    cudaEventRecord(e[3], h->stream);
+  });
+  return LBM_OK;
+}
+
+int check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(LBM_ECUDA, "kernel launch failed: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+bool shape_compiled(int bx, int rows) {
+  bool okb = false, okr = false;
+  for (int v : kShapesBX) okb |= v == bx;
+  for (int v : kShapesRows) okr |= v == rows;
+  return okb && okr;
+}
+
+}  // namespace
+
+// =========================================================================
+// C ABI
+// =========================================================================
+extern "C" {
+
+const char* lbm_last_error(void) { return g_last_error.c_str(); }
+
+lbm_t* lbm_create(int32_t nx, int32_t ny, double tau, double farfield_rho, const double farfield_u[2]) {
+  if (nx < 3 || ny < 3 || nx > 65536 || ny > 65536) {
+    fail(LBM_EINVAL, "lbm_create: nx=%d ny=%d outside [3, 65536]", nx, ny);
+    return nullptr;
+  }
+  if (!std::isfinite(tau) || !(tau > 0.5)) {
+    fail(LBM_EINVAL, "lbm_create: tau=%g must be finite and > 0.5", tau);
+    return nullptr;
+  }
+  if (!farfield_u || !std::isfinite(farfield_rho) || !(farfield_rho > 0.0) || !std::isfinite(farfield_u[0]) ||
+      !std::isfinite(farfield_u[1])) {
+    fail(LBM_EINVAL, "lbm_create: far field must be finite with rho > 0 and u non-NULL");
+    return nullptr;
+  }
+  lbm_t* h = new lbm_t();
+  h->nx = nx;
+  h->ny = ny;
+  h->tau = tau;
+  h->nsbc.gamma = 0.6;
+  h->nsbc.beta = 0.0;
+  h->nsbc.kappa = 3.0;
+  h->nsbc.order = 1;
+  h->nsbc.m0[0] = farfield_rho;
+  h->nsbc.m0[1] = farfield_u[0];
+  h->nsbc.m0[2] = farfield_u[1];
+  lbm_set_precision(h, LBM_F32);
+  return h;
+}
+
+void lbm_destroy(lbm_t* h) {
+  if (!h) return;
+  if (h->stream || h->cap) cudaStreamSynchronize(h->stream);
+  drop_graphs(h);
+  if (h->owns_memory) {
+    cudaFree(h->buf[0]);
+    cudaFree(h->buf[1]);
+    cudaFree(h->scratch);
+  }
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->cap) {
+    cudaStreamDestroy(h->cap);
+    cudaStreamDestroy(h->side);
+    cudaEventDestroy(h->ev_fork);
+    cudaEventDestroy(h->ev_join);
+  }
+  delete h;
+}
+
+int lbm_set_nsbc(lbm_t* h, double gamma, double beta, double kappa, int32_t grad_order) {
+  if (!h) return fail(LBM_EINVAL, "lbm_set_nsbc: NULL handle");
+  if (!std::isfinite(gamma) || !std::isfinite(beta) || !std::isfinite(kappa) || (grad_order != 1 && grad_order != 2))
+    return fail(LBM_EINVAL, "lbm_set_nsbc: need finite gamma, beta, kappa and grad_order 1 or 2");
+  h->nsbc.gamma = gamma;
+  h->nsbc.beta = beta;
+  h->nsbc.kappa = kappa;
+  h->nsbc.order = grad_order;
+  drop_graphs(h);
+  return LBM_OK;
+}
+
+int lbm_set_precision(lbm_t* h, int32_t storage) {
+  if (!h) return fail(LBM_EINVAL, "lbm_set_precision: NULL handle");
+  if (storage < LBM_F64 || storage > LBM_BF16) return fail(LBM_EINVAL, "lbm_set_precision: unknown storage %d", storage);
+  if (h->bound) return fail(LBM_ESTATE, "lbm_set_precision: memory already bound or allocated");
+  h->storage = storage;
+  h->elt = storage == LBM_F64 ? 8 : (storage == LBM_F32 ? 4 : 2);
+  h->pitch = (int)round_up((size_t)h->nx, 64);
+  h->plane = (long long)(round_up((size_t)h->ny * h->pitch * h->elt, 256) / h->elt);
+  return LBM_OK;
+}
+
+int lbm_set_stream(lbm_t* h, void* cuda_stream) {
+  if (!h) return fail(LBM_EINVAL, "lbm_set_stream: NULL handle");
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  return LBM_OK;
+}
+
+size_t lbm_buffer_bytes(const lbm_t* h) { return h ? (size_t)9 * h->plane * h->elt : 0; }
+
+size_t lbm_scratch_bytes(const lbm_t* h) {
+  return h ? 3 * macro_bytes(h) + round_up((kReduceBlocks * 4 + 4) * sizeof(double), 256) : 0;
+}
+
+int lbm_bind(lbm_t* h, void* dev_a, void* dev_b, void* dev_scratch) {
+  if (!h || !dev_a || !dev_b || !dev_scratch) return fail(LBM_EINVAL, "lbm_bind: NULL argument");
+  if (h->bound) return fail(LBM_ESTATE, "lbm_bind: memory already bound or allocated");
+  for (void* p : {dev_a, dev_b, dev_scratch})
+    if (reinterpret_cast<uintptr_t>(p) % 256) return fail(LBM_EINVAL, "lbm_bind: pointers must be 256-byte aligned");
+  LBM_CUDA(cudaGetDevice(&h->device));
+  h->buf[0] = dev_a;
+  h->buf[1] = dev_b;
+  h->scratch = dev_scratch;
+  h->bound = true;
+  h->owns_memory = false;
+  return LBM_OK;
+}
+
+int lbm_init_device(lbm_t* h, const double* d_rho, const double* d_ux, const double* d_uy) {
+  if (!h || !d_rho || !d_ux || !d_uy) return fail(LBM_EINVAL, "lbm_init_device: NULL argument");
+  int rc = ensure_memory(h);
+  if (rc) return rc;
+  h->cur = 0;
+  const long long n = (long long)h->ny * h->pitch;
+  dispatch(h->storage, [&](auto tag) {
+    using T = decltype(tag);
+    lbmk::init_kernel<T><<<grid_for(n, 256), 256, 0, h->stream>>>(static_cast<T*>(h->buf[0]), geom(h), d_rho, d_ux,
+                                                                   d_uy);
+    // the other buffer's boundary-free padding and untouched nodes start defined
+    lbmk::init_kernel<T><<<grid_for(n, 256), 256, 0, h->stream>>>(static_cast<T*>(h->buf[1]), geom(h), d_rho, d_ux,
+                                                                   d_uy);
+  });
+  rc = check_launch();
+  if (rc) return rc;
+  h->initialised = true;
+  h->steps = 0;
+  return LBM_OK;
+}
+
+int lbm_init(lbm_t* h, const double* rho, const double* ux, const double* uy) {
+  if (!h || !rho || !ux || !uy) return fail(LBM_EINVAL, "lbm_init: NULL argument");
+  int rc = ensure_memory(h);
+  if (rc) return rc;
+  const size_t bytes = (size_t)h->nx * h->ny * sizeof(double);
+  const double* src[3] = {rho, ux, uy};
+  for (int c = 0; c < 3; ++c)
+    LBM_CUDA(cudaMemcpyAsync(scratch_field(h, c), src[c], bytes, cudaMemcpyHostToDevice, h->stream));
+  rc = lbm_init_device(h, scratch_field(h, 0), scratch_field(h, 1), scratch_field(h, 2));
+  if (rc) return rc;
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_step(lbm_t* h, int32_t n) {
+  if (!h) return fail(LBM_EINVAL, "lbm_step: NULL handle");
+  if (n < 0) return fail(LBM_EINVAL, "lbm_step: n=%d < 0", n);
+  if (!h->initialised) return fail(LBM_ESTATE, "lbm_step: call lbm_init first");
+  int rc = ensure_streams(h);
+  if (rc) return rc;
+  int left = n;
+  if (h->profiling) {
+    for (; left > 0; --left) {
+      rc = enqueue_step_profiled(h, h->cur);
+      if (rc) return rc;
+      h->cur ^= 1;
+    }
+  }
+  if (left >= kGraphSteps) {
+    if (!h->graph[h->cur]) {
+      rc = capture_graph(h, h->cur);
+      if (rc) return rc;
+    }
+    while (left >= kGraphSteps) {
+      LBM_CUDA(cudaGraphLaunch(h->graph[h->cur], h->stream));
+      left -= kGraphSteps;  // kGraphSteps is even: h->cur is unchanged
+    }
+  }
+  for (; left > 0; --left) {
+    enqueue_step(h, h->cur, h->stream, false);
+    h->cur ^= 1;
+  }
+  rc = check_launch();
+  if (rc) return rc;
+  h->steps += n;
+  return LBM_OK;
+}
+
+int64_t lbm_steps_done(const lbm_t* h) { return h ? h->steps : -1; }
+
+int lbm_get_macros_device(lbm_t* h, double* d_rho, double* d_ux, double* d_uy) {
+  if (!h || !d_rho || !d_ux || !d_uy) return fail(LBM_EINVAL, "lbm_get_macros_device: NULL argument");
+  if (!h->initialised) return fail(LBM_ESTATE, "lbm_get_macros_device: call lbm_init first");
+  const long long n = (long long)h->nx * h->ny;
+  dispatch(h->storage, [&](auto tag) {
+    using T = decltype(tag);
+    lbmk::macros_kernel<T><<<grid_for(n, 256), 256, 0, h->stream>>>(static_cast<const T*>(h->buf[h->cur]), geom(h),
+                                                                     d_rho, d_ux, d_uy);
+  });
+  return check_launch();
+}
+
+int lbm_get_macros(lbm_t* h, double* rho, double* ux, double* uy) {
+  if (!h || !rho || !ux || !uy) return fail(LBM_EINVAL, "lbm_get_macros: NULL argument");
+  int rc = lbm_get_macros_device(h, scratch_field(h, 0), scratch_field(h, 1), scratch_field(h, 2));
+  if (rc) return rc;
+  const size_t bytes = (size_t)h->nx * h->ny * sizeof(double);
+  double* dst[3] = {rho, ux, uy};
+  for (int c = 0; c < 3; ++c)
+    LBM_CUDA(cudaMemcpyAsync(dst[c], scratch_field(h, c), bytes, cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  return LBM_OK;
+}
+
+int lbm_get_populations(lbm_t* h, double* f) {
+  if (!h || !f) return fail(LBM_EINVAL, "lbm_get_populations: NULL argument");
+  if (!h->initialised) return fail(LBM_ESTATE, "lbm_get_populations: call lbm_init first");
+  const long long n = (long long)h->nx * h->ny;
+  for (int i = 0; i < 9; ++i) {
+    dispatch(h->storage, [&](auto tag) {
+      using T = decltype(tag);
+      lbmk::plane_to_f64<T><<<grid_for(n, 256), 256, 0, h->stream>>>(static_cast<const T*>(h->buf[h->cur]), geom(h), i,
+                                                                      scratch_field(h, 0));
+    });
+    int rc = check_launch();
+    if (rc) return rc;
+    LBM_CUDA(cudaMemcpyAsync(f + i * n, scratch_field(h, 0), n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  return LBM_OK;
+}
+
+int lbm_set_populations(lbm_t* h, const double* f) {
+  if (!h || !f) return fail(LBM_EINVAL, "lbm_set_populations: NULL argument");
+  int rc = ensure_memory(h);
+  if (rc) return rc;
+  const long long n = (long long)h->nx * h->ny;
+  h->cur = 0;
+  for (int i = 0; i < 9; ++i) {
+    LBM_CUDA(cudaMemcpyAsync(scratch_field(h, 0), f + i * n, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    dispatch(h->storage, [&](auto tag) {
+      using T = decltype(tag);
+      for (int b = 0; b < 2; ++b)
+        lbmk::f64_to_plane<T><<<grid_for((long long)h->ny * h->pitch, 256), 256, 0, h->stream>>>(
+            static_cast<T*>(h->buf[b]), geom(h), i, scratch_field(h, 0));
+    });
+    rc = check_launch();
+    if (rc) return rc;
+    LBM_CUDA(cudaStreamSynchronize(h->stream));
+  }
+  h->initialised = true;
+  h->steps = 0;
+  return LBM_OK;
+}
+
+int lbm_reduce(lbm_t* h, const double* ref_rho, const double* ref_ux, const double* ref_uy, int32_t ref_pitch,
+               double out[4]) {
+  if (!h || !out) return fail(LBM_EINVAL, "lbm_reduce: NULL argument");
+  if (!h->initialised) return fail(LBM_ESTATE, "lbm_reduce: call lbm_init first");
+  if (ref_rho && (!ref_ux || !ref_uy || ref_pitch < h->nx))
+    return fail(LBM_EINVAL, "lbm_reduce: reference needs rho, ux, uy and pitch >= nx");
+  lbmk::RefField ref{ref_rho, ref_ux, ref_uy, ref_pitch};
+  const long long n = (long long)h->nx * h->ny;
+  const int blocks = (int)std::min<long long>(kReduceBlocks, (n + kReduceThreads - 1) / kReduceThreads);
+  dispatch(h->storage, [&](auto tag) {
+    using T = decltype(tag);
+    lbmk::reduce_kernel<T, kReduceThreads><<<blocks, kReduceThreads, 0, h->stream>>>(
+        static_cast<const T*>(h->buf[h->cur]), geom(h), ref, h->nsbc.m0[0], h->nsbc.m0[1], h->nsbc.m0[2],
+        scratch_partials(h));
+  });
+  lbmk::reduce_finish<kReduceThreads><<<1, kReduceThreads, 0, h->stream>>>(scratch_partials(h), blocks, scratch_out(h));
+  int rc = check_launch();
+  if (rc) return rc;
+  LBM_CUDA(cudaMemcpyAsync(out, scratch_out(h), 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  if (out[3] > 0.0) return fail(LBM_EUNSTABLE, "lbm_reduce: %.0f nodes with non-finite or non-positive density", out[3]);
+  return LBM_OK;
+}
+
+int lbm_profile(lbm_t* h, int32_t enable) {
+  if (!h) return fail(LBM_EINVAL, "lbm_profile: NULL handle");
+  h->profiling = enable != 0;
+  h->ev_used = 0;
+  return LBM_OK;
+}
+
+int lbm_profile_read(lbm_t* h, double out[4]) {
+  if (!h || !out) return fail(LBM_EINVAL, "lbm_profile_read: NULL argument");
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  double bulk = 0.0, nsbc = 0.0;
+  const size_t steps = h->ev_used / 4;
+  for (size_t k = 0; k < steps; ++k) {
+    float a = 0.f, b = 0.f;
+    LBM_CUDA(cudaEventElapsedTime(&a, h->ev_pool[4 * k], h->ev_pool[4 * k + 1]));
+    LBM_CUDA(cudaEventElapsedTime(&b, h->ev_pool[4 * k + 2], h->ev_pool[4 * k + 3]));
+    bulk += a;
+    nsbc += b;
+  }
+  out[0] = bulk;
+  out[1] = (double)steps;
+  out[2] = nsbc;
+  out[3] = (double)steps;
+  h->ev_used = 0;
+  return LBM_OK;
+}
+
+int lbm_set_launch(lbm_t* h, int32_t threads_x, int32_t rows) {
+  if (!h) return fail(LBM_EINVAL, "lbm_set_launch: NULL handle");
+  if (threads_x == 0 && rows == 0) {
+    threads_x = 128;
+    rows = 1;
+  }
+  if (!shape_compiled(threads_x, rows))
+    return fail(LBM_EINVAL, "lbm_set_launch: shape (%d, %d) not compiled", threads_x, rows);
+  h->bx = threads_x;
+  h->rows = rows;
+  drop_graphs(h);
+  return LBM_OK;
+}
+
+int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, double* ms_per_step) {
+  if (!h) return fail(LBM_EINVAL, "lbm_autotune: NULL handle");
+  if (!h->initialised) return fail(LBM_ESTATE, "lbm_autotune: call lbm_init first");
+  int rc = ensure_streams(h);
+  if (rc) return rc;
+  // keep the state: copy the current buffer aside, restore it at the end
+  const size_t bb = lbm_buffer_bytes(h);
+  void* backup = nullptr;
+  LBM_CUDA(cudaMallocAsync(&backup, bb, h->stream));
+  LBM_CUDA(cudaMemcpyAsync(backup, h->buf[h->cur], bb, cudaMemcpyDeviceToDevice, h->stream));
+  cudaEvent_t e0, e1;
+  LBM_CUDA(cudaEventCreate(&e0));
+  LBM_CUDA(cudaEventCreate(&e1));
+  const long long cells = (long long)h->nx * h->ny;
+  const int reps = (int)std::max<long long>(4, std::min<long long>(64, (1LL << 28) / std::max(cells, 1LL)));
+  float best = 1e30f;
+  int best_bx = h->bx, best_rows = h->rows;
+  for (int bx : kShapesBX)
+    for (int r : kShapesRows) {
+      if (r > 1 && (h->ny - 2) / r < 152) continue;  // too few blocks to fill the GPU
+      h->bx = bx;
+      h->rows = r;
+      for (int k = 0; k < 2; ++k) enqueue_step(h, k & 1, h->stream, false);
+      cudaEventRecord(e0, h->stream);
+      for (int k = 0; k < reps; ++k) enqueue_step(h, k & 1, h->stream, false);
+      cudaEventRecord(e1, h->stream);
+      LBM_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= reps;
+      if (ms < best) {
+        best = ms;
+        best_bx = bx;
+        best_rows = r;
+      }
+    }
+  rc = check_launch();
+  h->bx = best_bx;
+  h->rows = best_rows;
+  drop_graphs(h);
+  LBM_CUDA(cudaMemcpyAsync(h->buf[h->cur], backup, bb, cudaMemcpyDeviceToDevice, h->stream));
+  LBM_CUDA(cudaFreeAsync(backup, h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (threads_x) *threads_x = best_bx;
+  if (rows) *rows = best_rows;
+  if (ms_per_step) *ms_per_step = best;
+  return LBM_OK;
+}
+
+}  // extern "C"

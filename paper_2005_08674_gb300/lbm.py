@@ -1,0 +1,301 @@
+"""Thin ctypes binding of the C ABI declared in include/lbm.h.
+
+Functions keep the C names and only marshal arguments; every step of the
+simulation runs in the CUDA library.  PyTorch supplies device memory
+(``Simulation`` binds torch-allocated buffers) and the CUDA stream.  There is
+no CPU fallback: if ``liblbm.so`` is missing or fails to load, importing this
+module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblbm.so")
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE = 0, -1, -2, -3, -4, -5
+LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2, 3
+STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16, "bf16": LBM_BF16}
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built; run paper_2005_08674_gb300.build.build() "
+                      "(nvcc, sm_103a) first")
+
+_L = ctypes.CDLL(LIB_PATH)
+_vp, _dp, _i32, _dbl = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int32, ctypes.c_double
+_i32p = ctypes.POINTER(ctypes.c_int32)
+
+_SIGS = {
+    "lbm_create": (_vp, [_i32, _i32, _dbl, _dbl, _dp]),
+    "lbm_destroy": (None, [_vp]),
+    "lbm_set_nsbc": (ctypes.c_int, [_vp, _dbl, _dbl, _dbl, _i32]),
+    "lbm_set_precision": (ctypes.c_int, [_vp, _i32]),
+    "lbm_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "lbm_buffer_bytes": (ctypes.c_size_t, [_vp]),
+    "lbm_scratch_bytes": (ctypes.c_size_t, [_vp]),
+    "lbm_bind": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lbm_init": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lbm_init_device": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lbm_step": (ctypes.c_int, [_vp, _i32]),
+    "lbm_steps_done": (ctypes.c_int64, [_vp]),
+    "lbm_get_macros": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lbm_get_macros_device": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lbm_get_populations": (ctypes.c_int, [_vp, _vp]),
+    "lbm_set_populations": (ctypes.c_int, [_vp, _vp]),
+    "lbm_reduce": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _dp]),
+    "lbm_set_launch": (ctypes.c_int, [_vp, _i32, _i32]),
+    "lbm_autotune": (ctypes.c_int, [_vp, _i32p, _i32p, _dp]),
+    "lbm_profile": (ctypes.c_int, [_vp, _i32]),
+    "lbm_profile_read": (ctypes.c_int, [_vp, _dp]),
+    "lbm_last_error": (ctypes.c_char_p, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_L, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+def lbm_last_error() -> str:
+    return _L.lbm_last_error().decode()
+
+
+def _check(rc: int) -> int:
+    if rc != LBM_OK:
+        raise LbmError(rc, lbm_last_error())
+    return rc
+
+
+def _host(a) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def _hp(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# --- same-name wrappers ------------------------------------------------------
+
+def lbm_create(nx, ny, tau, farfield_rho=1.0, farfield_u=(0.0, 0.0)):
+    u = (ctypes.c_double * 2)(*farfield_u)
+    h = _L.lbm_create(int(nx), int(ny), float(tau), float(farfield_rho), u)
+    if not h:
+        raise LbmError(LBM_EINVAL, lbm_last_error())
+    return ctypes.c_void_p(h)
+
+
+def lbm_destroy(h):
+    _L.lbm_destroy(h)
+
+
+def lbm_set_nsbc(h, gamma=0.6, beta=0.0, kappa=3.0, grad_order=1):
+    return _check(_L.lbm_set_nsbc(h, gamma, beta, kappa, grad_order))
+
+
+def lbm_set_precision(h, storage):
+    return _check(_L.lbm_set_precision(h, STORAGE.get(storage, storage)))
+
+
+def lbm_set_stream(h, stream_handle: int):
+    return _check(_L.lbm_set_stream(h, ctypes.c_void_p(stream_handle)))
+
+
+def lbm_buffer_bytes(h) -> int:
+    return int(_L.lbm_buffer_bytes(h))
+
+
+def lbm_scratch_bytes(h) -> int:
+    return int(_L.lbm_scratch_bytes(h))
+
+
+def lbm_bind(h, dev_a: int, dev_b: int, dev_scratch: int):
+    return _check(_L.lbm_bind(h, ctypes.c_void_p(dev_a), ctypes.c_void_p(dev_b), ctypes.c_void_p(dev_scratch)))
+
+
+def lbm_init(h, rho, ux, uy):
+    """Host fields [ny][nx] (numpy float64)."""
+    rho, ux, uy = _host(rho), _host(ux), _host(uy)
+    return _check(_L.lbm_init(h, _hp(rho), _hp(ux), _hp(uy)))
+
+
+def lbm_init_device(h, d_rho: int, d_ux: int, d_uy: int):
+    return _check(_L.lbm_init_device(h, ctypes.c_void_p(d_rho), ctypes.c_void_p(d_ux), ctypes.c_void_p(d_uy)))
+
+
+def lbm_step(h, n: int):
+    return _check(_L.lbm_step(h, int(n)))
+
+
+def lbm_steps_done(h) -> int:
+    return int(_L.lbm_steps_done(h))
+
+
+def lbm_get_macros(h, rho: np.ndarray, ux: np.ndarray, uy: np.ndarray):
+    for a in (rho, ux, uy):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    return _check(_L.lbm_get_macros(h, _hp(rho), _hp(ux), _hp(uy)))
+
+
+def lbm_get_macros_device(h, d_rho: int, d_ux: int, d_uy: int):
+    return _check(_L.lbm_get_macros_device(h, ctypes.c_void_p(d_rho), ctypes.c_void_p(d_ux),
+                                           ctypes.c_void_p(d_uy)))
+
+
+def lbm_get_populations(h, f: np.ndarray):
+    assert f.dtype == np.float64 and f.flags.c_contiguous
+    return _check(_L.lbm_get_populations(h, _hp(f)))
+
+
+def lbm_set_populations(h, f):
+    f = _host(f)
+    return _check(_L.lbm_set_populations(h, _hp(f)))
+
+
+def lbm_reduce(h, ref_rho: int = 0, ref_ux: int = 0, ref_uy: int = 0, ref_pitch: int = 0,
+               allow_unstable: bool = False):
+    out = (ctypes.c_double * 4)()
+    rc = _L.lbm_reduce(h, ctypes.c_void_p(ref_rho or None), ctypes.c_void_p(ref_ux or None),
+                       ctypes.c_void_p(ref_uy or None), int(ref_pitch), out)
+    if rc == LBM_EUNSTABLE and allow_unstable:
+        return list(out)
+    _check(rc)
+    return list(out)
+
+
+def lbm_set_launch(h, threads_x: int, rows: int):
+    return _check(_L.lbm_set_launch(h, threads_x, rows))
+
+
+def lbm_autotune(h):
+    bx, rows, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(_L.lbm_autotune(h, ctypes.byref(bx), ctypes.byref(rows), ctypes.byref(ms)))
+    return bx.value, rows.value, ms.value
+
+
+def lbm_profile(h, enable: bool):
+    return _check(_L.lbm_profile(h, int(bool(enable))))
+
+
+def lbm_profile_read(h):
+    """(bulk_ms_total, bulk_launches, nsbc_ms_total, nsbc_launches)."""
+    out = (ctypes.c_double * 4)()
+    _check(_L.lbm_profile_read(h, out))
+    return out[0], int(out[1]), out[2], int(out[3])
+
+
+# --- convenience object over torch-owned memory --------------------------------
+
+class Simulation:
+    """One domain on the current CUDA device; torch allocates its memory."""
+
+    def __init__(self, nx, ny, tau, farfield_rho=1.0, farfield_u=(0.0, 0.0), storage="f32",
+                 gamma=0.6, beta=0.0, kappa=3.0, grad_order=1, stream=None):
+        import torch
+        self.nx, self.ny, self.tau = nx, ny, tau
+        self.storage = storage
+        self.h = lbm_create(nx, ny, tau, farfield_rho, farfield_u)
+        try:
+            lbm_set_precision(self.h, storage)
+            lbm_set_nsbc(self.h, gamma, beta, kappa, grad_order)
+            dev = torch.device("cuda", torch.cuda.current_device())
+            self.stream = stream or torch.cuda.current_stream(dev)
+            lbm_set_stream(self.h, self.stream.cuda_stream)
+            bb, sb = lbm_buffer_bytes(self.h), lbm_scratch_bytes(self.h)
+            self._a = torch.empty(bb, dtype=torch.uint8, device=dev)
+            self._b = torch.empty(bb, dtype=torch.uint8, device=dev)
+            self._s = torch.empty(sb, dtype=torch.uint8, device=dev)
+            lbm_bind(self.h, self._a.data_ptr(), self._b.data_ptr(), self._s.data_ptr())
+        except Exception:
+            lbm_destroy(self.h)
+            self.h = None
+            raise
+
+    def close(self):
+        if getattr(self, "h", None):
+            lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_nsbc(self, gamma=0.6, beta=0.0, kappa=3.0, grad_order=1):
+        lbm_set_nsbc(self.h, gamma, beta, kappa, grad_order)
+        return self
+
+    def init(self, rho, ux, uy):
+        lbm_init(self.h, rho, ux, uy)
+        return self
+
+    def init_device(self, rho, ux, uy):
+        """torch float64 CUDA tensors [ny][nx]."""
+        for t in (rho, ux, uy):
+            assert t.is_cuda and t.is_contiguous() and t.dtype.itemsize == 8
+        lbm_init_device(self.h, rho.data_ptr(), ux.data_ptr(), uy.data_ptr())
+        return self
+
+    def step(self, n=1):
+        lbm_step(self.h, n)
+        return self
+
+    @property
+    def steps(self):
+        return lbm_steps_done(self.h)
+
+    def macros(self):
+        rho = np.empty((self.ny, self.nx))
+        ux = np.empty_like(rho)
+        uy = np.empty_like(rho)
+        lbm_get_macros(self.h, rho, ux, uy)
+        return rho, ux, uy
+
+    def macros_device(self, out=None):
+        import torch
+        if out is None:
+            out = torch.empty((3, self.ny, self.nx), dtype=torch.float64, device=self._a.device)
+        lbm_get_macros_device(self.h, out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr())
+        return out
+
+    def populations(self):
+        f = np.empty((9, self.ny, self.nx))
+        lbm_get_populations(self.h, f)
+        return f
+
+    def set_populations(self, f):
+        lbm_set_populations(self.h, f)
+        return self
+
+    def reduce(self, ref=None, ref_pitch=None, allow_unstable=False):
+        """ref: None or a float64 CUDA tensor [3, H, W] whose [:, 0, 0] lines up with node (0, 0)."""
+        if ref is None:
+            return lbm_reduce(self.h, allow_unstable=allow_unstable)
+        pitch = ref_pitch or ref.stride(-2)
+        return lbm_reduce(self.h, ref[0].data_ptr(), ref[1].data_ptr(), ref[2].data_ptr(), pitch,
+                          allow_unstable=allow_unstable)
+
+    def autotune(self):
+        return lbm_autotune(self.h)
+
+    def set_launch(self, threads_x, rows):
+        lbm_set_launch(self.h, threads_x, rows)
+        return self
