@@ -46,7 +46,10 @@ def build(force: bool = False, openmp: bool = False) -> str:
 def lib(openmp: bool = False):
     with _lock:
         if openmp not in _libs:
-            L = ctypes.CDLL(build(openmp=openmp))
+            # a test may point the oracle at a deliberately broken build of the
+            # same source, to show that the pins catch the planted mistake
+            override = os.environ.get("LBM_ORACLE_LIB")
+            L = ctypes.CDLL(override if override else build(openmp=openmp))
             L.or_create.restype = ctypes.c_void_p
             L.or_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_double, ctypes.c_double]

@@ -49,13 +49,18 @@ def max_err(a, b):
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])
-def test_pulse_200_1000_steps(lbm, storage):
+@pytest.mark.parametrize("steps", [250, 1000])
+def test_pulse_200(lbm, storage, steps):
+    """200^2 pulse: at 250 steps the wave is crossing the edges; by 1000 steps the
+    NSBC has let almost all of it out (|rho - 1| ~ 4e-7 is what is left)."""
     w = inputs.pulse_200()
-    ref = oracle_run(w, 1000)
-    got = gpu_run(lbm, w, storage, 1000)
-    assert np.abs(ref[0] - 1).max() > 1e-6  # the pulse is still there
+    ref = oracle_run(w, steps)
+    got = gpu_run(lbm, w, storage, steps)
+    assert np.abs(ref[0] - 1).max() > 1e-7
     err = max_err(got, ref)
     assert err <= TOL[storage], err
+    # relative to the size of the disturbance, too
+    assert err <= 1e-3 * np.abs(ref[0] - 1).max() or storage == "f64", err
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])
