@@ -158,6 +158,28 @@ int lbm_set_launch(lbm_t* h, int32_t threads_x, int32_t rows);
  * milliseconds to the optional outputs. */
 int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, double* ms_per_step);
 
+/* Allocation-free form of lbm_reduce, for callers that cannot allocate
+ * device memory when they need the sums, such as a monitoring hook inside
+ * another framework's step loop where that framework owns all device memory
+ * or where a cudaMalloc/cudaFree would synchronise the device.  The paper has
+ * no counterpart; this is a library service.
+ * Same arguments, results, synchronisation and return codes as lbm_reduce,
+ * and the same kernels, but the partial sums live in a fixed device array
+ * inside the library (131,104 bytes, held by every GPU that loads the
+ * library until the process exits) instead of the handle's scratch area; the
+ * call makes no cudaMalloc, cudaFree or other allocating call.
+ * Limit: at most 67,108,864 nodes (8192 x 8192); larger domains get
+ * LBM_EINVAL with a message saying so (use lbm_reduce).
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress (once per device, with that device current); make
+ * that first call before any stream capture.  All calls on a device share
+ * the array and it keeps the last call's contents (no slot needs to start
+ * at zero: a call reads only what it wrote first); calls that overlap on the
+ * GPU -- other streams, threads or handles on the same device -- race on it
+ * and must be ordered by the caller. */
+int lbm_reduce_noalloc(lbm_t* h, const double* ref_rho, const double* ref_ux, const double* ref_uy,
+                       int32_t ref_pitch, double out[4]);
+
 /* Per-launch timing.  While enabled, lbm_step launches every step directly
  * (no graph) on the handle's stream with CUDA events around the bulk
  * stream-collide kernel and around the NSBC kernel, which then run one after

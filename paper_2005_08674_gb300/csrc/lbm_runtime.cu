@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -605,3 +606,98 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, double* ms_per_ste
 }
 
 }  // extern "C"
+
+// =========================================================================
+// Allocation-free reduction (lbm_reduce_noalloc).
+//
+// Some callers cannot allocate device memory at the moment they want the
+// reduction: a monitoring hook that runs inside another framework's step
+// loop, where that framework owns the device memory (its caching allocator
+// holds it) or where cudaMalloc/cudaFree would synchronise the device and
+// stall the framework's other streams.  For them, lbm_reduce_noalloc runs the
+// same reduction kernels as lbm_reduce but keeps the per-block partial sums
+// and the four results in the fixed array below instead of the handle's
+// scratch area.  It calls no cudaMalloc, cudaFree or allocating routine.
+//
+// The array lives in every GPU that loads this library until the process
+// exits.  Every call on a device shares it and it keeps the last call's
+// contents; nothing in it needs to start at zero, because a call reads only
+// slots that the same call wrote first.  Calls that overlap on the GPU
+// (other streams, other host threads, other handles on the same device) race
+// on it: the caller must order them.
+// =========================================================================
+namespace {
+
+constexpr int kNoAllocThreads = kReduceThreads;
+constexpr int kNoAllocNodesPerThread = 64;                  // grid = nodes / (256 * 64) blocks
+constexpr int kNoAllocMaxBlocks = 4096;                     // -> at most 67,108,864 nodes (8192^2)
+constexpr int kNoAllocDoubles = kNoAllocMaxBlocks * 4 + 4;  // partials + out[4]: 131,104 bytes
+
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device.  In host code
+// the array's name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+int noalloc_scratch(double** out) {
+  int dev = 0;
+  LBM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return fail(LBM_EINVAL, "lbm_reduce_noalloc: device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(LBM_ECUDA, "lbm_reduce_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" int lbm_reduce_noalloc(lbm_t* h, const double* ref_rho, const double* ref_ux, const double* ref_uy,
+                                  int32_t ref_pitch, double out[4]) {
+  if (!h || !out) return fail(LBM_EINVAL, "lbm_reduce_noalloc: NULL argument");
+  const long long n = (long long)h->nx * h->ny;
+  const long long per_block = (long long)kNoAllocThreads * kNoAllocNodesPerThread;
+  const long long blocks = (n + per_block - 1) / per_block;
+  if (blocks > kNoAllocMaxBlocks)
+    return fail(LBM_EINVAL,
+                "lbm_reduce_noalloc: %lld nodes exceed the fixed scratch limit of %lld nodes "
+                "(%d blocks x %d threads x %d nodes); use lbm_reduce",
+                n, (long long)kNoAllocMaxBlocks * per_block, kNoAllocMaxBlocks, kNoAllocThreads,
+                kNoAllocNodesPerThread);
+  if (!h->initialised) return fail(LBM_ESTATE, "lbm_reduce_noalloc: call lbm_init first");
+  if (ref_rho && (!ref_ux || !ref_uy || ref_pitch < h->nx))
+    return fail(LBM_EINVAL, "lbm_reduce_noalloc: reference needs rho, ux, uy and pitch >= nx");
+  if (h->bound) {
+    int dev = -1;
+    LBM_CUDA(cudaGetDevice(&dev));
+    if (dev != h->device) return fail(LBM_EINVAL, "lbm_reduce_noalloc: handle lives on device %d, current is %d",
+                                      h->device, dev);
+  }
+  double* scratch = nullptr;
+  int rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  double* partials = scratch;
+  double* d_out = scratch + kNoAllocMaxBlocks * 4;
+  lbmk::RefField ref{ref_rho, ref_ux, ref_uy, ref_pitch};
+  dispatch(h->storage, [&](auto tag) {
+    using T = decltype(tag);
+    lbmk::reduce_kernel<T, kNoAllocThreads><<<(int)blocks, kNoAllocThreads, 0, h->stream>>>(
+        static_cast<const T*>(h->buf[h->cur]), geom(h), ref, h->nsbc.m0[0], h->nsbc.m0[1], h->nsbc.m0[2], partials);
+  });
+  lbmk::reduce_finish<kNoAllocThreads><<<1, kNoAllocThreads, 0, h->stream>>>(partials, (int)blocks, d_out);
+  rc = check_launch();
+  if (rc) return rc;
+  LBM_CUDA(cudaMemcpyAsync(out, d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  if (out[3] > 0.0)
+    return fail(LBM_EUNSTABLE, "lbm_reduce_noalloc: %.0f nodes with non-finite or non-positive density", out[3]);
+  return LBM_OK;
+}

@@ -55,6 +55,7 @@ _SIGS = {
     "lbm_reduce": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _dp]),
     "lbm_set_launch": (ctypes.c_int, [_vp, _i32, _i32]),
     "lbm_autotune": (ctypes.c_int, [_vp, _i32p, _i32p, _dp]),
+    "lbm_reduce_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _dp]),
     "lbm_profile": (ctypes.c_int, [_vp, _i32]),
     "lbm_profile_read": (ctypes.c_int, [_vp, _dp]),
     "lbm_last_error": (ctypes.c_char_p, []),
@@ -168,6 +169,22 @@ def lbm_reduce(h, ref_rho: int = 0, ref_ux: int = 0, ref_uy: int = 0, ref_pitch:
     out = (ctypes.c_double * 4)()
     rc = _L.lbm_reduce(h, ctypes.c_void_p(ref_rho or None), ctypes.c_void_p(ref_ux or None),
                        ctypes.c_void_p(ref_uy or None), int(ref_pitch), out)
+    if rc == LBM_EUNSTABLE and allow_unstable:
+        return list(out)
+    _check(rc)
+    return list(out)
+
+
+def lbm_reduce_noalloc(h, ref_rho: int = 0, ref_ux: int = 0, ref_uy: int = 0, ref_pitch: int = 0,
+                       allow_unstable: bool = False):
+    """lbm_reduce without any device allocation: for callers that cannot
+    allocate device memory at that point (e.g. a hook inside another
+    framework's step loop that owns the device memory).  Its partial sums use
+    a fixed array inside the library, shared by every call on the device, so
+    calls that overlap on the GPU race; at most 8192^2 nodes."""
+    out = (ctypes.c_double * 4)()
+    rc = _L.lbm_reduce_noalloc(h, ctypes.c_void_p(ref_rho or None), ctypes.c_void_p(ref_ux or None),
+                               ctypes.c_void_p(ref_uy or None), int(ref_pitch), out)
     if rc == LBM_EUNSTABLE and allow_unstable:
         return list(out)
     _check(rc)
