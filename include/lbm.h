@@ -78,6 +78,18 @@ void lbm_destroy(lbm_t* h);
  * Returns LBM_EINVAL for grad_order not in {1, 2} or non-finite values. */
 int lbm_set_nsbc(lbm_t* h, double gamma, double beta, double kappa, int32_t grad_order);
 
+/* Collision model (bulk and boundary nodes alike).  LBM_BGK (default):
+ * Eq. lbe_1 with rate 1/tau.  LBM_MRT: Eq. mrt_lbe with the Gram-Schmidt
+ * moment basis of Sec. 4 and S = diag(-, omega_e, omega_eps, -, omega_q, -,
+ * omega_q, 1/tau, 1/tau) (Eq. mrt_rm; the conserved moments' rates do not
+ * matter, and the stress rate 1/tau keeps nu = cs^2 (tau - 1/2)).  The
+ * paper's tests use omega_e = omega_eps = omega_q = 1.9 (acoustic wave, Sec. 6)
+ * and 1.4, 1.4, 1.2 (vortex, Sec. 7).  The rates are ignored for BGK.
+ * Returns LBM_EINVAL for an unknown model or MRT rates outside (0, 2). */
+#define LBM_BGK 0
+#define LBM_MRT 1
+int lbm_set_collision(lbm_t* h, int32_t model, double omega_e, double omega_eps, double omega_q);
+
 /* Choose the storage type (LBM_F64 / LBM_F32 / LBM_F16 / LBM_BF16).
  * Only allowed before the first lbm_bind / lbm_init* (LBM_ESTATE after). */
 int lbm_set_precision(lbm_t* h, int32_t storage);

@@ -194,6 +194,68 @@ __device__ __forceinline__ void collide_bgk(C (&h)[9], C omega) {
 }
 
 // ---------------------------------------------------------------------------
+// MRT collision, Eq. (mrt_lbe): f* = f - M^-1 S (m - m^eq), with the
+// Gram-Schmidt moment basis of Sec. 4 in the order of Eq. (mrt_rm):
+// (rho, e, eps, jx, qx, jy, qy, pxx, pxy).  Rows scaled to integers:
+//   e   = (-4, -1, -1, -1, -1,  2,  2,  2,  2)   |e|^2   = 36
+//   eps = ( 4, -2, -2, -2, -2,  1,  1,  1,  1)   |eps|^2 = 36
+//   qx  = ( 0, -2,  2,  0,  0,  1, -1, -1,  1)   |qx|^2  = 12
+//   qy  = ( 0,  0,  0, -2,  2,  1, -1,  1, -1)   |qy|^2  = 12
+//   pxx = ( 0,  1,  1, -1, -1,  0,  0,  0,  0)   |pxx|^2 = 4
+//   pxy = ( 0,  0,  0,  0,  0,  1,  1, -1, -1)   |pxy|^2 = 4
+// The rows are orthogonal, so M^-1 = M^T diag(1/|row|^2); a row scale does
+// not change M^-1 S M.  The conserved moments of f - f^eq vanish, so their
+// rates (C_rho, C_jx, C_jy) never enter.  The stress rate is 1/tau.
+// ---------------------------------------------------------------------------
+template <typename C>
+struct Rates {
+  C omega;         // BGK rate 1/tau, also the MRT stress rate omega_nu
+  C s_e, s_eps, s_q;
+};
+
+template <typename C>
+__device__ __forceinline__ void collide_mrt(C (&h)[9], const Rates<C>& r) {
+  C drho, jx, jy;
+  moments(h, drho, jx, jy);
+  const C inv = C(1) / (C(1) + drho);
+  C e[9];
+  equilibrium(drho, jx * inv, jy * inv, e);
+  C n[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) n[i] = h[i] - e[i];
+  const C ax = n[1] + n[2], ay = n[3] + n[4], d = (n[5] + n[6]) + (n[7] + n[8]);
+  const C me = C(-4) * n[0] - (ax + ay) + C(2) * d;
+  const C mep = C(4) * n[0] - C(2) * (ax + ay) + d;
+  const C mqx = C(-2) * (n[1] - n[2]) + ((n[5] - n[6]) + (n[8] - n[7]));
+  const C mqy = C(-2) * (n[3] - n[4]) + ((n[5] - n[6]) + (n[7] - n[8]));
+  const C mxx = ax - ay;
+  const C mxy = (n[5] + n[6]) - (n[7] + n[8]);
+  const C re = r.s_e * me * C(1.0 / 36.0), rep = r.s_eps * mep * C(1.0 / 36.0);
+  const C rqx = r.s_q * mqx * C(1.0 / 12.0), rqy = r.s_q * mqy * C(1.0 / 12.0);
+  const C rxx = r.omega * mxx * C(0.25), rxy = r.omega * mxy * C(0.25);
+  const C a0 = C(-1) * re - C(2) * rep;  // e/eps part of the axis columns
+  const C a1 = C(2) * re + rep;          // e/eps part of the diagonal columns
+  h[0] -= C(4) * (rep - re);
+  h[1] -= a0 - C(2) * rqx + rxx;
+  h[2] -= a0 + C(2) * rqx + rxx;
+  h[3] -= a0 - C(2) * rqy - rxx;
+  h[4] -= a0 + C(2) * rqy - rxx;
+  h[5] -= a1 + rqx + rqy + rxy;
+  h[6] -= a1 - rqx - rqy + rxy;
+  h[7] -= a1 - rqx + rqy - rxy;
+  h[8] -= a1 + rqx - rqy - rxy;
+}
+
+// Collision model: 0 = BGK (Eq. lbe_1), 1 = MRT (Eq. mrt_lbe).
+template <int MODEL, typename C>
+__device__ __forceinline__ void collide(C (&h)[9], const Rates<C>& r) {
+  if constexpr (MODEL == 1)
+    collide_mrt(h, r);
+  else
+    collide_bgk(h, r.omega);
+}
+
+// ---------------------------------------------------------------------------
 // Geometry and NSBC parameters passed by value to the kernels.
 // ---------------------------------------------------------------------------
 struct Geom {

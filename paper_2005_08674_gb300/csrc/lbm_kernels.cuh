@@ -1,7 +1,8 @@
 // lbm_kernels.cuh -- the sm_103a kernels of one D2Q9 + NSBC time step and
 // their helpers (initialisation, macroscopic fields, FP64 reductions).
 //
-//   bulk_kernel  : fused pull-stream (Eq. lbe_0) + BGK collide (Eq. lbe_1)
+//   bulk_kernel  : fused pull-stream (Eq. lbe_0) + collide (BGK, Eq. lbe_1,
+//                  or MRT, Eq. mrt_lbe)
 //                  over interior nodes, 16-byte vector loads/stores along x,
 //                  x-1 / x+1 neighbours exchanged with warp shuffles.
 //   nsbc_kernel  : the boundary of Sec. 5 on every edge and corner node:
@@ -24,9 +25,9 @@ namespace lbmk {
 // segment (V = 16 bytes / sizeof(T)), blocks of BX threads cover BX*V cells
 // of `rows` consecutive rows.  Only nodes 1..nx-2 are stored.
 // ---------------------------------------------------------------------------
-template <typename T, int BX>
+template <typename T, int BX, int MODEL>
 __global__ void __launch_bounds__(BX) bulk_kernel(const T* __restrict__ A, T* __restrict__ B, Geom g,
-                                                  typename Store<T>::C omega, int rows) {
+                                                  Rates<typename Store<T>::C> rates, int rows) {
   using S = Store<T>;
   using C = typename S::C;
   constexpr int V = S::V;
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(BX) bulk_kernel(const T* __restrict__ A, T* __
       h[6] = k == V - 1 ? r6 : v[6][k + 1];
       h[7] = k == V - 1 ? r7 : v[7][k + 1];
       h[8] = k == 0 ? l8 : v[8][k - 1];
-      collide_bgk(h, omega);
+      collide<MODEL>(h, rates);
 #pragma unroll
       for (int i = 0; i < 9; ++i) o[i][k] = h[i];
     }
@@ -117,9 +118,9 @@ __global__ void __launch_bounds__(BX) bulk_kernel(const T* __restrict__ A, T* __
 // and blends m_c in double, then rebuilds, corrects and collides the node in
 // the compute type.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int MODEL>
 __global__ void __launch_bounds__(128) nsbc_kernel(const T* __restrict__ A, T* __restrict__ B, Geom g, Nsbc p,
-                                                   typename Store<T>::C omega) {
+                                                   Rates<typename Store<T>::C> rates) {
   using S = Store<T>;
   using C = typename S::C;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(128) nsbc_kernel(const T* __restrict__ A, T* _
 #pragma unroll
   for (int i = 0; i < 9; ++i) h[i] -= wt<C>(i) * (d_rho + kap * (C(cx(i)) * d_jx + C(cy(i)) * d_jy));
 
-  collide_bgk(h, omega);
+  collide<MODEL>(h, rates);
   const long long o = (long long)y * g.pitch + x;
 #pragma unroll
   for (int i = 0; i < 9; ++i) S::st1(B + i * g.plane + o, h[i]);

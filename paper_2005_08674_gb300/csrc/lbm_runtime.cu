@@ -69,6 +69,8 @@ struct lbm {
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by starting buffer
   int bx = 128, rows = 1;
   int device = 0;
+  int collision = 0;                          // 0 = BGK, 1 = MRT
+  double s_e = 1.0, s_eps = 1.0, s_q = 1.0;   // MRT energy, energy-square and flux rates
   // per-launch timing (lbm_profile): event pairs around every bulk and NSBC launch
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -129,14 +131,23 @@ int grid_for(long long n, int threads) {
 
 // ---- typed launchers ------------------------------------------------------
 
+template <typename C>
+lbmk::Rates<C> rates(const lbm_t* h) {
+  return lbmk::Rates<C>{C(1.0 / h->tau), C(h->s_e), C(h->s_eps), C(h->s_q)};
+}
+
 template <typename T, int BX>
 void launch_bulk_bx(const lbm_t* h, const void* a, void* b, int rows, cudaStream_t s) {
   using C = typename lbmk::Store<T>::C;
   constexpr int V = lbmk::Store<T>::V;
   const int nvec = (h->nx + V - 1) / V;
   dim3 grid((nvec + BX - 1) / BX, (h->ny - 2 + rows - 1) / rows);
-  lbmk::bulk_kernel<T, BX><<<grid, BX, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
-                                              C(1.0 / h->tau), rows);
+  if (h->collision == 1)
+    lbmk::bulk_kernel<T, BX, 1><<<grid, BX, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
+                                                   rates<C>(h), rows);
+  else
+    lbmk::bulk_kernel<T, BX, 0><<<grid, BX, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
+                                                   rates<C>(h), rows);
 }
 
 template <typename T>
@@ -154,8 +165,12 @@ void launch_nsbc(const lbm_t* h, const void* a, void* b, cudaStream_t s) {
   using C = typename lbmk::Store<T>::C;
   const long long perim = 2LL * h->nx + 2LL * (h->ny - 2);
   const int blocks = (int)((perim * 4 + kNsbcThreads - 1) / kNsbcThreads);
-  lbmk::nsbc_kernel<T><<<blocks, kNsbcThreads, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
-                                                       h->nsbc, C(1.0 / h->tau));
+  if (h->collision == 1)
+    lbmk::nsbc_kernel<T, 1><<<blocks, kNsbcThreads, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
+                                                            h->nsbc, rates<C>(h));
+  else
+    lbmk::nsbc_kernel<T, 0><<<blocks, kNsbcThreads, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
+                                                            h->nsbc, rates<C>(h));
 }
 
 template <typename F>
@@ -311,6 +326,23 @@ int lbm_set_nsbc(lbm_t* h, double gamma, double beta, double kappa, int32_t grad
   h->nsbc.beta = beta;
   h->nsbc.kappa = kappa;
   h->nsbc.order = grad_order;
+  drop_graphs(h);
+  return LBM_OK;
+}
+
+int lbm_set_collision(lbm_t* h, int32_t model, double omega_e, double omega_eps, double omega_q) {
+  if (!h) return fail(LBM_EINVAL, "lbm_set_collision: NULL handle");
+  if (model != LBM_BGK && model != LBM_MRT) return fail(LBM_EINVAL, "lbm_set_collision: unknown model %d", model);
+  if (model == LBM_MRT)
+    for (double r : {omega_e, omega_eps, omega_q})
+      if (!std::isfinite(r) || !(r > 0.0) || !(r < 2.0))
+        return fail(LBM_EINVAL, "lbm_set_collision: MRT rates must lie in (0, 2)");
+  h->collision = model;
+  if (model == LBM_MRT) {
+    h->s_e = omega_e;
+    h->s_eps = omega_eps;
+    h->s_q = omega_q;
+  }
   drop_graphs(h);
   return LBM_OK;
 }

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "liblbm.so")
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE = 0, -1, -2, -3, -4, -5
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2, 3
+LBM_BGK, LBM_MRT = 0, 1
 STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16, "bf16": LBM_BF16}
 
 
@@ -40,6 +41,7 @@ _SIGS = {
     "lbm_destroy": (None, [_vp]),
     "lbm_set_nsbc": (ctypes.c_int, [_vp, _dbl, _dbl, _dbl, _i32]),
     "lbm_set_precision": (ctypes.c_int, [_vp, _i32]),
+    "lbm_set_collision": (ctypes.c_int, [_vp, _i32, _dbl, _dbl, _dbl]),
     "lbm_set_stream": (ctypes.c_int, [_vp, _vp]),
     "lbm_buffer_bytes": (ctypes.c_size_t, [_vp]),
     "lbm_scratch_bytes": (ctypes.c_size_t, [_vp]),
@@ -107,6 +109,11 @@ def lbm_set_nsbc(h, gamma=0.6, beta=0.0, kappa=3.0, grad_order=1):
 
 def lbm_set_precision(h, storage):
     return _check(_L.lbm_set_precision(h, STORAGE.get(storage, storage)))
+
+
+def lbm_set_collision(h, model, omega_e=1.0, omega_eps=1.0, omega_q=1.0):
+    m = {"bgk": LBM_BGK, "mrt": LBM_MRT}.get(model, model)
+    return _check(_L.lbm_set_collision(h, m, omega_e, omega_eps, omega_q))
 
 
 def lbm_set_stream(h, stream_handle: int):
@@ -218,7 +225,8 @@ class Simulation:
     """One domain on the current CUDA device; torch allocates its memory."""
 
     def __init__(self, nx, ny, tau, farfield_rho=1.0, farfield_u=(0.0, 0.0), storage="f32",
-                 gamma=0.6, beta=0.0, kappa=3.0, grad_order=1, stream=None):
+                 gamma=0.6, beta=0.0, kappa=3.0, grad_order=1, stream=None, collision="bgk",
+                 mrt_rates=(1.0, 1.0, 1.0)):
         import torch
         self.nx, self.ny, self.tau = nx, ny, tau
         self.storage = storage
@@ -226,6 +234,7 @@ class Simulation:
         try:
             lbm_set_precision(self.h, storage)
             lbm_set_nsbc(self.h, gamma, beta, kappa, grad_order)
+            lbm_set_collision(self.h, collision, *mrt_rates)
             dev = torch.device("cuda", torch.cuda.current_device())
             self.stream = stream or torch.cuda.current_stream(dev)
             lbm_set_stream(self.h, self.stream.cuda_stream)

@@ -1,0 +1,81 @@
+"""16-bit shifted storage (f16, bf16) against the FP64 oracle.
+
+Workload: the 8192^2 pulse recipe at 1024^2 (four pulses A = 1e-3, half-width
+64, centres in [256, 768]^2, tau 0.55), 2000 steps.  Bars: density error
+<= 1e-4 and a change of the reflection coefficient R_max of at most 1 %
+relative to the oracle's.  R(t) = E[run(t), ref(t)] / E[ref(0), m0] with E the
+acoustic energy of the difference and ref an oracle run on the domain padded
+by P nodes of far field on every side, so that nothing comes back from its
+edge within the run; R_max over samples every 20 steps.  The f32 path is
+measured the same way.  If LBM_RESULTS_DIR is set, the figures are written
+there as JSON.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import reflection as R
+from paper_2005_08674_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+STEPS, EVERY = 2000, 20
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    from paper_2005_08674_gb300 import build
+    build.build()
+    from paper_2005_08674_gb300 import lbm as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def reference():
+    """Oracle on the test domain and on the padded domain: fields every EVERY steps."""
+    w = inputs.pulse_1024()
+    f0 = w.fields()
+    P = R.padding_for(STEPS)
+    big = oracle.Oracle(w.nx + 2 * P, w.ny + 2 * P, w.tau, openmp=True).init(*R.embed(f0, P, (1.0, 0.0, 0.0)))
+    test = oracle.Oracle(w.nx, w.ny, w.tau, openmp=True).init(*f0)
+    z = np.zeros_like(f0[0])
+    e0 = R.energy(*f0, np.ones_like(z), z, z)
+    refs, rs = [], []
+    for _ in range(STEPS // EVERY):
+        big.step(EVERY)
+        test.step(EVERY)
+        ref = R.window(big.macros(), P, w.nx, w.ny)
+        refs.append(ref)
+        rs.append(R.energy(*test.macros(), *ref) / e0)
+    final = test.macros()
+    return dict(w=w, f0=f0, refs=refs, e0=e0, r_max=max(rs), final=final)
+
+
+@pytest.mark.parametrize("storage,rho_tol", [("f16", 1e-4), ("bf16", 1e-4), ("f32", 1e-6)])
+def test_storage_error_and_reflection(lbm, reference, storage, rho_tol):
+    w = reference["w"]
+    sim = lbm.Simulation(w.nx, w.ny, w.tau, storage=storage).init(*reference["f0"])
+    rs = []
+    for ref in reference["refs"]:
+        sim.step(EVERY)
+        rs.append(R.energy(*sim.macros(), *ref) / reference["e0"])
+    got = sim.macros()
+    sim.close()
+    ref_final = reference["final"]
+    d_rho = float(np.abs(got[0] - ref_final[0]).max())
+    d_u = float(max(np.abs(got[1] - ref_final[1]).max(), np.abs(got[2] - ref_final[2]).max()))
+    r_max = max(rs)
+    change = abs(r_max - reference["r_max"]) / reference["r_max"]
+    res = dict(storage=storage, workload="pulse-1024, 2000 steps", max_abs_drho=d_rho, max_abs_du=d_u,
+               r_max=r_max, r_max_oracle=reference["r_max"], r_change=change)
+    out = os.environ.get("LBM_RESULTS_DIR")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, f"mixed_{storage}.json"), "w") as f:
+            json.dump(res, f)
+    print(res)
+    assert d_rho <= rho_tol, res
+    assert change <= 0.01, res

@@ -29,8 +29,8 @@ def lbm():
     return m
 
 
-def gpu_run(lbm, w, storage, steps, fields=None, **nsbc):
-    sim = lbm.Simulation(w.nx, w.ny, w.tau, w.farfield_rho, w.farfield_u, storage=storage, **nsbc)
+def gpu_run(lbm, w, storage, steps, fields=None, **kw):
+    sim = lbm.Simulation(w.nx, w.ny, w.tau, w.farfield_rho, w.farfield_u, storage=storage, **kw)
     sim.init(*(fields or w.fields()))
     sim.step(steps)
     out = sim.macros()
@@ -38,8 +38,8 @@ def gpu_run(lbm, w, storage, steps, fields=None, **nsbc):
     return out
 
 
-def oracle_run(w, steps, fields=None, **nsbc):
-    o = oracle.Oracle(w.nx, w.ny, w.tau, w.farfield_rho, w.farfield_u, openmp=True, **nsbc)
+def oracle_run(w, steps, fields=None, **kw):
+    o = oracle.Oracle(w.nx, w.ny, w.tau, w.farfield_rho, w.farfield_u, openmp=True, **kw)
     o.init(*(fields or w.fields()))
     return o.step(steps).macros()
 
@@ -178,3 +178,53 @@ def test_full_size_8192_sampled(lbm, storage):
     del mac
     torch.cuda.empty_cache()
     assert worst <= TOL[storage], worst
+
+
+PAPER_VORTEX_RATES = (1.4, 1.4, 1.2)  # omega_e, omega_eps, omega_q of the vortex test (Sec. 7)
+PAPER_WAVE_RATES = (1.9, 1.9, 1.9)    # of the acoustic test (Sec. 6)
+
+
+def _oracle_mrt_rates(rates, tau):
+    e, eps, q = rates
+    return [1.0, e, eps, 1.0, q, 1.0, q, 1.0 / tau, 1.0 / tau]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("rates", [PAPER_VORTEX_RATES, PAPER_WAVE_RATES])
+def test_mrt_vortex_in_stream(lbm, storage, rates):
+    u0 = 0.1 * inputs.CS
+    w = inputs.Workload("vortex-160", 160, 120, 0.52, 300, farfield_u=(u0, 0.0), kind="vortex",
+                        params=dict(u0=u0, beta_u0=0.5 * u0, rc=10.0, x0=110.0, y0=60.0))
+    ref = oracle_run(w, 300, beta=0.05, collision="mrt", mrt_rates=_oracle_mrt_rates(rates, w.tau))
+    got = gpu_run(lbm, w, storage, 300, beta=0.05, collision="mrt", mrt_rates=rates)
+    err = max_err(got, ref)
+    assert err <= TOL[storage] * (10 if storage == "f32" else 1), err
+
+
+def test_vortex_400_mrt_4000_steps(lbm):
+    """The 400^2 convected vortex (tau 0.505, Ma 0.1) over 4000 steps.  With BGK
+    the NSBC run goes unstable near the outflow corners after ~1000 steps (see
+    the next test); with the paper's MRT rates it stays bounded, and the FP32
+    path follows the oracle."""
+    w = inputs.vortex_400()
+    rates = PAPER_VORTEX_RATES
+    ref = oracle_run(w, 4000, collision="mrt", mrt_rates=_oracle_mrt_rates(rates, w.tau))
+    assert all(np.isfinite(a).all() for a in ref)
+    got = gpu_run(lbm, w, "f32", 4000, collision="mrt", mrt_rates=rates)
+    err = max_err(got, ref)
+    assert err <= 1e-5, err
+
+
+def test_instability_is_reported_not_faulted(lbm):
+    """BGK at tau 0.505 with the vortex blows up (the oracle shows the same);
+    NaNs do not fault the GPU and lbm_reduce reports LBM_EUNSTABLE."""
+    w = inputs.vortex_400()
+    sim = lbm.Simulation(w.nx, w.ny, w.tau, w.farfield_rho, w.farfield_u, storage="f32")
+    sim.init(*w.fields())
+    sim.step(2000)
+    with pytest.raises(lbm.LbmError) as e:
+        sim.reduce()
+    assert e.value.code == lbm.LBM_EUNSTABLE
+    out = sim.reduce(allow_unstable=True)
+    assert out[3] > 0
+    sim.close()
