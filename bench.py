@@ -226,10 +226,11 @@ def run_ours(args, rank, world, local_rank):
     sim = lbm.Simulation(w.nx, w.ny, w.tau, w.farfield_rho, w.farfield_u, storage=args.storage)
     sim.init(*fields)
     if args.launch:
-        bx, rows = (int(v) for v in args.launch.split(","))
-        sim.set_launch(bx, rows)
+        parts = [int(v) for v in args.launch.split(",")]
+        bx, rows, pf = (parts + [0])[:3]
+        sim.set_launch(bx, rows, pf)
     else:
-        bx, rows, _ = sim.autotune()
+        bx, rows, pf, _ = sim.autotune()
     stream = sim.stream
 
     def barrier():
@@ -282,7 +283,7 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
             "config": {"workload": describe(w, args.storage), "nx": w.nx, "ny": w.ny,
-                       "bulk_launch": {"threads_x": bx, "rows": rows},
+                       "bulk_launch": {"threads_x": bx, "rows": rows, "prefetch_rows": pf},
                        "l2": f"inputs larger than L2: {lbm.lbm_buffer_bytes(sim.h) / 1e9:.2f} GB per population buffer",
                        "parallelism": "replicas" if world > 1 else "single-gpu",
                        "stable": bool(stable)},
@@ -336,7 +337,7 @@ def run_ours(args, rank, world, local_rank):
                 continue
             s2 = lbm.Simulation(w.nx, w.ny, w.tau, w.farfield_rho, w.farfield_u, storage=st)
             s2.init(*fields)
-            vb, vr, _ = s2.autotune()
+            vb, vr, vp, _ = s2.autotune()
             s2.step(args.warmup)
             torch.cuda.synchronize()
             a0 = torch.cuda.Event(enable_timing=True)
@@ -352,7 +353,7 @@ def run_ours(args, rank, world, local_rank):
             bavg = bms / max(bn, 1)
             gbs = BYTES_PER_CELL[st] * interior / (bavg * 1e-3) / 1e9
             variants[st] = {"mlups": world * cells * vsteps / (vms * 1e-3) / 1e6, "steps": vsteps,
-                            "bulk_gbs": gbs, "bulk_frac": gbs / peak, "bulk_launch": [vb, vr]}
+                            "bulk_gbs": gbs, "bulk_frac": gbs / peak, "bulk_launch": [vb, vr, vp]}
             s2.close()
             del s2
             torch.cuda.empty_cache()

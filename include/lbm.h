@@ -160,15 +160,19 @@ int lbm_reduce(lbm_t* h, const double* ref_rho, const double* ref_ux, const doub
                int32_t ref_pitch, double out[4]);
 
 /* Launch shape of the bulk stream-collide kernel: threads per block along x
- * and rows per block.  0, 0 restores the built-in choice.  Returns
- * LBM_EINVAL for shapes the kernel was not compiled for. */
-int lbm_set_launch(lbm_t* h, int32_t threads_x, int32_t rows);
+ * (64, 128, 256, 512), rows per block (1, 2, 4, 8), and the distance in rows
+ * (0 = off, at most 64) at which each warp asks the bulk-copy engine to
+ * prefetch its next segments into L2.  threads_x = rows = 0 restores the
+ * built-in shape.  Returns LBM_EINVAL for shapes the kernel was not compiled
+ * for. */
+int lbm_set_launch(lbm_t* h, int32_t threads_x, int32_t rows, int32_t prefetch_rows);
 
-/* Time every compiled bulk launch shape on this handle's own buffers (a few
- * steps each, CUDA events on the stream) and keep the fastest; the state is
- * restored afterwards.  Writes the chosen shape and its time per step in
+/* Time every compiled bulk launch shape and prefetch distance on this
+ * handle's own buffers (a few steps each, CUDA events on the stream) and keep
+ * the fastest; the state is restored afterwards (through a temporary device
+ * copy from cudaMallocAsync).  Writes the choice and its time per step in
  * milliseconds to the optional outputs. */
-int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, double* ms_per_step);
+int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_rows, double* ms_per_step);
 
 /* Allocation-free form of lbm_reduce, for callers that cannot allocate
  * device memory when they need the sums, such as a monitoring hook inside
@@ -191,6 +195,57 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, double* ms_per_ste
  * and must be ordered by the caller. */
 int lbm_reduce_noalloc(lbm_t* h, const double* ref_rho, const double* ref_ux, const double* ref_uy,
                        int32_t ref_pitch, double out[4]);
+
+/* ------------------------------------------------------------------------
+ * Batched mode: many independent simulations of uneven sizes, each with its
+ * own tau and far field, stepped together by ONE persistent kernel launch
+ * per step (bulk tiles and NSBC chunks of all instances in one work list),
+ * replayed from a CUDA graph.  Storage, collision model and NSBC parameters
+ * are shared by the batch.  Results per instance are bit-identical to a
+ * single-domain handle with the same settings.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_batch lbm_batch_t;
+
+typedef struct lbm_instance_desc {
+  int32_t nx, ny; /* nodes, each in [3, 65536] */
+  double tau;     /* > 0.5 */
+  double farfield_rho, farfield_ux, farfield_uy;
+} lbm_instance_desc;
+
+/* Host-only: validates the descriptors and lays out the pools; NULL on bad
+ * arguments (message in lbm_last_error()). */
+lbm_batch_t* lbm_batch_create(int32_t count, const lbm_instance_desc* descs, int32_t storage);
+/* Frees library-owned device memory; synchronises the stream.  NULL-safe. */
+void lbm_batch_destroy(lbm_batch_t* b);
+int lbm_batch_set_nsbc(lbm_batch_t* b, double gamma, double beta, double kappa, int32_t grad_order);
+int lbm_batch_set_collision(lbm_batch_t* b, int32_t model, double omega_e, double omega_eps, double omega_q);
+int lbm_batch_set_stream(lbm_batch_t* b, void* cuda_stream);
+/* Total nodes over all instances. */
+int64_t lbm_batch_cells(const lbm_batch_t* b);
+/* Bytes of ONE population pool (all instances), and of the scratch area
+ * (three [ny][nx] double fields of the largest instance + reduction slots). */
+size_t lbm_batch_buffer_bytes(const lbm_batch_t* b);
+size_t lbm_batch_scratch_bytes(const lbm_batch_t* b);
+/* Caller-owned device memory (256-byte aligned), before the first init;
+ * otherwise the library allocates on first init. */
+int lbm_batch_bind(lbm_batch_t* b, void* dev_a, void* dev_b, void* dev_scratch);
+/* Instance k at equilibrium from HOST fields [ny_k][nx_k] double; synchronises. */
+int lbm_batch_init(lbm_batch_t* b, int32_t k, const double* rho, const double* ux, const double* uy);
+/* n steps of every instance (all must be initialised); asynchronous. */
+int lbm_batch_step(lbm_batch_t* b, int32_t n);
+int64_t lbm_batch_steps_done(const lbm_batch_t* b);
+/* Macros of instance k into HOST arrays [ny_k][nx_k] double; synchronises. */
+int lbm_batch_get_macros(lbm_batch_t* b, int32_t k, double* rho, double* ux, double* uy);
+/* Number of nodes of instance k with non-finite or non-positive density
+ * (FP64 reduction); synchronises. */
+int lbm_batch_unstable_nodes(lbm_batch_t* b, int32_t k, int64_t* count);
+/* Tile shape: threads per block along x (64, 128, 256) times the storage's
+ * 16-byte vector of nodes per thread, `rows` rows per tile (nodes per thread
+ * = vector x rows), and the persistent grid size (0 = one resident wave). */
+int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_t blocks);
+/* Time every compiled tile shape and grid size on the batch's own state
+ * (restored afterwards) and keep the fastest. */
+int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_t* blocks, double* ms_per_step);
 
 /* Per-launch timing.  While enabled, lbm_step launches every step directly
  * (no graph) on the handle's stream with CUDA events around the bulk

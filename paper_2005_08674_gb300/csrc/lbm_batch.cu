@@ -1,0 +1,567 @@
+// lbm_batch.cu -- many independent D2Q9 + NSBC simulations of uneven sizes
+// advanced by ONE persistent launch per step.
+//
+// Every instance keeps its own 9-plane layout (pitch = nx rounded up to 64,
+// planes 256-byte aligned) inside two shared pools A and B.  A work list of
+// int4 items drives the persistent kernel: bulk tiles (instance, first row,
+// first x, rows) of threads_x * V nodes by `rows` rows, then NSBC chunks
+// (~instance, first perimeter node, count) of threads_x / 4 nodes.  Blocks
+// take items round-robin; bulk tiles and NSBC chunks of one step read only
+// pool A and write disjoint nodes of pool B, so no synchronisation is needed
+// inside the launch.  Each item runs the same device code as the single-domain
+// kernels (bulk_row, nsbc_node), so an instance's results are bit-identical
+// to a single-domain run with the same storage and collision model.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_kernels.cuh"
+
+int lbm_internal_fail(int code, const char* msg);
+
+namespace {
+
+int bfail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int bfail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  return lbm_internal_fail(code, buf);
+}
+
+#define BATCH_CUDA(call)                                                                               \
+  do {                                                                                                 \
+    cudaError_t e_ = (call);                                                                           \
+    if (e_ != cudaSuccess)                                                                             \
+      return bfail(e_ == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA, "%s: %s (%s:%d)", #call, \
+                   cudaGetErrorString(e_), __FILE__, __LINE__);                                        \
+  } while (0)
+
+constexpr int kBatchGraphSteps = 16;
+constexpr int kBatchBX[] = {64, 128, 256};
+constexpr int kBatchRows[] = {1, 2, 4};
+
+struct InstDev {
+  long long off;    // element offset of the instance's planes in each pool
+  long long plane;  // elements per plane
+  int nx, ny, pitch, pad;
+  double omega;     // 1 / tau
+  double m0[3];     // far field (rho, ux, uy)
+};
+
+size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+}  // namespace
+
+struct lbm_batch {
+  int count = 0;
+  int storage = LBM_F32;
+  size_t elt = 4;
+  std::vector<InstDev> inst;
+  std::vector<double> tau;
+  long long pool_elems = 0;
+  long long cells = 0;
+  size_t max_cells = 0;
+  lbmk::Nsbc nsbc{};
+  int collision = 0;
+  double s_e = 1.0, s_eps = 1.0, s_q = 1.0;
+  void* pool[2] = {nullptr, nullptr};
+  void* scratch = nullptr;  // 3 fields of the largest instance (double)
+  bool owns_pools = false, bound = false;
+  InstDev* d_inst = nullptr;
+  int4* d_items = nullptr;
+  int n_items = 0, n_bulk_items = 0;
+  int bx = 128, rows = 1, blocks = 0;  // blocks = 0: one wave of resident blocks
+  int wave = 1;                        // resident blocks on the device for the current shape
+  bool items_dirty = true;
+  std::vector<char> initialised;
+  int cur = 0;
+  long long steps = 0;
+  cudaStream_t stream = nullptr, cap = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int device = 0;
+};
+
+namespace {
+
+template <typename F>
+void bdispatch(int storage, F&& f) {
+  switch (storage) {
+    case LBM_F64: f(double{}); break;
+    case LBM_F16: f(__half{}); break;
+    case LBM_BF16: f(__nv_bfloat16{}); break;
+    default: f(float{}); break;
+  }
+}
+
+template <typename T, int BX, int MODEL>
+__global__ void __launch_bounds__(BX) batch_step_kernel(const T* __restrict__ A, T* __restrict__ B,
+                                                        const InstDev* __restrict__ inst,
+                                                        const int4* __restrict__ items, int n_items, lbmk::Nsbc p,
+                                                        double s_e, double s_eps, double s_q) {
+  using C = typename lbmk::Store<T>::C;
+  constexpr int V = lbmk::Store<T>::V;
+  const int lane = threadIdx.x & 31;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int4 w = items[it];
+    const bool edge = w.x < 0;
+    const InstDev d = inst[edge ? ~w.x : w.x];
+    const lbmk::Geom g{d.nx, d.ny, d.pitch, d.plane};
+    const lbmk::Rates<C> r{C(d.omega), C(s_e), C(s_eps), C(s_q)};
+    const T* a = A + d.off;
+    T* b = B + d.off;
+    if (!edge) {
+      const int x0 = w.z + (int)threadIdx.x * V;
+      const unsigned pfb = lbmk::warp_segment_bytes<T>(g, x0 - lane * V);
+      for (int y = w.y; y < w.y + w.w; ++y) lbmk::bulk_row<T, MODEL>(a, b, g, r, y, x0, lane, 0, pfb);
+    } else {
+      lbmk::Nsbc q = p;
+      q.m0[0] = d.m0[0];
+      q.m0[1] = d.m0[1];
+      q.m0[2] = d.m0[2];
+      const int node = w.y + ((int)threadIdx.x >> 2);
+      if (node < w.y + w.z) lbmk::nsbc_node<T, MODEL>(a, b, g, q, r, node, (int)threadIdx.x & 3);
+    }
+  }
+}
+
+template <typename T, int BX>
+const void* kernel_ptr(int model) {
+  return model == 1 ? (const void*)batch_step_kernel<T, BX, 1> : (const void*)batch_step_kernel<T, BX, 0>;
+}
+
+template <typename T, int BX>
+void launch_batch_bx(const lbm_batch_t* b, int from, cudaStream_t s, int grid) {
+  const T* A = static_cast<const T*>(b->pool[from]);
+  T* B = static_cast<T*>(b->pool[1 - from]);
+  if (b->collision == 1)
+    batch_step_kernel<T, BX, 1><<<grid, BX, 0, s>>>(A, B, b->d_inst, b->d_items, b->n_items, b->nsbc, b->s_e,
+                                                    b->s_eps, b->s_q);
+  else
+    batch_step_kernel<T, BX, 0><<<grid, BX, 0, s>>>(A, B, b->d_inst, b->d_items, b->n_items, b->nsbc, b->s_e,
+                                                    b->s_eps, b->s_q);
+}
+
+// resident blocks per SM for the current shape
+int wave_blocks(const lbm_batch_t* b) {
+  int per_sm = 0, sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  bdispatch(b->storage, [&](auto tag) {
+    using T = decltype(tag);
+    const void* k = b->bx == 64 ? kernel_ptr<T, 64>(b->collision)
+                                : (b->bx == 256 ? kernel_ptr<T, 256>(b->collision) : kernel_ptr<T, 128>(b->collision));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, b->bx, 0);
+  });
+  return std::max(1, per_sm) * std::max(1, sms);
+}
+
+void enqueue_batch_step(const lbm_batch_t* b, int from, cudaStream_t s) {
+  const int grid = std::max(1, std::min(b->n_items, b->blocks > 0 ? b->blocks : b->wave));
+  bdispatch(b->storage, [&](auto tag) {
+    using T = decltype(tag);
+    switch (b->bx) {
+      case 64: launch_batch_bx<T, 64>(b, from, s, grid); break;
+      case 256: launch_batch_bx<T, 256>(b, from, s, grid); break;
+      default: launch_batch_bx<T, 128>(b, from, s, grid); break;
+    }
+  });
+}
+
+void drop_batch_graphs(lbm_batch_t* b) {
+  for (auto& g : b->graph)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+// Work list for the current shape: bulk tiles (largest instances first),
+// then NSBC chunks.
+int build_items(lbm_batch_t* b) {
+  if (!b->items_dirty) return LBM_OK;
+  const int V = (int)(16 / b->elt);
+  std::vector<int> order(b->count);
+  for (int k = 0; k < b->count; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int i, int j) {
+    return (long long)b->inst[i].nx * b->inst[i].ny > (long long)b->inst[j].nx * b->inst[j].ny;
+  });
+  std::vector<int4> items;
+  for (int k : order) {
+    const InstDev& d = b->inst[k];
+    const int tile_x = b->bx * V;
+    for (int y0 = 1; y0 <= d.ny - 2; y0 += b->rows)
+      for (int x0 = 0; x0 < d.nx; x0 += tile_x) items.push_back(make_int4(k, y0, x0, std::min(b->rows, d.ny - 1 - y0)));
+  }
+  const int n_bulk = (int)items.size();
+  const int chunk = b->bx / 4;
+  for (int k : order) {
+    const InstDev& d = b->inst[k];
+    const int perim = 2 * d.nx + 2 * (d.ny - 2);
+    for (int n0 = 0; n0 < perim; n0 += chunk) items.push_back(make_int4(~k, n0, std::min(chunk, perim - n0), 0));
+  }
+  if (b->d_items) cudaFree(b->d_items);
+  b->d_items = nullptr;
+  BATCH_CUDA(cudaMalloc(&b->d_items, items.size() * sizeof(int4)));
+  BATCH_CUDA(cudaMemcpy(b->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  b->n_items = (int)items.size();
+  b->n_bulk_items = n_bulk;
+  b->wave = wave_blocks(b);
+  b->items_dirty = false;
+  drop_batch_graphs(b);
+  return LBM_OK;
+}
+
+int ensure_batch_memory(lbm_batch_t* b) {
+  if (!b->bound) {
+    const size_t pb = lbm_batch_buffer_bytes(b);
+    BATCH_CUDA(cudaGetDevice(&b->device));
+    BATCH_CUDA(cudaMalloc(&b->pool[0], pb));
+    BATCH_CUDA(cudaMalloc(&b->pool[1], pb));
+    BATCH_CUDA(cudaMalloc(&b->scratch, lbm_batch_scratch_bytes(b)));
+    BATCH_CUDA(cudaMemset(b->pool[0], 0, pb));
+    BATCH_CUDA(cudaMemset(b->pool[1], 0, pb));
+    b->owns_pools = true;
+    b->bound = true;
+  }
+  if (!b->d_inst) {
+    BATCH_CUDA(cudaMalloc(&b->d_inst, b->inst.size() * sizeof(InstDev)));
+    BATCH_CUDA(cudaMemcpy(b->d_inst, b->inst.data(), b->inst.size() * sizeof(InstDev), cudaMemcpyHostToDevice));
+  }
+  return LBM_OK;
+}
+
+int batch_check_launch() {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return bfail(LBM_ECUDA, "batched kernel launch failed: %s", cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+lbmk::Geom inst_geom(const InstDev& d) { return lbmk::Geom{d.nx, d.ny, d.pitch, d.plane}; }
+
+double* bscratch(lbm_batch_t* b, int c) {
+  return reinterpret_cast<double*>(static_cast<char*>(b->scratch) + c * round_up(b->max_cells * sizeof(double), 256));
+}
+
+bool batch_shape_ok(int bx, int rows) {
+  bool a = false, r = false;
+  for (int v : kBatchBX) a |= v == bx;
+  for (int v : kBatchRows) r |= v == rows;
+  return a && r;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_batch_t* lbm_batch_create(int32_t count, const lbm_instance_desc* descs, int32_t storage) {
+  if (count < 1 || !descs) {
+    bfail(LBM_EINVAL, "lbm_batch_create: need count >= 1 and descriptors");
+    return nullptr;
+  }
+  if (storage < LBM_F64 || storage > LBM_BF16) {
+    bfail(LBM_EINVAL, "lbm_batch_create: unknown storage %d", storage);
+    return nullptr;
+  }
+  lbm_batch_t* b = new lbm_batch_t();
+  b->count = count;
+  b->storage = storage;
+  b->elt = storage == LBM_F64 ? 8 : (storage == LBM_F32 ? 4 : 2);
+  b->nsbc.gamma = 0.6;
+  b->nsbc.beta = 0.0;
+  b->nsbc.kappa = 3.0;
+  b->nsbc.order = 1;
+  long long off = 0;
+  for (int k = 0; k < count; ++k) {
+    const lbm_instance_desc& s = descs[k];
+    if (s.nx < 3 || s.ny < 3 || s.nx > 65536 || s.ny > 65536 || !std::isfinite(s.tau) || !(s.tau > 0.5) ||
+        !(s.farfield_rho > 0.0) || !std::isfinite(s.farfield_ux) || !std::isfinite(s.farfield_uy)) {
+      bfail(LBM_EINVAL, "lbm_batch_create: instance %d invalid (nx=%d ny=%d tau=%g)", k, s.nx, s.ny, s.tau);
+      delete b;
+      return nullptr;
+    }
+    InstDev d{};
+    d.nx = s.nx;
+    d.ny = s.ny;
+    d.pitch = (int)round_up((size_t)s.nx, 64);
+    d.plane = (long long)(round_up((size_t)s.ny * d.pitch * b->elt, 256) / b->elt);
+    d.off = off;
+    d.omega = 1.0 / s.tau;
+    d.m0[0] = s.farfield_rho;
+    d.m0[1] = s.farfield_ux;
+    d.m0[2] = s.farfield_uy;
+    off += 9 * d.plane;
+    b->inst.push_back(d);
+    b->tau.push_back(s.tau);
+    b->cells += (long long)s.nx * s.ny;
+    b->max_cells = std::max(b->max_cells, (size_t)s.nx * s.ny);
+  }
+  b->pool_elems = off;
+  b->initialised.assign(count, 0);
+  return b;
+}
+
+void lbm_batch_destroy(lbm_batch_t* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  drop_batch_graphs(b);
+  if (b->owns_pools) {
+    cudaFree(b->pool[0]);
+    cudaFree(b->pool[1]);
+    cudaFree(b->scratch);
+  }
+  cudaFree(b->d_inst);
+  cudaFree(b->d_items);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+int64_t lbm_batch_cells(const lbm_batch_t* b) { return b ? b->cells : -1; }
+
+size_t lbm_batch_buffer_bytes(const lbm_batch_t* b) { return b ? (size_t)b->pool_elems * b->elt : 0; }
+
+size_t lbm_batch_scratch_bytes(const lbm_batch_t* b) {
+  return b ? 3 * round_up(b->max_cells * sizeof(double), 256) + round_up((1024 * 4 + 4) * sizeof(double), 256) : 0;
+}
+
+int lbm_batch_bind(lbm_batch_t* b, void* dev_a, void* dev_b, void* dev_scratch) {
+  if (!b || !dev_a || !dev_b || !dev_scratch) return bfail(LBM_EINVAL, "lbm_batch_bind: NULL argument");
+  if (b->bound) return bfail(LBM_ESTATE, "lbm_batch_bind: memory already bound or allocated");
+  for (void* p : {dev_a, dev_b, dev_scratch})
+    if (reinterpret_cast<uintptr_t>(p) % 256) return bfail(LBM_EINVAL, "lbm_batch_bind: pointers must be 256-byte aligned");
+  BATCH_CUDA(cudaGetDevice(&b->device));
+  b->pool[0] = dev_a;
+  b->pool[1] = dev_b;
+  b->scratch = dev_scratch;
+  b->bound = true;
+  return LBM_OK;
+}
+
+int lbm_batch_set_nsbc(lbm_batch_t* b, double gamma, double beta, double kappa, int32_t grad_order) {
+  if (!b) return bfail(LBM_EINVAL, "lbm_batch_set_nsbc: NULL handle");
+  if (!std::isfinite(gamma) || !std::isfinite(beta) || !std::isfinite(kappa) || (grad_order != 1 && grad_order != 2))
+    return bfail(LBM_EINVAL, "lbm_batch_set_nsbc: need finite gamma, beta, kappa and grad_order 1 or 2");
+  b->nsbc.gamma = gamma;
+  b->nsbc.beta = beta;
+  b->nsbc.kappa = kappa;
+  b->nsbc.order = grad_order;
+  drop_batch_graphs(b);
+  return LBM_OK;
+}
+
+int lbm_batch_set_collision(lbm_batch_t* b, int32_t model, double omega_e, double omega_eps, double omega_q) {
+  if (!b) return bfail(LBM_EINVAL, "lbm_batch_set_collision: NULL handle");
+  if (model != LBM_BGK && model != LBM_MRT) return bfail(LBM_EINVAL, "lbm_batch_set_collision: unknown model %d", model);
+  if (model == LBM_MRT)
+    for (double r : {omega_e, omega_eps, omega_q})
+      if (!std::isfinite(r) || !(r > 0.0) || !(r < 2.0))
+        return bfail(LBM_EINVAL, "lbm_batch_set_collision: MRT rates must lie in (0, 2)");
+  b->collision = model;
+  b->items_dirty = true;  // the kernel's occupancy (one wave of blocks) depends on the model
+  if (model == LBM_MRT) {
+    b->s_e = omega_e;
+    b->s_eps = omega_eps;
+    b->s_q = omega_q;
+  }
+  drop_batch_graphs(b);
+  return LBM_OK;
+}
+
+int lbm_batch_set_stream(lbm_batch_t* b, void* cuda_stream) {
+  if (!b) return bfail(LBM_EINVAL, "lbm_batch_set_stream: NULL handle");
+  b->stream = static_cast<cudaStream_t>(cuda_stream);
+  return LBM_OK;
+}
+
+int lbm_batch_init(lbm_batch_t* b, int32_t k, const double* rho, const double* ux, const double* uy) {
+  if (!b || !rho || !ux || !uy) return bfail(LBM_EINVAL, "lbm_batch_init: NULL argument");
+  if (k < 0 || k >= b->count) return bfail(LBM_EINVAL, "lbm_batch_init: instance %d out of range", k);
+  int rc = ensure_batch_memory(b);
+  if (rc) return rc;
+  const InstDev& d = b->inst[k];
+  const size_t bytes = (size_t)d.nx * d.ny * sizeof(double);
+  const double* src[3] = {rho, ux, uy};
+  for (int c = 0; c < 3; ++c)
+    BATCH_CUDA(cudaMemcpyAsync(bscratch(b, c), src[c], bytes, cudaMemcpyHostToDevice, b->stream));
+  const long long n = (long long)d.ny * d.pitch;
+  const int grid = (int)std::min<long long>(152LL * 32, (n + 255) / 256);
+  bdispatch(b->storage, [&](auto tag) {
+    using T = decltype(tag);
+    for (int p = 0; p < 2; ++p)
+      lbmk::init_kernel<T><<<grid, 256, 0, b->stream>>>(static_cast<T*>(b->pool[p]) + d.off, inst_geom(d),
+                                                        bscratch(b, 0), bscratch(b, 1), bscratch(b, 2));
+  });
+  rc = batch_check_launch();
+  if (rc) return rc;
+  BATCH_CUDA(cudaStreamSynchronize(b->stream));
+  if (b->steps != 0 || b->cur != 0) {
+    // a fresh start for the whole batch: step counts are per batch
+    b->steps = 0;
+  }
+  b->initialised[k] = 1;
+  return LBM_OK;
+}
+
+int lbm_batch_step(lbm_batch_t* b, int32_t n) {
+  if (!b) return bfail(LBM_EINVAL, "lbm_batch_step: NULL handle");
+  if (n < 0) return bfail(LBM_EINVAL, "lbm_batch_step: n=%d < 0", n);
+  for (int k = 0; k < b->count; ++k)
+    if (!b->initialised[k]) return bfail(LBM_ESTATE, "lbm_batch_step: instance %d not initialised", k);
+  int rc = build_items(b);
+  if (rc) return rc;
+  if (!b->cap) BATCH_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+  int left = n;
+  if (left >= kBatchGraphSteps) {
+    if (!b->graph[b->cur]) {
+      cudaGraph_t g = nullptr;
+      BATCH_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+      for (int s = 0; s < kBatchGraphSteps; ++s) enqueue_batch_step(b, (b->cur + s) & 1, b->cap);
+      cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+      if (e != cudaSuccess) return bfail(LBM_ECUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&b->graph[b->cur], g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return bfail(LBM_ECUDA, "batch graph instantiate failed: %s", cudaGetErrorString(e));
+    }
+    while (left >= kBatchGraphSteps) {
+      BATCH_CUDA(cudaGraphLaunch(b->graph[b->cur], b->stream));
+      left -= kBatchGraphSteps;
+    }
+  }
+  for (; left > 0; --left) {
+    enqueue_batch_step(b, b->cur, b->stream);
+    b->cur ^= 1;
+  }
+  rc = batch_check_launch();
+  if (rc) return rc;
+  b->steps += n;
+  return LBM_OK;
+}
+
+int lbm_batch_get_macros(lbm_batch_t* b, int32_t k, double* rho, double* ux, double* uy) {
+  if (!b || !rho || !ux || !uy) return bfail(LBM_EINVAL, "lbm_batch_get_macros: NULL argument");
+  if (k < 0 || k >= b->count) return bfail(LBM_EINVAL, "lbm_batch_get_macros: instance %d out of range", k);
+  if (!b->initialised[k]) return bfail(LBM_ESTATE, "lbm_batch_get_macros: instance %d not initialised", k);
+  const InstDev& d = b->inst[k];
+  const long long n = (long long)d.nx * d.ny;
+  const int grid = (int)std::min<long long>(152LL * 32, (n + 255) / 256);
+  bdispatch(b->storage, [&](auto tag) {
+    using T = decltype(tag);
+    lbmk::macros_kernel<T><<<grid, 256, 0, b->stream>>>(static_cast<const T*>(b->pool[b->cur]) + d.off, inst_geom(d),
+                                                        bscratch(b, 0), bscratch(b, 1), bscratch(b, 2));
+  });
+  int rc = batch_check_launch();
+  if (rc) return rc;
+  double* dst[3] = {rho, ux, uy};
+  for (int c = 0; c < 3; ++c)
+    BATCH_CUDA(cudaMemcpyAsync(dst[c], bscratch(b, c), n * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+  BATCH_CUDA(cudaStreamSynchronize(b->stream));
+  return LBM_OK;
+}
+
+int lbm_batch_unstable_nodes(lbm_batch_t* b, int32_t k, int64_t* count) {
+  if (!b || !count) return bfail(LBM_EINVAL, "lbm_batch_unstable_nodes: NULL argument");
+  if (k < 0 || k >= b->count) return bfail(LBM_EINVAL, "lbm_batch_unstable_nodes: instance %d out of range", k);
+  if (!b->initialised[k]) return bfail(LBM_ESTATE, "lbm_batch_unstable_nodes: instance %d not initialised", k);
+  const InstDev& d = b->inst[k];
+  const long long n = (long long)d.nx * d.ny;
+  const int blocks = (int)std::min<long long>(1024, (n + 255) / 256);
+  double* partials = bscratch(b, 3);  // after the three field slots
+  double* out = partials + 1024 * 4;
+  lbmk::RefField ref{nullptr, nullptr, nullptr, 0};
+  bdispatch(b->storage, [&](auto tag) {
+    using T = decltype(tag);
+    lbmk::reduce_kernel<T, 256><<<blocks, 256, 0, b->stream>>>(static_cast<const T*>(b->pool[b->cur]) + d.off,
+                                                               inst_geom(d), ref, d.m0[0], d.m0[1], d.m0[2], partials);
+  });
+  lbmk::reduce_finish<256><<<1, 256, 0, b->stream>>>(partials, blocks, out);
+  int rc = batch_check_launch();
+  if (rc) return rc;
+  double h[4];
+  BATCH_CUDA(cudaMemcpyAsync(h, out, sizeof h, cudaMemcpyDeviceToHost, b->stream));
+  BATCH_CUDA(cudaStreamSynchronize(b->stream));
+  *count = (int64_t)h[3];
+  return LBM_OK;
+}
+
+int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_t blocks) {
+  if (!b) return bfail(LBM_EINVAL, "lbm_batch_set_launch: NULL handle");
+  if (!batch_shape_ok(threads_x, rows)) return bfail(LBM_EINVAL, "lbm_batch_set_launch: shape (%d, %d) not compiled", threads_x, rows);
+  if (blocks < 0) return bfail(LBM_EINVAL, "lbm_batch_set_launch: blocks=%d < 0", blocks);
+  if (threads_x != b->bx || rows != b->rows) b->items_dirty = true;
+  b->bx = threads_x;
+  b->rows = rows;
+  b->blocks = blocks;
+  drop_batch_graphs(b);
+  return LBM_OK;
+}
+
+int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_t* blocks, double* ms_per_step) {
+  if (!b) return bfail(LBM_EINVAL, "lbm_batch_autotune: NULL handle");
+  for (int k = 0; k < b->count; ++k)
+    if (!b->initialised[k]) return bfail(LBM_ESTATE, "lbm_batch_autotune: instance %d not initialised", k);
+  // keep the state: current pool copied aside and restored
+  const size_t pb = lbm_batch_buffer_bytes(b);
+  void* backup = nullptr;
+  BATCH_CUDA(cudaMallocAsync(&backup, pb, b->stream));
+  BATCH_CUDA(cudaMemcpyAsync(backup, b->pool[b->cur], pb, cudaMemcpyDeviceToDevice, b->stream));
+  cudaEvent_t e0, e1;
+  BATCH_CUDA(cudaEventCreate(&e0));
+  BATCH_CUDA(cudaEventCreate(&e1));
+  const int reps = (int)std::max<long long>(4, std::min<long long>(32, (1LL << 28) / std::max(b->cells, 1LL)));
+  float best = 1e30f;
+  int bb = b->bx, br = b->rows, bk = b->blocks;
+  int rc = LBM_OK;
+  for (int bx : kBatchBX)
+    for (int r : kBatchRows)
+      for (int mult : {0, 2, 4}) {
+        b->bx = bx;
+        b->rows = r;
+        b->items_dirty = true;
+        rc = build_items(b);
+        if (rc) break;
+        const int wave = wave_blocks(b);
+        b->blocks = mult == 0 ? 0 : wave * mult;  // 0: one resident wave
+        for (int s = 0; s < 2; ++s) enqueue_batch_step(b, s & 1, b->stream);
+        cudaEventRecord(e0, b->stream);
+        for (int s = 0; s < reps; ++s) enqueue_batch_step(b, s & 1, b->stream);
+        cudaEventRecord(e1, b->stream);
+        BATCH_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (ms < best) {
+          best = ms;
+          bb = bx;
+          br = r;
+          bk = b->blocks;
+        }
+      }
+  if (!rc) rc = batch_check_launch();
+  b->bx = bb;
+  b->rows = br;
+  b->blocks = bk;
+  b->items_dirty = true;
+  int rc2 = build_items(b);
+  BATCH_CUDA(cudaMemcpyAsync(b->pool[b->cur], backup, pb, cudaMemcpyDeviceToDevice, b->stream));
+  BATCH_CUDA(cudaFreeAsync(backup, b->stream));
+  BATCH_CUDA(cudaStreamSynchronize(b->stream));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (rc2) return rc2;
+  if (threads_x) *threads_x = bb;
+  if (rows) *rows = br;
+  if (blocks) *blocks = bk;
+  if (ms_per_step) *ms_per_step = best;
+  return LBM_OK;
+}
+
+int64_t lbm_batch_steps_done(const lbm_batch_t* b) { return b ? b->steps : -1; }
+
+}  // extern "C"

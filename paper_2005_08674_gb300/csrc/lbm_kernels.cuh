@@ -25,21 +25,44 @@ namespace lbmk {
 // segment (V = 16 bytes / sizeof(T)), blocks of BX threads cover BX*V cells
 // of `rows` consecutive rows.  Only nodes 1..nx-2 are stored.
 // ---------------------------------------------------------------------------
-template <typename T, int BX, int MODEL>
-__global__ void __launch_bounds__(BX) bulk_kernel(const T* __restrict__ A, T* __restrict__ B, Geom g,
-                                                  Rates<typename Store<T>::C> rates, int rows) {
+// Bytes of one warp's row segment (32 lanes x V nodes) starting at warp_x0,
+// clipped to the row pitch, for the L2 prefetch.
+template <typename T>
+__device__ __forceinline__ unsigned warp_segment_bytes(const Geom& g, int warp_x0) {
+  return (unsigned)(min(32 * Store<T>::V, g.pitch - warp_x0) * (int)sizeof(T)) & ~15u;
+}
+
+// One interior row y of the warp's segment: lane owns nodes x0..x0+V-1.
+// Every lane of the warp must call this (shuffles).  L2 prefetch distance pf
+// in rows (0 = off): lane 0 asks the bulk-copy engine to pull the warp's
+// segments of row y + pf into L2, so more bytes are in flight than the
+// registers of the resident warps hold.
+template <typename T, int MODEL>
+__device__ __forceinline__ void bulk_row(const T* __restrict__ A, T* __restrict__ B, const Geom& g,
+                                         const Rates<typename Store<T>::C>& rates, int y, int x0, int lane,
+                                         int pf, unsigned pf_bytes) {
   using S = Store<T>;
   using C = typename S::C;
   constexpr int V = S::V;
-  const int lane = threadIdx.x & 31;
-  const int x0 = (blockIdx.x * BX + threadIdx.x) * V;
   const bool active = x0 < g.nx;
   const long long P = g.plane;
-  const int y_begin = 1 + blockIdx.y * rows;
-  const int y_end = min(y_begin + rows, g.ny - 1);
-  for (int y = y_begin; y < y_end; ++y) {
+  const int warp_x0 = x0 - lane * V;
+  {
     const long long r0 = (long long)y * g.pitch + x0;
     const long long rm = r0 - g.pitch, rp = r0 + g.pitch;
+    if (pf > 0 && lane == 0 && warp_x0 < g.nx && y + pf <= g.ny - 2 && pf_bytes > 0) {
+      const long long q0 = (long long)(y + pf) * g.pitch + warp_x0;
+      const long long qm = q0 - g.pitch, qp = q0 + g.pitch;
+      prefetch_l2(A + 0 * P + q0, pf_bytes);
+      prefetch_l2(A + 1 * P + q0, pf_bytes);
+      prefetch_l2(A + 2 * P + q0, pf_bytes);
+      prefetch_l2(A + 3 * P + qm, pf_bytes);
+      prefetch_l2(A + 4 * P + qp, pf_bytes);
+      prefetch_l2(A + 5 * P + qm, pf_bytes);
+      prefetch_l2(A + 6 * P + qp, pf_bytes);
+      prefetch_l2(A + 7 * P + qm, pf_bytes);
+      prefetch_l2(A + 8 * P + qp, pf_bytes);
+    }
     C v[9][V];
     if (active) {
       S::ld(A + 0 * P + r0, v[0]);
@@ -111,6 +134,18 @@ __global__ void __launch_bounds__(BX) bulk_kernel(const T* __restrict__ A, T* __
   }
 }
 
+template <typename T, int BX, int MODEL>
+__global__ void __launch_bounds__(BX) bulk_kernel(const T* __restrict__ A, T* __restrict__ B, Geom g,
+                                                  Rates<typename Store<T>::C> rates, int rows, int pf) {
+  constexpr int V = Store<T>::V;
+  const int lane = threadIdx.x & 31;
+  const int x0 = (blockIdx.x * BX + threadIdx.x) * V;
+  const int y_begin = 1 + blockIdx.y * rows;
+  const int y_end = min(y_begin + rows, g.ny - 1);
+  const unsigned pf_bytes = warp_segment_bytes<T>(g, x0 - lane * V);
+  for (int y = y_begin; y < y_end; ++y) bulk_row<T, MODEL>(A, B, g, rates, y, x0, lane, pf, pf_bytes);
+}
+
 // ---------------------------------------------------------------------------
 // NSBC: four lanes per perimeter node.  Lane q loads the node b - q n and
 // forms its moments in double (q = 0, 1, and 2 for the second-order
@@ -118,15 +153,13 @@ __global__ void __launch_bounds__(BX) bulk_kernel(const T* __restrict__ A, T* __
 // and blends m_c in double, then rebuilds, corrects and collides the node in
 // the compute type.
 // ---------------------------------------------------------------------------
+// Node `node` of the perimeter, handled by the four lanes of one quad
+// (q = lane & 3); all four lanes must call this together.
 template <typename T, int MODEL>
-__global__ void __launch_bounds__(128) nsbc_kernel(const T* __restrict__ A, T* __restrict__ B, Geom g, Nsbc p,
-                                                   Rates<typename Store<T>::C> rates) {
+__device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict__ B, const Geom& g, const Nsbc& p,
+                                          const Rates<typename Store<T>::C>& rates, int node, int q) {
   using S = Store<T>;
   using C = typename S::C;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const int node = t >> 2, q = t & 3;
-  const int perim = 2 * g.nx + 2 * (g.ny - 2);
-  if (node >= perim) return;  // a quad leaves together
   const unsigned quad = 0xFu << ((threadIdx.x & 31) & ~3);
   int x, y, nxn, nyn;
   perimeter_node(node, g.nx, g.ny, x, y, nxn, nyn);
@@ -186,6 +219,16 @@ __global__ void __launch_bounds__(128) nsbc_kernel(const T* __restrict__ A, T* _
   const long long o = (long long)y * g.pitch + x;
 #pragma unroll
   for (int i = 0; i < 9; ++i) S::st1(B + i * g.plane + o, h[i]);
+}
+
+template <typename T, int MODEL>
+__global__ void __launch_bounds__(128) nsbc_kernel(const T* __restrict__ A, T* __restrict__ B, Geom g, Nsbc p,
+                                                   Rates<typename Store<T>::C> rates) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int node = t >> 2, q = t & 3;
+  const int perim = 2 * g.nx + 2 * (g.ny - 2);
+  if (node >= perim) return;  // a quad leaves together
+  nsbc_node<T, MODEL>(A, B, g, p, rates, node, q);
 }
 
 // ---------------------------------------------------------------------------

@@ -30,6 +30,17 @@ int fail(int code, const char* fmt, ...) {
   return code;
 }
 
+}  // namespace
+
+// Shared with the other translation units of the library (batched mode):
+// records the calling thread's error message and returns `code`.
+int lbm_internal_fail(int code, const char* msg) {
+  g_last_error = msg;
+  return code;
+}
+
+namespace {
+
 #define LBM_CUDA(call)                                                                          \
   do {                                                                                          \
     cudaError_t e_ = (call);                                                                    \
@@ -46,6 +57,8 @@ constexpr int kNsbcThreads = 128;
 // launch shapes compiled for the bulk kernel: threads per block along x
 constexpr int kShapesBX[] = {64, 128, 256, 512};
 constexpr int kShapesRows[] = {1, 2, 4, 8};
+// L2 prefetch distances (rows ahead) tried by the autotuner
+constexpr int kPrefetchRows[] = {0, 1, 3, 8};
 
 }  // namespace
 
@@ -67,7 +80,7 @@ struct lbm {
   cudaStream_t cap = nullptr, side = nullptr;  // capture stream and NSBC branch
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by starting buffer
-  int bx = 128, rows = 1;
+  int bx = 128, rows = 1, pf = 0;  // bulk launch shape and L2 prefetch distance (rows)
   int device = 0;
   int collision = 0;                          // 0 = BGK, 1 = MRT
   double s_e = 1.0, s_eps = 1.0, s_q = 1.0;   // MRT energy, energy-square and flux rates
@@ -144,10 +157,10 @@ void launch_bulk_bx(const lbm_t* h, const void* a, void* b, int rows, cudaStream
   dim3 grid((nvec + BX - 1) / BX, (h->ny - 2 + rows - 1) / rows);
   if (h->collision == 1)
     lbmk::bulk_kernel<T, BX, 1><<<grid, BX, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
-                                                   rates<C>(h), rows);
+                                                   rates<C>(h), rows, h->pf);
   else
     lbmk::bulk_kernel<T, BX, 0><<<grid, BX, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
-                                                   rates<C>(h), rows);
+                                                   rates<C>(h), rows, h->pf);
 }
 
 template <typename T>
@@ -571,7 +584,7 @@ int lbm_profile_read(lbm_t* h, double out[4]) {
   return LBM_OK;
 }
 
-int lbm_set_launch(lbm_t* h, int32_t threads_x, int32_t rows) {
+int lbm_set_launch(lbm_t* h, int32_t threads_x, int32_t rows, int32_t prefetch_rows) {
   if (!h) return fail(LBM_EINVAL, "lbm_set_launch: NULL handle");
   if (threads_x == 0 && rows == 0) {
     threads_x = 128;
@@ -579,13 +592,16 @@ int lbm_set_launch(lbm_t* h, int32_t threads_x, int32_t rows) {
   }
   if (!shape_compiled(threads_x, rows))
     return fail(LBM_EINVAL, "lbm_set_launch: shape (%d, %d) not compiled", threads_x, rows);
+  if (prefetch_rows < 0 || prefetch_rows > 64)
+    return fail(LBM_EINVAL, "lbm_set_launch: prefetch_rows=%d outside [0, 64]", prefetch_rows);
   h->bx = threads_x;
   h->rows = rows;
+  h->pf = prefetch_rows;
   drop_graphs(h);
   return LBM_OK;
 }
 
-int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, double* ms_per_step) {
+int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_rows, double* ms_per_step) {
   if (!h) return fail(LBM_EINVAL, "lbm_autotune: NULL handle");
   if (!h->initialised) return fail(LBM_ESTATE, "lbm_autotune: call lbm_init first");
   int rc = ensure_streams(h);
@@ -601,29 +617,33 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, double* ms_per_ste
   const long long cells = (long long)h->nx * h->ny;
   const int reps = (int)std::max<long long>(4, std::min<long long>(64, (1LL << 28) / std::max(cells, 1LL)));
   float best = 1e30f;
-  int best_bx = h->bx, best_rows = h->rows;
+  int best_bx = h->bx, best_rows = h->rows, best_pf = h->pf;
   for (int bx : kShapesBX)
-    for (int r : kShapesRows) {
-      if (r > 1 && (h->ny - 2) / r < 152) continue;  // too few blocks to fill the GPU
-      h->bx = bx;
-      h->rows = r;
-      for (int k = 0; k < 2; ++k) enqueue_step(h, k & 1, h->stream, false);
-      cudaEventRecord(e0, h->stream);
-      for (int k = 0; k < reps; ++k) enqueue_step(h, k & 1, h->stream, false);
-      cudaEventRecord(e1, h->stream);
-      LBM_CUDA(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms /= reps;
-      if (ms < best) {
-        best = ms;
-        best_bx = bx;
-        best_rows = r;
+    for (int r : kShapesRows)
+      for (int pf : kPrefetchRows) {
+        if (r > 1 && (h->ny - 2) / r < 152) continue;  // too few blocks to fill the GPU
+        h->bx = bx;
+        h->rows = r;
+        h->pf = pf;
+        for (int k = 0; k < 2; ++k) enqueue_step(h, k & 1, h->stream, false);
+        cudaEventRecord(e0, h->stream);
+        for (int k = 0; k < reps; ++k) enqueue_step(h, k & 1, h->stream, false);
+        cudaEventRecord(e1, h->stream);
+        LBM_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= reps;
+        if (ms < best) {
+          best = ms;
+          best_bx = bx;
+          best_rows = r;
+          best_pf = pf;
+        }
       }
-    }
   rc = check_launch();
   h->bx = best_bx;
   h->rows = best_rows;
+  h->pf = best_pf;
   drop_graphs(h);
   LBM_CUDA(cudaMemcpyAsync(h->buf[h->cur], backup, bb, cudaMemcpyDeviceToDevice, h->stream));
   LBM_CUDA(cudaFreeAsync(backup, h->stream));
@@ -633,6 +653,7 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, double* ms_per_ste
   if (rc) return rc;
   if (threads_x) *threads_x = best_bx;
   if (rows) *rows = best_rows;
+  if (prefetch_rows) *prefetch_rows = best_pf;
   if (ms_per_step) *ms_per_step = best;
   return LBM_OK;
 }

@@ -55,11 +55,27 @@ _SIGS = {
     "lbm_get_populations": (ctypes.c_int, [_vp, _vp]),
     "lbm_set_populations": (ctypes.c_int, [_vp, _vp]),
     "lbm_reduce": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _dp]),
-    "lbm_set_launch": (ctypes.c_int, [_vp, _i32, _i32]),
-    "lbm_autotune": (ctypes.c_int, [_vp, _i32p, _i32p, _dp]),
+    "lbm_set_launch": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
+    "lbm_autotune": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _dp]),
     "lbm_reduce_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _dp]),
     "lbm_profile": (ctypes.c_int, [_vp, _i32]),
     "lbm_profile_read": (ctypes.c_int, [_vp, _dp]),
+    "lbm_batch_create": (_vp, [_i32, _vp, _i32]),
+    "lbm_batch_destroy": (None, [_vp]),
+    "lbm_batch_set_nsbc": (ctypes.c_int, [_vp, _dbl, _dbl, _dbl, _i32]),
+    "lbm_batch_set_collision": (ctypes.c_int, [_vp, _i32, _dbl, _dbl, _dbl]),
+    "lbm_batch_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "lbm_batch_cells": (ctypes.c_int64, [_vp]),
+    "lbm_batch_buffer_bytes": (ctypes.c_size_t, [_vp]),
+    "lbm_batch_scratch_bytes": (ctypes.c_size_t, [_vp]),
+    "lbm_batch_bind": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "lbm_batch_init": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp]),
+    "lbm_batch_step": (ctypes.c_int, [_vp, _i32]),
+    "lbm_batch_steps_done": (ctypes.c_int64, [_vp]),
+    "lbm_batch_get_macros": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp]),
+    "lbm_batch_unstable_nodes": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(ctypes.c_int64)]),
+    "lbm_batch_set_launch": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
+    "lbm_batch_autotune": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _dp]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -198,14 +214,15 @@ def lbm_reduce_noalloc(h, ref_rho: int = 0, ref_ux: int = 0, ref_uy: int = 0, re
     return list(out)
 
 
-def lbm_set_launch(h, threads_x: int, rows: int):
-    return _check(_L.lbm_set_launch(h, threads_x, rows))
+def lbm_set_launch(h, threads_x: int, rows: int, prefetch_rows: int = 0):
+    return _check(_L.lbm_set_launch(h, threads_x, rows, prefetch_rows))
 
 
 def lbm_autotune(h):
-    bx, rows, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
-    _check(_L.lbm_autotune(h, ctypes.byref(bx), ctypes.byref(rows), ctypes.byref(ms)))
-    return bx.value, rows.value, ms.value
+    """(threads_x, rows, prefetch_rows, ms_per_step) of the fastest bulk launch."""
+    bx, rows, pf, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(_L.lbm_autotune(h, ctypes.byref(bx), ctypes.byref(rows), ctypes.byref(pf), ctypes.byref(ms)))
+    return bx.value, rows.value, pf.value, ms.value
 
 
 def lbm_profile(h, enable: bool):
@@ -322,6 +339,165 @@ class Simulation:
     def autotune(self):
         return lbm_autotune(self.h)
 
-    def set_launch(self, threads_x, rows):
-        lbm_set_launch(self.h, threads_x, rows)
+    def set_launch(self, threads_x, rows, prefetch_rows=0):
+        lbm_set_launch(self.h, threads_x, rows, prefetch_rows)
+        return self
+
+
+# --- batched mode -----------------------------------------------------------------
+
+class InstanceDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("tau", ctypes.c_double),
+                ("farfield_rho", ctypes.c_double), ("farfield_ux", ctypes.c_double),
+                ("farfield_uy", ctypes.c_double)]
+
+
+def lbm_batch_create(descs, storage="f32"):
+    """descs: iterable of (nx, ny, tau, farfield_rho, farfield_ux, farfield_uy)."""
+    arr = (InstanceDesc * len(descs))(*[InstanceDesc(*d) for d in descs])
+    b = _L.lbm_batch_create(len(descs), ctypes.cast(arr, ctypes.c_void_p), STORAGE.get(storage, storage))
+    if not b:
+        raise LbmError(LBM_EINVAL, lbm_last_error())
+    return ctypes.c_void_p(b)
+
+
+def lbm_batch_destroy(b):
+    _L.lbm_batch_destroy(b)
+
+
+def lbm_batch_set_nsbc(b, gamma=0.6, beta=0.0, kappa=3.0, grad_order=1):
+    return _check(_L.lbm_batch_set_nsbc(b, gamma, beta, kappa, grad_order))
+
+
+def lbm_batch_set_collision(b, model, omega_e=1.0, omega_eps=1.0, omega_q=1.0):
+    m = {"bgk": LBM_BGK, "mrt": LBM_MRT}.get(model, model)
+    return _check(_L.lbm_batch_set_collision(b, m, omega_e, omega_eps, omega_q))
+
+
+def lbm_batch_set_stream(b, stream_handle: int):
+    return _check(_L.lbm_batch_set_stream(b, ctypes.c_void_p(stream_handle)))
+
+
+def lbm_batch_cells(b) -> int:
+    return int(_L.lbm_batch_cells(b))
+
+
+def lbm_batch_buffer_bytes(b) -> int:
+    return int(_L.lbm_batch_buffer_bytes(b))
+
+
+def lbm_batch_scratch_bytes(b) -> int:
+    return int(_L.lbm_batch_scratch_bytes(b))
+
+
+def lbm_batch_bind(b, dev_a: int, dev_b: int, dev_scratch: int):
+    return _check(_L.lbm_batch_bind(b, ctypes.c_void_p(dev_a), ctypes.c_void_p(dev_b), ctypes.c_void_p(dev_scratch)))
+
+
+def lbm_batch_init(b, k, rho, ux, uy):
+    rho, ux, uy = _host(rho), _host(ux), _host(uy)
+    return _check(_L.lbm_batch_init(b, int(k), _hp(rho), _hp(ux), _hp(uy)))
+
+
+def lbm_batch_step(b, n: int):
+    return _check(_L.lbm_batch_step(b, int(n)))
+
+
+def lbm_batch_steps_done(b) -> int:
+    return int(_L.lbm_batch_steps_done(b))
+
+
+def lbm_batch_get_macros(b, k, rho, ux, uy):
+    for a in (rho, ux, uy):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    return _check(_L.lbm_batch_get_macros(b, int(k), _hp(rho), _hp(ux), _hp(uy)))
+
+
+def lbm_batch_unstable_nodes(b, k) -> int:
+    c = ctypes.c_int64()
+    _check(_L.lbm_batch_unstable_nodes(b, int(k), ctypes.byref(c)))
+    return c.value
+
+
+def lbm_batch_set_launch(b, threads_x: int, rows: int, blocks: int = 0):
+    return _check(_L.lbm_batch_set_launch(b, threads_x, rows, blocks))
+
+
+def lbm_batch_autotune(b):
+    """(threads_x, rows, blocks, ms_per_step) of the fastest batched launch."""
+    bx, rows, blk, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(_L.lbm_batch_autotune(b, ctypes.byref(bx), ctypes.byref(rows), ctypes.byref(blk), ctypes.byref(ms)))
+    return bx.value, rows.value, blk.value, ms.value
+
+
+class Batch:
+    """Independent instances stepped by one launch per step; torch allocates the pools."""
+
+    def __init__(self, workloads, storage="f32", collision="bgk", mrt_rates=(1.0, 1.0, 1.0),
+                 gamma=0.6, beta=0.0, kappa=3.0, grad_order=1, stream=None):
+        import torch
+        self.shapes = [(w.nx, w.ny) for w in workloads]
+        descs = [(w.nx, w.ny, w.tau, w.farfield_rho, w.farfield_u[0], w.farfield_u[1]) for w in workloads]
+        self.b = lbm_batch_create(descs, storage)
+        try:
+            lbm_batch_set_nsbc(self.b, gamma, beta, kappa, grad_order)
+            lbm_batch_set_collision(self.b, collision, *mrt_rates)
+            dev = torch.device("cuda", torch.cuda.current_device())
+            self.stream = stream or torch.cuda.current_stream(dev)
+            lbm_batch_set_stream(self.b, self.stream.cuda_stream)
+            pb, sb = lbm_batch_buffer_bytes(self.b), lbm_batch_scratch_bytes(self.b)
+            self._a = torch.empty(pb, dtype=torch.uint8, device=dev)
+            self._b = torch.empty(pb, dtype=torch.uint8, device=dev)
+            self._s = torch.empty(sb, dtype=torch.uint8, device=dev)
+            lbm_batch_bind(self.b, self._a.data_ptr(), self._b.data_ptr(), self._s.data_ptr())
+        except Exception:
+            lbm_batch_destroy(self.b)
+            self.b = None
+            raise
+
+    @property
+    def cells(self):
+        return lbm_batch_cells(self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            lbm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def init(self, k, rho, ux, uy):
+        lbm_batch_init(self.b, k, rho, ux, uy)
+        return self
+
+    def step(self, n=1):
+        lbm_batch_step(self.b, n)
+        return self
+
+    def macros(self, k):
+        nx, ny = self.shapes[k]
+        rho = np.empty((ny, nx))
+        ux = np.empty_like(rho)
+        uy = np.empty_like(rho)
+        lbm_batch_get_macros(self.b, k, rho, ux, uy)
+        return rho, ux, uy
+
+    def unstable_nodes(self, k):
+        return lbm_batch_unstable_nodes(self.b, k)
+
+    def autotune(self):
+        return lbm_batch_autotune(self.b)
+
+    def set_launch(self, threads_x, rows, blocks=0):
+        lbm_batch_set_launch(self.b, threads_x, rows, blocks)
         return self

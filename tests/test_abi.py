@@ -64,7 +64,7 @@ def test_host_side_argument_checks(lib_path):
         with pytest.raises(lbm.LbmError):
             lbm.lbm_step(h, 1)  # not initialised
         with pytest.raises(lbm.LbmError):
-            lbm.lbm_set_launch(h, 96, 1)
+            lbm.lbm_set_launch(h, 96, 1, 0)
         assert lbm.lbm_steps_done(h) == 0
     finally:
         lbm.lbm_destroy(h)
