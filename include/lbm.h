@@ -241,11 +241,15 @@ int lbm_batch_get_macros(lbm_batch_t* b, int32_t k, double* rho, double* ux, dou
 int lbm_batch_unstable_nodes(lbm_batch_t* b, int32_t k, int64_t* count);
 /* Tile shape: threads per block along x (64, 128, 256) times the storage's
  * 16-byte vector of nodes per thread, `rows` rows per tile (nodes per thread
- * = vector x rows), and the persistent grid size (0 = one resident wave). */
-int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_t blocks);
-/* Time every compiled tile shape and grid size on the batch's own state
- * (restored afterwards) and keep the fastest. */
-int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_t* blocks, double* ms_per_step);
+ * = vector x rows); grid size `blocks` (-1 = one block per work item,
+ * 0 = one resident wave of blocks looping over the list, > 0 = that many);
+ * L2 prefetch distance in rows inside tiles (0 = off, at most 64). */
+int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_t blocks, int32_t prefetch_rows);
+/* Time every compiled tile shape, grid size and prefetch distance on the
+ * batch's own state (restored afterwards, through a temporary device copy
+ * from cudaMallocAsync) and keep the fastest. */
+int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_t* blocks, int32_t* prefetch_rows,
+                       double* ms_per_step);
 
 /* Per-launch timing.  While enabled, lbm_step launches every step directly
  * (no graph) on the handle's stream with CUDA events around the bulk

@@ -78,7 +78,8 @@ struct lbm_batch {
   InstDev* d_inst = nullptr;
   int4* d_items = nullptr;
   int n_items = 0, n_bulk_items = 0;
-  int bx = 128, rows = 1, blocks = 0;  // blocks = 0: one wave of resident blocks
+  int bx = 128, rows = 1, blocks = -1;  // blocks: -1 one per item, 0 one resident wave, > 0 as given
+  int pf = 0;                           // L2 prefetch distance in rows inside bulk tiles
   int wave = 1;                        // resident blocks on the device for the current shape
   bool items_dirty = true;
   std::vector<char> initialised;
@@ -105,7 +106,7 @@ template <typename T, int BX, int MODEL>
 __global__ void __launch_bounds__(BX) batch_step_kernel(const T* __restrict__ A, T* __restrict__ B,
                                                         const InstDev* __restrict__ inst,
                                                         const int4* __restrict__ items, int n_items, lbmk::Nsbc p,
-                                                        double s_e, double s_eps, double s_q) {
+                                                        double s_e, double s_eps, double s_q, int pf) {
   using C = typename lbmk::Store<T>::C;
   constexpr int V = lbmk::Store<T>::V;
   const int lane = threadIdx.x & 31;
@@ -120,7 +121,7 @@ __global__ void __launch_bounds__(BX) batch_step_kernel(const T* __restrict__ A,
     if (!edge) {
       const int x0 = w.z + (int)threadIdx.x * V;
       const unsigned pfb = lbmk::warp_segment_bytes<T>(g, x0 - lane * V);
-      for (int y = w.y; y < w.y + w.w; ++y) lbmk::bulk_row<T, MODEL>(a, b, g, r, y, x0, lane, 0, pfb);
+      for (int y = w.y; y < w.y + w.w; ++y) lbmk::bulk_row<T, MODEL>(a, b, g, r, y, x0, lane, pf, pfb);
     } else {
       lbmk::Nsbc q = p;
       q.m0[0] = d.m0[0];
@@ -143,10 +144,10 @@ void launch_batch_bx(const lbm_batch_t* b, int from, cudaStream_t s, int grid) {
   T* B = static_cast<T*>(b->pool[1 - from]);
   if (b->collision == 1)
     batch_step_kernel<T, BX, 1><<<grid, BX, 0, s>>>(A, B, b->d_inst, b->d_items, b->n_items, b->nsbc, b->s_e,
-                                                    b->s_eps, b->s_q);
+                                                    b->s_eps, b->s_q, b->pf);
   else
     batch_step_kernel<T, BX, 0><<<grid, BX, 0, s>>>(A, B, b->d_inst, b->d_items, b->n_items, b->nsbc, b->s_e,
-                                                    b->s_eps, b->s_q);
+                                                    b->s_eps, b->s_q, b->pf);
 }
 
 // resident blocks per SM for the current shape
@@ -163,7 +164,8 @@ int wave_blocks(const lbm_batch_t* b) {
 }
 
 void enqueue_batch_step(const lbm_batch_t* b, int from, cudaStream_t s) {
-  const int grid = std::max(1, std::min(b->n_items, b->blocks > 0 ? b->blocks : b->wave));
+  // blocks < 0: one block per work item; 0: one resident wave; > 0: as given
+  const int grid = std::max(1, b->blocks < 0 ? b->n_items : std::min(b->n_items, b->blocks > 0 ? b->blocks : b->wave));
   bdispatch(b->storage, [&](auto tag) {
     using T = decltype(tag);
     switch (b->bx) {
@@ -182,8 +184,9 @@ void drop_batch_graphs(lbm_batch_t* b) {
     }
 }
 
-// Work list for the current shape: bulk tiles (largest instances first),
-// then NSBC chunks.
+// Work list for the current shape: NSBC chunks first (latency-bound; they
+// start early and overlap with the bandwidth-bound tiles), then bulk tiles,
+// largest instances first.
 int build_items(lbm_batch_t* b) {
   if (!b->items_dirty) return LBM_OK;
   const int V = (int)(16 / b->elt);
@@ -193,19 +196,20 @@ int build_items(lbm_batch_t* b) {
     return (long long)b->inst[i].nx * b->inst[i].ny > (long long)b->inst[j].nx * b->inst[j].ny;
   });
   std::vector<int4> items;
-  for (int k : order) {
-    const InstDev& d = b->inst[k];
-    const int tile_x = b->bx * V;
-    for (int y0 = 1; y0 <= d.ny - 2; y0 += b->rows)
-      for (int x0 = 0; x0 < d.nx; x0 += tile_x) items.push_back(make_int4(k, y0, x0, std::min(b->rows, d.ny - 1 - y0)));
-  }
-  const int n_bulk = (int)items.size();
   const int chunk = b->bx / 4;
   for (int k : order) {
     const InstDev& d = b->inst[k];
     const int perim = 2 * d.nx + 2 * (d.ny - 2);
     for (int n0 = 0; n0 < perim; n0 += chunk) items.push_back(make_int4(~k, n0, std::min(chunk, perim - n0), 0));
   }
+  const int n_edge = (int)items.size();
+  for (int k : order) {
+    const InstDev& d = b->inst[k];
+    const int tile_x = b->bx * V;
+    for (int y0 = 1; y0 <= d.ny - 2; y0 += b->rows)
+      for (int x0 = 0; x0 < d.nx; x0 += tile_x) items.push_back(make_int4(k, y0, x0, std::min(b->rows, d.ny - 1 - y0)));
+  }
+  const int n_bulk = (int)items.size() - n_edge;
   if (b->d_items) cudaFree(b->d_items);
   b->d_items = nullptr;
   BATCH_CUDA(cudaMalloc(&b->d_items, items.size() * sizeof(int4)));
@@ -489,19 +493,23 @@ int lbm_batch_unstable_nodes(lbm_batch_t* b, int32_t k, int64_t* count) {
   return LBM_OK;
 }
 
-int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_t blocks) {
+int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_t blocks, int32_t prefetch_rows) {
   if (!b) return bfail(LBM_EINVAL, "lbm_batch_set_launch: NULL handle");
   if (!batch_shape_ok(threads_x, rows)) return bfail(LBM_EINVAL, "lbm_batch_set_launch: shape (%d, %d) not compiled", threads_x, rows);
-  if (blocks < 0) return bfail(LBM_EINVAL, "lbm_batch_set_launch: blocks=%d < 0", blocks);
+  if (blocks < -1) return bfail(LBM_EINVAL, "lbm_batch_set_launch: blocks=%d < -1", blocks);
+  if (prefetch_rows < 0 || prefetch_rows > 64)
+    return bfail(LBM_EINVAL, "lbm_batch_set_launch: prefetch_rows=%d outside [0, 64]", prefetch_rows);
   if (threads_x != b->bx || rows != b->rows) b->items_dirty = true;
   b->bx = threads_x;
   b->rows = rows;
   b->blocks = blocks;
+  b->pf = prefetch_rows;
   drop_batch_graphs(b);
   return LBM_OK;
 }
 
-int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_t* blocks, double* ms_per_step) {
+int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_t* blocks, int32_t* prefetch_rows,
+                       double* ms_per_step) {
   if (!b) return bfail(LBM_EINVAL, "lbm_batch_autotune: NULL handle");
   for (int k = 0; k < b->count; ++k)
     if (!b->initialised[k]) return bfail(LBM_ESTATE, "lbm_batch_autotune: instance %d not initialised", k);
@@ -515,37 +523,41 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
   BATCH_CUDA(cudaEventCreate(&e1));
   const int reps = (int)std::max<long long>(4, std::min<long long>(32, (1LL << 28) / std::max(b->cells, 1LL)));
   float best = 1e30f;
-  int bb = b->bx, br = b->rows, bk = b->blocks;
+  int bb = b->bx, br = b->rows, bk = b->blocks, bp = b->pf;
   int rc = LBM_OK;
   for (int bx : kBatchBX)
-    for (int r : kBatchRows)
-      for (int mult : {0, 2, 4}) {
-        b->bx = bx;
-        b->rows = r;
-        b->items_dirty = true;
-        rc = build_items(b);
-        if (rc) break;
-        const int wave = wave_blocks(b);
-        b->blocks = mult == 0 ? 0 : wave * mult;  // 0: one resident wave
-        for (int s = 0; s < 2; ++s) enqueue_batch_step(b, s & 1, b->stream);
-        cudaEventRecord(e0, b->stream);
-        for (int s = 0; s < reps; ++s) enqueue_batch_step(b, s & 1, b->stream);
-        cudaEventRecord(e1, b->stream);
-        BATCH_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        ms /= reps;
-        if (ms < best) {
-          best = ms;
-          bb = bx;
-          br = r;
-          bk = b->blocks;
+    for (int r : kBatchRows) {
+      b->bx = bx;
+      b->rows = r;
+      b->items_dirty = true;
+      rc = build_items(b);
+      if (rc) break;
+      for (int mult : {-1, 1, 2, 4})  // -1: one block per item; k: k resident waves, persistent
+        for (int pf : {0, 1}) {
+          b->blocks = mult < 0 ? -1 : b->wave * mult;
+          b->pf = pf;
+          for (int s = 0; s < 2; ++s) enqueue_batch_step(b, s & 1, b->stream);
+          cudaEventRecord(e0, b->stream);
+          for (int s = 0; s < reps; ++s) enqueue_batch_step(b, s & 1, b->stream);
+          cudaEventRecord(e1, b->stream);
+          BATCH_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          ms /= reps;
+          if (ms < best) {
+            best = ms;
+            bb = bx;
+            br = r;
+            bk = b->blocks;
+            bp = pf;
+          }
         }
-      }
+    }
   if (!rc) rc = batch_check_launch();
   b->bx = bb;
   b->rows = br;
   b->blocks = bk;
+  b->pf = bp;
   b->items_dirty = true;
   int rc2 = build_items(b);
   BATCH_CUDA(cudaMemcpyAsync(b->pool[b->cur], backup, pb, cudaMemcpyDeviceToDevice, b->stream));
@@ -558,6 +570,7 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
   if (threads_x) *threads_x = bb;
   if (rows) *rows = br;
   if (blocks) *blocks = bk;
+  if (prefetch_rows) *prefetch_rows = bp;
   if (ms_per_step) *ms_per_step = best;
   return LBM_OK;
 }

@@ -51,9 +51,11 @@ struct Store<double> {
   __device__ static void st(double* p, const C (&o)[V]) {
     __stcs(reinterpret_cast<double2*>(p), make_double2(o[0], o[1]));
   }
+  static constexpr double kScale = 1.0;
   __device__ static C ld1(const double* p) { return __ldcs(p); }
   __device__ static C ldg1(const double* p) { return __ldg(p); }
   __device__ static void st1(double* p, C v) { *p = v; }
+  __device__ static void st1r(double* p, C v) { *p = v; }
   __device__ static double cvt(C v) { return v; }
 };
 
@@ -71,9 +73,11 @@ struct Store<float> {
   __device__ static void st(float* p, const C (&o)[V]) {
     __stcs(reinterpret_cast<float4*>(p), make_float4(o[0], o[1], o[2], o[3]));
   }
+  static constexpr float kScale = 1.0f;
   __device__ static C ld1(const float* p) { return __ldcs(p); }
   __device__ static C ldg1(const float* p) { return __ldg(p); }
   __device__ static void st1(float* p, C v) { *p = v; }
+  __device__ static void st1r(float* p, C v) { *p = v; }
   __device__ static float cvt(C v) { return v; }
 };
 
@@ -84,10 +88,14 @@ struct Store<float> {
 constexpr float kHalfScale = 4096.0f;
 constexpr float kHalfUnscale = 1.0f / 4096.0f;
 
+// ld / st / ld1 / st1r move STORED values (s * h, s = kScale) and are used by
+// the bulk kernel, whose collision works in stored units; ldg1 / st1 / cvt
+// convert to and from h itself for the boundary and the helper kernels.
 template <>
 struct Store<__half> {
   using C = float;
   static constexpr int V = 8;
+  static constexpr float kScale = kHalfScale;
   __device__ static void ld(const __half* p, C (&o)[V]) {
     const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
     const uint32_t w[4] = {t.x, t.y, t.z, t.w};
@@ -96,20 +104,21 @@ struct Store<__half> {
       __half2 h2;
       memcpy(&h2, &w[k], 4);
       const float2 f = __half22float2(h2);
-      o[2 * k] = f.x * kHalfUnscale;
-      o[2 * k + 1] = f.y * kHalfUnscale;
+      o[2 * k] = f.x;
+      o[2 * k + 1] = f.y;
     }
   }
   __device__ static void st(__half* p, const C (&o)[V]) {
     uint32_t w[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      const __half2 h2 = __floats2half2_rn(o[2 * k] * kHalfScale, o[2 * k + 1] * kHalfScale);
+      const __half2 h2 = __floats2half2_rn(o[2 * k], o[2 * k + 1]);
       memcpy(&w[k], &h2, 4);
     }
     __stcs(reinterpret_cast<uint4*>(p), make_uint4(w[0], w[1], w[2], w[3]));
   }
-  __device__ static C ld1(const __half* p) { return __half2float(*p) * kHalfUnscale; }
+  __device__ static C ld1(const __half* p) { return __half2float(*p); }
+  __device__ static void st1r(__half* p, C v) { *p = __float2half_rn(v); }
   __device__ static C ldg1(const __half* p) { return __half2float(__ldg(p)) * kHalfUnscale; }
   __device__ static void st1(__half* p, C v) { *p = __float2half_rn(v * kHalfScale); }
   __device__ static __half cvt(C v) { return __float2half_rn(v * kHalfScale); }
@@ -140,9 +149,11 @@ struct Store<__nv_bfloat16> {
     }
     __stcs(reinterpret_cast<uint4*>(p), make_uint4(w[0], w[1], w[2], w[3]));
   }
+  static constexpr float kScale = 1.0f;
   __device__ static C ld1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
   __device__ static C ldg1(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
   __device__ static void st1(__nv_bfloat16* p, C v) { *p = __float2bfloat16_rn(v); }
+  __device__ static void st1r(__nv_bfloat16* p, C v) { *p = __float2bfloat16_rn(v); }
   __device__ static __nv_bfloat16 cvt(C v) { return __float2bfloat16_rn(v); }
 };
 
@@ -162,12 +173,13 @@ __device__ __forceinline__ void moments(const C (&h)[9], C& drho, C& jx, C& jy) 
   jy = (h[3] - h[4]) + (h[5] - h[6]) + (h[7] - h[8]);
 }
 
-// Shifted equilibrium h^eq_i at (d_rho, u), Eq. (feq_1) minus w_i.
+// Shifted equilibrium h^eq_i at (d_rho, u), Eq. (feq_1) minus w_i, times the
+// storage scale s (1 except for binary16 storage, where it folds into w_i).
 template <typename C>
-__device__ __forceinline__ void equilibrium(C drho, C ux, C uy, C (&e)[9]) {
+__device__ __forceinline__ void equilibrium(C drho, C ux, C uy, C (&e)[9], C s = C(1)) {
   const C rho = C(1) + drho;
   const C usq = C(1.5) * (ux * ux + uy * uy);
-  const C w0 = wt<C>(0), wa = wt<C>(1), wd = wt<C>(5);
+  const C w0 = wt<C>(0) * s, wa = wt<C>(1) * s, wd = wt<C>(5) * s;
   e[0] = w0 * (drho - rho * usq);
   // axis directions: c.u = +-ux, +-uy
   {
@@ -194,14 +206,18 @@ __device__ __forceinline__ void equilibrium(C drho, C ux, C uy, C (&e)[9]) {
   }
 }
 
-// BGK collision, Eq. (lbe_1) with dt = 1, on shifted populations.
+// BGK collision, Eq. (lbe_1) with dt = 1, on shifted populations held as
+// s * h (s = storage scale; the relaxation is linear in h, only the moments
+// need 1/s).
 template <typename C>
-__device__ __forceinline__ void collide_bgk(C (&h)[9], C omega) {
-  C drho, jx, jy;
-  moments(h, drho, jx, jy);
-  const C inv = C(1) / (C(1) + drho);
+__device__ __forceinline__ void collide_bgk(C (&h)[9], C omega, C s = C(1)) {
+  C sd, sjx, sjy;
+  moments(h, sd, sjx, sjy);
+  const C is = C(1) / s;
+  const C drho = sd * is;
+  const C inv = is / (C(1) + drho);
   C e[9];
-  equilibrium(drho, jx * inv, jy * inv, e);
+  equilibrium(drho, sjx * inv, sjy * inv, e, s);
 #pragma unroll
   for (int i = 0; i < 9; ++i) h[i] = h[i] + omega * (e[i] - h[i]);
 }
@@ -227,12 +243,14 @@ struct Rates {
 };
 
 template <typename C>
-__device__ __forceinline__ void collide_mrt(C (&h)[9], const Rates<C>& r) {
-  C drho, jx, jy;
-  moments(h, drho, jx, jy);
-  const C inv = C(1) / (C(1) + drho);
+__device__ __forceinline__ void collide_mrt(C (&h)[9], const Rates<C>& r, C s = C(1)) {
+  C sd, sjx, sjy;
+  moments(h, sd, sjx, sjy);
+  const C is = C(1) / s;
+  const C drho = sd * is;
+  const C inv = is / (C(1) + drho);
   C e[9];
-  equilibrium(drho, jx * inv, jy * inv, e);
+  equilibrium(drho, sjx * inv, sjy * inv, e, s);
   C n[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) n[i] = h[i] - e[i];
@@ -261,11 +279,11 @@ __device__ __forceinline__ void collide_mrt(C (&h)[9], const Rates<C>& r) {
 
 // Collision model: 0 = BGK (Eq. lbe_1), 1 = MRT (Eq. mrt_lbe).
 template <int MODEL, typename C>
-__device__ __forceinline__ void collide(C (&h)[9], const Rates<C>& r) {
+__device__ __forceinline__ void collide(C (&h)[9], const Rates<C>& r, C s = C(1)) {
   if constexpr (MODEL == 1)
-    collide_mrt(h, r);
+    collide_mrt(h, r, s);
   else
-    collide_bgk(h, r.omega);
+    collide_bgk(h, r.omega, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -317,6 +335,26 @@ __device__ __forceinline__ void node_moments_f64(const T* __restrict__ A, const 
   m[0] = rho;
   m[1] = jx / rho;
   m[2] = jy / rho;
+}
+
+// (rho - 1, ux, uy) at node (x, y) in the compute type of the storage: the
+// shifted populations keep d_rho free of cancellation, so float is exact to
+// float rounding of the perturbation itself.
+template <typename T>
+__device__ __forceinline__ void node_dmoments(const T* __restrict__ A, const Geom& g, int x, int y,
+                                              double (&m)[3]) {
+  using S = Store<T>;
+  using C = typename S::C;
+  const long long o = (long long)y * g.pitch + x;
+  C h[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) h[i] = S::ldg1(A + i * g.plane + o);
+  C drho, jx, jy;
+  moments(h, drho, jx, jy);
+  const C inv = C(1) / (C(1) + drho);
+  m[0] = (double)drho;
+  m[1] = (double)(jx * inv);
+  m[2] = (double)(jy * inv);
 }
 
 }  // namespace lbmk

@@ -112,7 +112,7 @@ __device__ __forceinline__ void bulk_row(const T* __restrict__ A, T* __restrict_
       h[6] = k == V - 1 ? r6 : v[6][k + 1];
       h[7] = k == V - 1 ? r7 : v[7][k + 1];
       h[8] = k == 0 ? l8 : v[8][k - 1];
-      collide<MODEL>(h, rates);
+      collide<MODEL>(h, rates, C(S::kScale));  // in stored units
 #pragma unroll
       for (int i = 0; i < 9; ++i) o[i][k] = h[i];
     }
@@ -126,7 +126,7 @@ __device__ __forceinline__ void bulk_row(const T* __restrict__ A, T* __restrict_
           const int x = x0 + k;
           if (x >= 1 && x <= g.nx - 2) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) S::st1(B + i * P + r0 + k, o[i][k]);
+            for (int i = 0; i < 9; ++i) S::st1r(B + i * P + r0 + k, o[i][k]);
           }
         }
       }
@@ -148,10 +148,11 @@ __global__ void __launch_bounds__(BX) bulk_kernel(const T* __restrict__ A, T* __
 
 // ---------------------------------------------------------------------------
 // NSBC: four lanes per perimeter node.  Lane q loads the node b - q n and
-// forms its moments in double (q = 0, 1, and 2 for the second-order
-// difference); lane 0 gathers them by shuffles within its quad, predicts
-// and blends m_c in double, then rebuilds, corrects and collides the node in
-// the compute type.
+// forms its moments (q = 0, 1, and 2 for the second-order difference) as
+// (rho - 1, ux, uy) in the compute type; lane 0 gathers them by shuffles
+// within its quad, predicts and blends m_c in double (the prediction is
+// linear, so predicting rho - 1 is predicting rho), then rebuilds, corrects
+// and collides the node in the compute type.
 // ---------------------------------------------------------------------------
 // Node `node` of the perimeter, handled by the four lanes of one quad
 // (q = lane & 3); all four lanes must call this together.
@@ -165,7 +166,7 @@ __device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict
   perimeter_node(node, g.nx, g.ny, x, y, nxn, nyn);
 
   double m[3] = {0.0, 0.0, 0.0};
-  if (q <= p.order) node_moments_f64(A, g, x - q * nxn, y - q * nyn, m);
+  if (q <= p.order) node_dmoments(A, g, x - q * nxn, y - q * nyn, m);
   double m1[3], m2[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -177,12 +178,13 @@ __device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict
   // Eq. (nes_2): m_p = m_b - gamma d_n m along the outward unit normal;
   // Eq. (nes_3): m_c = (1 - beta) m_p + beta m_0.
   const double len = (nxn != 0 && nyn != 0) ? 1.4142135623730951 : 1.0;
-  double mc[3];
+  const double m0[3] = {p.m0[0] - 1.0, p.m0[1], p.m0[2]};
+  double mc[3];  // (rho_c - 1, u_c)
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const double dn = p.order == 2 ? (3.0 * m[c] - 4.0 * m1[c] + m2[c]) / (2.0 * len) : (m[c] - m1[c]) / len;
     const double mp = m[c] - p.gamma * dn;
-    mc[c] = (1.0 - p.beta) * mp + p.beta * p.m0[c];
+    mc[c] = (1.0 - p.beta) * mp + p.beta * m0[c];
   }
 
   // pulled populations; unknown where the source lies outside the domain
@@ -196,7 +198,7 @@ __device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict
   }
 
   // Eqs. (nes_0), (nes_1): f_in = f_in^eq(m_c) + f_out - f_out^eq(m_c)
-  const C drho_c = C(mc[0] - 1.0);
+  const C drho_c = C(mc[0]);
   C e[9];
   equilibrium(drho_c, C(mc[1]), C(mc[2]), e);
 #pragma unroll
@@ -209,8 +211,8 @@ __device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict
   C drho, jx, jy;
   moments(h, drho, jx, jy);
   const C d_rho = drho - drho_c;
-  const C d_jx = jx - C(mc[0] * mc[1]);
-  const C d_jy = jy - C(mc[0] * mc[2]);
+  const C d_jx = jx - C((1.0 + mc[0]) * mc[1]);
+  const C d_jy = jy - C((1.0 + mc[0]) * mc[2]);
   const C kap = C(p.kappa);
 #pragma unroll
   for (int i = 0; i < 9; ++i) h[i] -= wt<C>(i) * (d_rho + kap * (C(cx(i)) * d_jx + C(cy(i)) * d_jy));
