@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--launch", default="", help="bulk launch shape 'threads_x,rows' instead of autotuning")
+    p.add_argument("--batched-only", action="store_true", help="time only the batched workload")
+    p.add_argument("--batch-launch", default="", help="batched launch 'threads_x,rows,blocks,prefetch'")
     return p.parse_args()
 
 
@@ -206,6 +208,78 @@ def run_reference(args, rank, world):
 
 # --- GPU arm ------------------------------------------------------------------
 
+def max_over_ranks(x: float, device: str) -> float:
+    """Largest value of x over the ranks of the default process group (the
+    whole job is as slow as its slowest rank)."""
+    import torch
+    import torch.distributed as td
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_mlups(cells_per_rank: int, steps: int, ms_max: float, world: int) -> float:
+    """Whole-job MLUPS: every rank advanced its own replica of `cells_per_rank`
+    nodes by `steps` steps; the job took the slowest rank's time."""
+    return world * cells_per_rank * steps / (ms_max * 1e-3) / 1e6
+
+
+BATCH_WHAT = ("256 instances 64..1024 per side, tau 0.51..0.8, pulses and vortices, "
+              "one persistent launch per step replayed from a CUDA graph")
+
+
+def run_batched(lbm, ws, bfields, storage, steps, warmup, world, peak, launch=None):
+    """The batched workload: MLUPS over all instances, CUDA events on the stream."""
+    import torch
+    bt = lbm.Batch(ws, storage=storage)
+    for k, f in enumerate(bfields):
+        bt.init(k, *f)
+    if launch:
+        tb, tr, tg, tp = launch
+        bt.set_launch(tb, tr, tg, tp)
+    else:
+        tb, tr, tg, tp, _ = bt.autotune()
+    bt.step(warmup)
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(bt.stream)
+    bt.step(steps)
+    a1.record(bt.stream)
+    torch.cuda.synchronize()
+    bms = a0.elapsed_time(a1)
+    bad = sum(bt.unstable_nodes(k) for k in range(len(ws)))
+    gbs = BYTES_PER_CELL[storage] * bt.cells * steps / (bms * 1e-3) / 1e9
+    out = {"mlups": world * bt.cells * steps / (bms * 1e-3) / 1e6, "steps": steps, "ms_per_step": bms / steps,
+           "instances": len(ws), "cells": bt.cells, "step_gbs": gbs, "step_frac": gbs / peak,
+           "launch": {"threads_x": tb, "rows": tr, "blocks": tg, "prefetch_rows": tp},
+           "unstable_nodes": bad, "what": BATCH_WHAT}
+    bt.close()
+    del bt
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched_only(args, rank, world, local_rank):
+    """--batched-only: the batched workload alone (for profiling runs)."""
+    import torch
+    from paper_2005_08674_gb300 import build
+    build.build()
+    from paper_2005_08674_gb300 import inputs, lbm
+    torch.cuda.set_device(local_rank)
+    ws = inputs.batch_instances()
+    bfields = [w.fields() for w in ws]
+    peak, _ = measured_peak_gbs()
+    launch = [int(v) for v in args.batch_launch.split(",")] if args.batch_launch else None
+    r = run_batched(lbm, ws, bfields, args.storage, args.steps, args.warmup, world, peak, launch)
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "value": r["mlups"], "unit": UNIT, "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                          "dtype": args.storage, "data": "synthetic",
+                          "config": {"workload": "batched: " + BATCH_WHAT}, "batched": r}), flush=True)
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -254,12 +328,8 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = world * cells * args.steps / (ms_max * 1e-3) / 1e6
+    ms_max = max_over_ranks(ms, "cuda") if dist else ms
+    value = aggregate_mlups(cells, args.steps, ms_max, world)
     out = sim.reduce(allow_unstable=True)
     stable = out[3] == 0
 
@@ -314,9 +384,7 @@ def run_ours(args, rank, world, local_rank):
         barrier()
         e2e_s = t1 - t0
         if dist:
-            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            td.all_reduce(t, op=td.ReduceOp.MAX)
-            e2e_s = float(t.item())
+            e2e_s = max_over_ranks(e2e_s, "cuda")
         if line is not None:
             nbytes = 3 * cells * 8
             line["e2e"] = {"value": world * cells * args.steps / e2e_s / 1e6, "unit": UNIT,
@@ -363,31 +431,7 @@ def run_ours(args, rank, world, local_rank):
         bfields = [w.fields() for w in ws]
         bsteps = min(args.steps, 1000)
         for st in ("f32", "f16"):
-            bt = lbm.Batch(ws, storage=st)
-            for k, f in enumerate(bfields):
-                bt.init(k, *f)
-            tb, tr, tg, tp, _ = bt.autotune()
-            bt.step(args.warmup)
-            torch.cuda.synchronize()
-            a0 = torch.cuda.Event(enable_timing=True)
-            a1 = torch.cuda.Event(enable_timing=True)
-            a0.record(bt.stream)
-            bt.step(bsteps)
-            a1.record(bt.stream)
-            torch.cuda.synchronize()
-            bms = a0.elapsed_time(a1)
-            bad = sum(bt.unstable_nodes(k) for k in range(len(ws)))
-            gbs = BYTES_PER_CELL[st] * bt.cells * bsteps / (bms * 1e-3) / 1e9
-            variants[f"batched_{st}"] = {
-                "mlups": world * bt.cells * bsteps / (bms * 1e-3) / 1e6, "steps": bsteps,
-                "instances": len(ws), "cells": bt.cells, "step_gbs": gbs, "step_frac": gbs / peak,
-                "launch": {"threads_x": tb, "rows": tr, "blocks": tg, "prefetch_rows": tp},
-                "unstable_nodes": bad,
-                "what": "256 instances 64..1024 per side, tau 0.51..0.8, pulses and vortices, "
-                        "one persistent launch per step replayed from a CUDA graph"}
-            bt.close()
-            del bt
-            torch.cuda.empty_cache()
+            variants[f"batched_{st}"] = run_batched(lbm, ws, bfields, st, bsteps, args.warmup, world, peak)
         del bfields
         if line is not None:
             line["variants"] = variants
@@ -412,7 +456,11 @@ def main():
         import torch.distributed as td
         torch.cuda.set_device(local_rank)
         td.init_process_group("nccl")
-    line = run_ours(args, rank, world, local_rank)
+    if args.batched_only:
+        run_batched_only(args, rank, world, local_rank)
+        line = None
+    else:
+        line = run_ours(args, rank, world, local_rank)
     if line is not None:
         print(json.dumps(line), flush=True)
     if world > 1:
