@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--launch", default="", help="bulk launch shape 'threads_x,rows' instead of autotuning")
     p.add_argument("--batched-only", action="store_true", help="time only the batched workload")
-    p.add_argument("--batch-launch", default="", help="batched launch 'threads_x,rows,blocks,prefetch'")
+    p.add_argument("--batch-launch", default="", help="batched launch 'threads_x,rows,blocks,prefetch,split'")
     return p.parse_args()
 
 
@@ -235,10 +235,10 @@ def run_batched(lbm, ws, bfields, storage, steps, warmup, world, peak, launch=No
     for k, f in enumerate(bfields):
         bt.init(k, *f)
     if launch:
-        tb, tr, tg, tp = launch
-        bt.set_launch(tb, tr, tg, tp)
+        tb, tr, tg, tp, ts = (list(launch) + [0])[:5]
+        bt.set_launch(tb, tr, tg, tp, ts)
     else:
-        tb, tr, tg, tp, _ = bt.autotune()
+        tb, tr, tg, tp, ts, _ = bt.autotune()
     bt.step(warmup)
     torch.cuda.synchronize()
     a0 = torch.cuda.Event(enable_timing=True)
@@ -252,7 +252,7 @@ def run_batched(lbm, ws, bfields, storage, steps, warmup, world, peak, launch=No
     gbs = BYTES_PER_CELL[storage] * bt.cells * steps / (bms * 1e-3) / 1e9
     out = {"mlups": world * bt.cells * steps / (bms * 1e-3) / 1e6, "steps": steps, "ms_per_step": bms / steps,
            "instances": len(ws), "cells": bt.cells, "step_gbs": gbs, "step_frac": gbs / peak,
-           "launch": {"threads_x": tb, "rows": tr, "blocks": tg, "prefetch_rows": tp},
+           "launch": {"threads_x": tb, "rows": tr, "blocks": tg, "prefetch_rows": tp, "split": ts},
            "unstable_nodes": bad, "what": BATCH_WHAT}
     bt.close()
     del bt

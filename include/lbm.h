@@ -239,17 +239,21 @@ int lbm_batch_get_macros(lbm_batch_t* b, int32_t k, double* rho, double* ux, dou
 /* Number of nodes of instance k with non-finite or non-positive density
  * (FP64 reduction); synchronises. */
 int lbm_batch_unstable_nodes(lbm_batch_t* b, int32_t k, int64_t* count);
-/* Tile shape: threads per block along x (64, 128, 256) times the storage's
- * 16-byte vector of nodes per thread, `rows` rows per tile (nodes per thread
- * = vector x rows); grid size `blocks` (-1 = one block per work item,
+/* Work split: a bulk tile is threads_x (64, 128, 256) x `rows` (1, 2, 4)
+ * 16-byte vectors of an instance's interior rows laid end to end (nodes per
+ * thread = vector x rows); grid size `blocks` (-1 = one block per work item,
  * 0 = one resident wave of blocks looping over the list, > 0 = that many);
- * L2 prefetch distance in rows inside tiles (0 = off, at most 64). */
-int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_t blocks, int32_t prefetch_rows);
-/* Time every compiled tile shape, grid size and prefetch distance on the
- * batch's own state (restored afterwards, through a temporary device copy
- * from cudaMallocAsync) and keep the fastest. */
+ * `prefetch_rows` > 0 lets each warp pull its next tile segment into L2
+ * (at most 64); `split` = 0 runs NSBC chunks and bulk tiles in ONE launch
+ * per step, 1 runs the NSBC chunks as a second launch beside the bulk tiles
+ * (the bulk launch then keeps the single-domain kernel's register budget). */
+int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_t blocks, int32_t prefetch_rows,
+                         int32_t split);
+/* Time every compiled tile shape, grid size, prefetch setting and split on
+ * the batch's own state (restored afterwards, through a temporary device
+ * copy from cudaMallocAsync) and keep the fastest. */
 int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_t* blocks, int32_t* prefetch_rows,
-                       double* ms_per_step);
+                       int32_t* split, double* ms_per_step);
 
 /* Per-launch timing.  While enabled, lbm_step launches every step directly
  * (no graph) on the handle's stream with CUDA events around the bulk

@@ -3,10 +3,12 @@
 //
 // Every instance keeps its own 9-plane layout (pitch = nx rounded up to 64,
 // planes 256-byte aligned) inside two shared pools A and B.  A work list of
-// int4 items drives the persistent kernel: bulk tiles (instance, first row,
-// first x, rows) of threads_x * V nodes by `rows` rows, then NSBC chunks
-// (~instance, first perimeter node, count) of threads_x / 4 nodes.  Blocks
-// take items round-robin; bulk tiles and NSBC chunks of one step read only
+// int4 items drives the kernel: NSBC chunks (~instance, first perimeter
+// node, count) of threads_x / 4 nodes, then bulk tiles (instance, first
+// vector, count) of up to threads_x * rows 16-byte vectors of the instance's
+// interior rows flattened end to end (so narrow instances leave no lanes
+// idle; a warp may straddle two rows).  Blocks take items round-robin (or
+// one item each); bulk tiles and NSBC chunks of one step read only
 // pool A and write disjoint nodes of pool B, so no synchronisation is needed
 // inside the launch.  Each item runs the same device code as the single-domain
 // kernels (bulk_row, nsbc_node), so an instance's results are bit-identical
@@ -17,6 +19,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <type_traits>
 #include <vector>
 
 #include "lbm.h"
@@ -80,6 +83,9 @@ struct lbm_batch {
   int n_items = 0, n_bulk_items = 0;
   int bx = 128, rows = 1, blocks = -1;  // blocks: -1 one per item, 0 one resident wave, > 0 as given
   int pf = 0;                           // L2 prefetch distance in rows inside bulk tiles
+  bool split = false;                   // NSBC chunks in their own concurrent launch
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int wave = 1;                        // resident blocks on the device for the current shape
   bool items_dirty = true;
   std::vector<char> initialised;
@@ -102,27 +108,62 @@ void bdispatch(int storage, F&& f) {
   }
 }
 
-template <typename T, int BX, int MODEL>
+// PART 0: the whole work list in one launch (NSBC chunks and bulk tiles);
+// PART 1: bulk tiles only; PART 2: NSBC chunks only (the split schedule runs
+// 1 and 2 as two concurrent launches, so the bulk launch keeps the register
+// budget -- and occupancy -- of the single-domain bulk kernel).
+template <typename T, int BX, int MODEL, int PART>
 __global__ void __launch_bounds__(BX) batch_step_kernel(const T* __restrict__ A, T* __restrict__ B,
                                                         const InstDev* __restrict__ inst,
-                                                        const int4* __restrict__ items, int n_items, lbmk::Nsbc p,
-                                                        double s_e, double s_eps, double s_q, int pf) {
+                                                        const int4* __restrict__ items, int i0, int i1,
+                                                        lbmk::Nsbc p, double s_e, double s_eps, double s_q, int pf) {
   using C = typename lbmk::Store<T>::C;
   constexpr int V = lbmk::Store<T>::V;
   const int lane = threadIdx.x & 31;
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+  for (int it = i0 + blockIdx.x; it < i1; it += gridDim.x) {
     const int4 w = items[it];
-    const bool edge = w.x < 0;
+    const bool edge = PART == 2 || (PART == 0 && w.x < 0);
     const InstDev d = inst[edge ? ~w.x : w.x];
     const lbmk::Geom g{d.nx, d.ny, d.pitch, d.plane};
     const lbmk::Rates<C> r{C(d.omega), C(s_e), C(s_eps), C(s_q)};
     const T* a = A + d.off;
     T* b = B + d.off;
-    if (!edge) {
-      const int x0 = w.z + (int)threadIdx.x * V;
-      const unsigned pfb = lbmk::warp_segment_bytes<T>(g, x0 - lane * V);
-      for (int y = w.y; y < w.y + w.w; ++y) lbmk::bulk_row<T, MODEL>(a, b, g, r, y, x0, lane, pf, pfb);
-    } else {
+    if constexpr (PART != 2) {
+      if (!edge) {
+        // the instance's interior rows 1..ny-2 flattened into one sequence of
+        // 16-byte vectors, nvec per row; this item is vectors [w.y, w.y + w.z)
+        const int nvec = (d.nx + V - 1) / V;
+        const int warp0 = (int)threadIdx.x - lane;
+        for (int base = 0; base < w.z; base += BX) {
+          const int jr = base + (int)threadIdx.x;
+          const bool valid = jr < w.z;
+          const int j = w.y + (valid ? jr : 0);
+          const int yy = 1 + j / nvec;
+          const int x0 = (j - (yy - 1) * nvec) * V;
+          if (pf > 0 && lane == 0 && base + BX + warp0 < w.z) {
+            // next pass of this warp: pull its first row segment into L2
+            const int jn = w.y + base + BX + warp0;
+            const int yn = 1 + jn / nvec;
+            const int cn = jn - (yn - 1) * nvec;
+            const unsigned bytes = (unsigned)(min(32, nvec - cn) * 16);
+            const long long q0 = (long long)yn * g.pitch + (long long)cn * V;
+            const long long P = g.plane;
+            lbmk::prefetch_l2(a + 0 * P + q0, bytes);
+            lbmk::prefetch_l2(a + 1 * P + q0, bytes);
+            lbmk::prefetch_l2(a + 2 * P + q0, bytes);
+            lbmk::prefetch_l2(a + 3 * P + q0 - g.pitch, bytes);
+            lbmk::prefetch_l2(a + 4 * P + q0 + g.pitch, bytes);
+            lbmk::prefetch_l2(a + 5 * P + q0 - g.pitch, bytes);
+            lbmk::prefetch_l2(a + 6 * P + q0 + g.pitch, bytes);
+            lbmk::prefetch_l2(a + 7 * P + q0 - g.pitch, bytes);
+            lbmk::prefetch_l2(a + 8 * P + q0 + g.pitch, bytes);
+          }
+          lbmk::bulk_row<T, MODEL>(a, b, g, r, yy, x0, lane, 0, 0u, valid);
+        }
+        continue;
+      }
+    }
+    if constexpr (PART != 1) {
       lbmk::Nsbc q = p;
       q.m0[0] = d.m0[0];
       q.m0[1] = d.m0[1];
@@ -133,46 +174,72 @@ __global__ void __launch_bounds__(BX) batch_step_kernel(const T* __restrict__ A,
   }
 }
 
-template <typename T, int BX>
+template <typename T, int BX, int PART>
 const void* kernel_ptr(int model) {
-  return model == 1 ? (const void*)batch_step_kernel<T, BX, 1> : (const void*)batch_step_kernel<T, BX, 0>;
+  return model == 1 ? (const void*)batch_step_kernel<T, BX, 1, PART> : (const void*)batch_step_kernel<T, BX, 0, PART>;
 }
 
-template <typename T, int BX>
-void launch_batch_bx(const lbm_batch_t* b, int from, cudaStream_t s, int grid) {
+template <typename T, int BX, int PART>
+void launch_part(const lbm_batch_t* b, int from, cudaStream_t s, int grid, int i0, int i1) {
   const T* A = static_cast<const T*>(b->pool[from]);
   T* B = static_cast<T*>(b->pool[1 - from]);
   if (b->collision == 1)
-    batch_step_kernel<T, BX, 1><<<grid, BX, 0, s>>>(A, B, b->d_inst, b->d_items, b->n_items, b->nsbc, b->s_e,
-                                                    b->s_eps, b->s_q, b->pf);
+    batch_step_kernel<T, BX, 1, PART><<<grid, BX, 0, s>>>(A, B, b->d_inst, b->d_items, i0, i1, b->nsbc, b->s_e,
+                                                          b->s_eps, b->s_q, b->pf);
   else
-    batch_step_kernel<T, BX, 0><<<grid, BX, 0, s>>>(A, B, b->d_inst, b->d_items, b->n_items, b->nsbc, b->s_e,
-                                                    b->s_eps, b->s_q, b->pf);
+    batch_step_kernel<T, BX, 0, PART><<<grid, BX, 0, s>>>(A, B, b->d_inst, b->d_items, i0, i1, b->nsbc, b->s_e,
+                                                          b->s_eps, b->s_q, b->pf);
 }
 
-// resident blocks per SM for the current shape
+template <typename F>
+void with_bx(int bx, F&& f) {
+  switch (bx) {
+    case 64: f(std::integral_constant<int, 64>{}); break;
+    case 256: f(std::integral_constant<int, 256>{}); break;
+    default: f(std::integral_constant<int, 128>{}); break;
+  }
+}
+
+// resident blocks on the device for the launch that carries the bulk tiles
 int wave_blocks(const lbm_batch_t* b) {
   int per_sm = 0, sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
   bdispatch(b->storage, [&](auto tag) {
     using T = decltype(tag);
-    const void* k = b->bx == 64 ? kernel_ptr<T, 64>(b->collision)
-                                : (b->bx == 256 ? kernel_ptr<T, 256>(b->collision) : kernel_ptr<T, 128>(b->collision));
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, b->bx, 0);
+    with_bx(b->bx, [&](auto bxc) {
+      constexpr int BX = decltype(bxc)::value;
+      const void* k = b->split ? kernel_ptr<T, BX, 1>(b->collision) : kernel_ptr<T, BX, 0>(b->collision);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BX, 0);
+    });
   });
   return std::max(1, per_sm) * std::max(1, sms);
 }
 
-void enqueue_batch_step(const lbm_batch_t* b, int from, cudaStream_t s) {
+int grid_for_items(const lbm_batch_t* b, int n) {
   // blocks < 0: one block per work item; 0: one resident wave; > 0: as given
-  const int grid = std::max(1, b->blocks < 0 ? b->n_items : std::min(b->n_items, b->blocks > 0 ? b->blocks : b->wave));
+  return std::max(1, b->blocks < 0 ? n : std::min(n, b->blocks > 0 ? b->blocks : b->wave));
+}
+
+// One step from pool `from`.  Fused: one launch over the whole list.  Split:
+// the NSBC chunks on the side stream beside the bulk tiles (fork/join events,
+// captured as two parallel graph nodes).
+void enqueue_batch_step(const lbm_batch_t* b, int from, cudaStream_t s) {
   bdispatch(b->storage, [&](auto tag) {
     using T = decltype(tag);
-    switch (b->bx) {
-      case 64: launch_batch_bx<T, 64>(b, from, s, grid); break;
-      case 256: launch_batch_bx<T, 256>(b, from, s, grid); break;
-      default: launch_batch_bx<T, 128>(b, from, s, grid); break;
-    }
+    with_bx(b->bx, [&](auto bxc) {
+      constexpr int BX = decltype(bxc)::value;
+      if (!b->split) {
+        launch_part<T, BX, 0>(b, from, s, grid_for_items(b, b->n_items), 0, b->n_items);
+      } else {
+        const int n_edge = b->n_items - b->n_bulk_items;
+        cudaEventRecord(b->ev_fork, s);
+        cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+        launch_part<T, BX, 2>(b, from, b->side, std::max(1, n_edge), 0, n_edge);
+        launch_part<T, BX, 1>(b, from, s, grid_for_items(b, b->n_bulk_items), n_edge, b->n_items);
+        cudaEventRecord(b->ev_join, b->side);
+        cudaStreamWaitEvent(s, b->ev_join, 0);
+      }
+    });
   });
 }
 
@@ -205,9 +272,10 @@ int build_items(lbm_batch_t* b) {
   const int n_edge = (int)items.size();
   for (int k : order) {
     const InstDev& d = b->inst[k];
-    const int tile_x = b->bx * V;
-    for (int y0 = 1; y0 <= d.ny - 2; y0 += b->rows)
-      for (int x0 = 0; x0 < d.nx; x0 += tile_x) items.push_back(make_int4(k, y0, x0, std::min(b->rows, d.ny - 1 - y0)));
+    const int nvec = (d.nx + V - 1) / V;
+    const int total = (d.ny - 2) * nvec;  // interior rows flattened into 16-byte vectors
+    const int per_item = b->bx * b->rows;
+    for (int j0 = 0; j0 < total; j0 += per_item) items.push_back(make_int4(k, j0, std::min(per_item, total - j0), 0));
   }
   const int n_bulk = (int)items.size() - n_edge;
   if (b->d_items) cudaFree(b->d_items);
@@ -237,6 +305,16 @@ int ensure_batch_memory(lbm_batch_t* b) {
   if (!b->d_inst) {
     BATCH_CUDA(cudaMalloc(&b->d_inst, b->inst.size() * sizeof(InstDev)));
     BATCH_CUDA(cudaMemcpy(b->d_inst, b->inst.data(), b->inst.size() * sizeof(InstDev), cudaMemcpyHostToDevice));
+  }
+  return LBM_OK;
+}
+
+int ensure_batch_streams(lbm_batch_t* b) {
+  if (!b->cap) {
+    BATCH_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+    BATCH_CUDA(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+    BATCH_CUDA(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+    BATCH_CUDA(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
   }
   return LBM_OK;
 }
@@ -323,6 +401,9 @@ void lbm_batch_destroy(lbm_batch_t* b) {
   cudaFree(b->d_inst);
   cudaFree(b->d_items);
   if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->side) cudaStreamDestroy(b->side);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
   delete b;
 }
 
@@ -419,7 +500,8 @@ int lbm_batch_step(lbm_batch_t* b, int32_t n) {
     if (!b->initialised[k]) return bfail(LBM_ESTATE, "lbm_batch_step: instance %d not initialised", k);
   int rc = build_items(b);
   if (rc) return rc;
-  if (!b->cap) BATCH_CUDA(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
+  rc = ensure_batch_streams(b);
+  if (rc) return rc;
   int left = n;
   if (left >= kBatchGraphSteps) {
     if (!b->graph[b->cur]) {
@@ -493,26 +575,30 @@ int lbm_batch_unstable_nodes(lbm_batch_t* b, int32_t k, int64_t* count) {
   return LBM_OK;
 }
 
-int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_t blocks, int32_t prefetch_rows) {
+int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_t blocks, int32_t prefetch_rows,
+                         int32_t split) {
   if (!b) return bfail(LBM_EINVAL, "lbm_batch_set_launch: NULL handle");
   if (!batch_shape_ok(threads_x, rows)) return bfail(LBM_EINVAL, "lbm_batch_set_launch: shape (%d, %d) not compiled", threads_x, rows);
   if (blocks < -1) return bfail(LBM_EINVAL, "lbm_batch_set_launch: blocks=%d < -1", blocks);
   if (prefetch_rows < 0 || prefetch_rows > 64)
     return bfail(LBM_EINVAL, "lbm_batch_set_launch: prefetch_rows=%d outside [0, 64]", prefetch_rows);
-  if (threads_x != b->bx || rows != b->rows) b->items_dirty = true;
+  if (threads_x != b->bx || rows != b->rows || (split != 0) != b->split) b->items_dirty = true;
   b->bx = threads_x;
   b->rows = rows;
   b->blocks = blocks;
   b->pf = prefetch_rows;
+  b->split = split != 0;
   drop_batch_graphs(b);
   return LBM_OK;
 }
 
 int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_t* blocks, int32_t* prefetch_rows,
-                       double* ms_per_step) {
+                       int32_t* split, double* ms_per_step) {
   if (!b) return bfail(LBM_EINVAL, "lbm_batch_autotune: NULL handle");
   for (int k = 0; k < b->count; ++k)
     if (!b->initialised[k]) return bfail(LBM_ESTATE, "lbm_batch_autotune: instance %d not initialised", k);
+  int rcs = ensure_batch_streams(b);
+  if (rcs) return rcs;
   // keep the state: current pool copied aside and restored
   const size_t pb = lbm_batch_buffer_bytes(b);
   void* backup = nullptr;
@@ -524,11 +610,14 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
   const int reps = (int)std::max<long long>(4, std::min<long long>(32, (1LL << 28) / std::max(b->cells, 1LL)));
   float best = 1e30f;
   int bb = b->bx, br = b->rows, bk = b->blocks, bp = b->pf;
+  bool bs = b->split;
   int rc = LBM_OK;
+  for (int split : {0, 1})
   for (int bx : kBatchBX)
     for (int r : kBatchRows) {
       b->bx = bx;
       b->rows = r;
+      b->split = split != 0;
       b->items_dirty = true;
       rc = build_items(b);
       if (rc) break;
@@ -550,6 +639,7 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
             br = r;
             bk = b->blocks;
             bp = pf;
+            bs = b->split;
           }
         }
     }
@@ -558,6 +648,7 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
   b->rows = br;
   b->blocks = bk;
   b->pf = bp;
+  b->split = bs;
   b->items_dirty = true;
   int rc2 = build_items(b);
   BATCH_CUDA(cudaMemcpyAsync(b->pool[b->cur], backup, pb, cudaMemcpyDeviceToDevice, b->stream));
@@ -571,6 +662,7 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
   if (rows) *rows = br;
   if (blocks) *blocks = bk;
   if (prefetch_rows) *prefetch_rows = bp;
+  if (split) *split = bs ? 1 : 0;
   if (ms_per_step) *ms_per_step = best;
   return LBM_OK;
 }

@@ -32,19 +32,23 @@ __device__ __forceinline__ unsigned warp_segment_bytes(const Geom& g, int warp_x
   return (unsigned)(min(32 * Store<T>::V, g.pitch - warp_x0) * (int)sizeof(T)) & ~15u;
 }
 
-// One interior row y of the warp's segment: lane owns nodes x0..x0+V-1.
-// Every lane of the warp must call this (shuffles).  L2 prefetch distance pf
-// in rows (0 = off): lane 0 asks the bulk-copy engine to pull the warp's
-// segments of row y + pf into L2, so more bytes are in flight than the
-// registers of the resident warps hold.
+// Interior nodes x0..x0+V-1 of row y for this lane.  Every lane of the warp
+// must call this (shuffles).  Lanes normally share y and hold consecutive
+// vectors; a lane may also sit on the next row (the batched kernel flattens
+// rows): the neighbour value it then gets from the shuffle belongs to a node
+// it never stores (x = 0 or x = nx - 1), so it is harmless.  `valid` = false
+// makes the lane load and store nothing.  L2 prefetch distance pf in rows
+// (0 = off, only with a row shared by the warp): lane 0 asks the bulk-copy
+// engine to pull the warp's segments of row y + pf into L2, so more bytes
+// are in flight than the registers of the resident warps hold.
 template <typename T, int MODEL>
 __device__ __forceinline__ void bulk_row(const T* __restrict__ A, T* __restrict__ B, const Geom& g,
                                          const Rates<typename Store<T>::C>& rates, int y, int x0, int lane,
-                                         int pf, unsigned pf_bytes) {
+                                         int pf, unsigned pf_bytes, bool valid = true) {
   using S = Store<T>;
   using C = typename S::C;
   constexpr int V = S::V;
-  const bool active = x0 < g.nx;
+  const bool active = valid && x0 < g.nx;
   const long long P = g.plane;
   const int warp_x0 = x0 - lane * V;
   {
@@ -94,7 +98,7 @@ __device__ __forceinline__ void bulk_row(const T* __restrict__ A, T* __restrict_
       l5 = S::ld1(A + 5 * P + rm - 1);
       l8 = S::ld1(A + 8 * P + rp - 1);
     }
-    if (lane == 31 && x0 + V < g.nx) {
+    if (lane == 31 && active && x0 + V < g.nx) {
       r2 = S::ld1(A + 2 * P + r0 + V);
       r6 = S::ld1(A + 6 * P + rp + V);
       r7 = S::ld1(A + 7 * P + rm + V);

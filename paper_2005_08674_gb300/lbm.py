@@ -74,8 +74,8 @@ _SIGS = {
     "lbm_batch_steps_done": (ctypes.c_int64, [_vp]),
     "lbm_batch_get_macros": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp]),
     "lbm_batch_unstable_nodes": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(ctypes.c_int64)]),
-    "lbm_batch_set_launch": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32]),
-    "lbm_batch_autotune": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _dp]),
+    "lbm_batch_set_launch": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32, _i32]),
+    "lbm_batch_autotune": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p, _dp]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -419,17 +419,18 @@ def lbm_batch_unstable_nodes(b, k) -> int:
     return c.value
 
 
-def lbm_batch_set_launch(b, threads_x: int, rows: int, blocks: int = -1, prefetch_rows: int = 0):
-    return _check(_L.lbm_batch_set_launch(b, threads_x, rows, blocks, prefetch_rows))
+def lbm_batch_set_launch(b, threads_x: int, rows: int, blocks: int = -1, prefetch_rows: int = 0,
+                         split: int = 0):
+    return _check(_L.lbm_batch_set_launch(b, threads_x, rows, blocks, prefetch_rows, split))
 
 
 def lbm_batch_autotune(b):
-    """(threads_x, rows, blocks, prefetch_rows, ms_per_step) of the fastest batched launch."""
-    bx, rows, blk, pf, ms = (ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(),
-                             ctypes.c_double())
+    """(threads_x, rows, blocks, prefetch_rows, split, ms_per_step) of the fastest batched launch."""
+    bx, rows, blk, pf, sp, ms = (ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(),
+                                 ctypes.c_int32(), ctypes.c_double())
     _check(_L.lbm_batch_autotune(b, ctypes.byref(bx), ctypes.byref(rows), ctypes.byref(blk), ctypes.byref(pf),
-                                 ctypes.byref(ms)))
-    return bx.value, rows.value, blk.value, pf.value, ms.value
+                                 ctypes.byref(sp), ctypes.byref(ms)))
+    return bx.value, rows.value, blk.value, pf.value, sp.value, ms.value
 
 
 class Batch:
@@ -500,6 +501,6 @@ class Batch:
     def autotune(self):
         return lbm_batch_autotune(self.b)
 
-    def set_launch(self, threads_x, rows, blocks=-1, prefetch_rows=0):
-        lbm_batch_set_launch(self.b, threads_x, rows, blocks, prefetch_rows)
+    def set_launch(self, threads_x, rows, blocks=-1, prefetch_rows=0, split=0):
+        lbm_batch_set_launch(self.b, threads_x, rows, blocks, prefetch_rows, split)
         return self
