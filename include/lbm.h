@@ -78,6 +78,22 @@ void lbm_destroy(lbm_t* h);
  * Returns LBM_EINVAL for grad_order not in {1, 2} or non-finite values. */
 int lbm_set_nsbc(lbm_t* h, double gamma, double beta, double kappa, int32_t grad_order);
 
+/* Edge types, per side in the order left (x = 0), right (x = nx-1), bottom
+ * (y = 0), top (y = ny-1).  LBM_EDGE_NSBC (default): the boundary of Sec. 5.
+ * LBM_EDGE_PERIODIC: the axis wraps (both sides of an axis together).
+ * LBM_EDGE_VELOCITY: a Dirichlet velocity edge (the paper's vortex test uses
+ * one on its inflow side and only cites the scheme): the same reconstruction
+ * as the NSBC with the velocity of m_c replaced by the prescribed
+ * (uw[2 side], uw[2 side + 1]) and the density still predicted by Eq. nes_2,
+ * so the correction of Eq. nes_4 leaves exactly that velocity on the node;
+ * at a corner a left/right velocity edge wins over a bottom/top one.
+ * uw may be NULL when no side is a velocity edge.  LBM_EINVAL for unknown
+ * types, unpaired periodic sides or non-finite velocities. */
+#define LBM_EDGE_NSBC 0
+#define LBM_EDGE_PERIODIC 1
+#define LBM_EDGE_VELOCITY 2
+int lbm_set_edges(lbm_t* h, const int32_t types[4], const double uw[8]);
+
 /* Collision model (bulk and boundary nodes alike).  LBM_BGK (default):
  * Eq. lbe_1 with rate 1/tau.  LBM_MRT: Eq. mrt_lbe with the Gram-Schmidt
  * moment basis of Sec. 4 and S = diag(-, omega_e, omega_eps, -, omega_q, -,
@@ -219,6 +235,8 @@ lbm_batch_t* lbm_batch_create(int32_t count, const lbm_instance_desc* descs, int
 void lbm_batch_destroy(lbm_batch_t* b);
 int lbm_batch_set_nsbc(lbm_batch_t* b, double gamma, double beta, double kappa, int32_t grad_order);
 int lbm_batch_set_collision(lbm_batch_t* b, int32_t model, double omega_e, double omega_eps, double omega_q);
+/* Edge types for every instance of the batch, as lbm_set_edges. */
+int lbm_batch_set_edges(lbm_batch_t* b, const int32_t types[4], const double uw[8]);
 int lbm_batch_set_stream(lbm_batch_t* b, void* cuda_stream);
 /* Total nodes over all instances. */
 int64_t lbm_batch_cells(const lbm_batch_t* b);
@@ -243,8 +261,9 @@ int lbm_batch_unstable_nodes(lbm_batch_t* b, int32_t k, int64_t* count);
  * 16-byte vectors of an instance's interior rows laid end to end (nodes per
  * thread = vector x rows); grid size `blocks` (-1 = one block per work item,
  * 0 = one resident wave of blocks looping over the list, > 0 = that many);
- * `prefetch_rows` > 0 lets each warp pull its next tile segment into L2
- * (at most 64); `split` = 0 runs NSBC chunks and bulk tiles in ONE launch
+ * `prefetch_rows`: 0 = off, 1 = each tile asks the bulk-copy engine for its
+ * whole footprint in L2 when it starts, k > 1 = each warp pulls the vectors
+ * it meets k passes later (at most 64); `split` = 0 runs NSBC chunks and bulk tiles in ONE launch
  * per step, 1 runs the NSBC chunks as a second launch beside the bulk tiles
  * (the bulk launch then keeps the single-domain kernel's register budget). */
 int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_t blocks, int32_t prefetch_rows,

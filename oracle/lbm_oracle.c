@@ -75,7 +75,9 @@ typedef struct or_sim {
   double beta;        /* far-field factor, Eq. (nes_3) */
   double kappa;       /* momentum factor of the correction, Eq. (nes_4) */
   int grad_order;     /* 1 or 2: one-sided difference order for d_n m */
-  int periodic[2];    /* test-only periodic axes (x, y) instead of NSBC edges */
+  int periodic[2];    /* periodic axes (x, y) instead of NSBC edges */
+  int velocity[4];    /* edges (left, right, bottom, top) with a prescribed velocity */
+  double uw[4][2];    /* that velocity */
   int collision;      /* 0 = BGK (Eq. lbe_1), 1 = MRT (Eq. mrt_lbe) */
   double mrt_s[9];    /* diagonal of S, Eq. (mrt_rm) */
   double M[9][9];     /* Gram-Schmidt moment matrix, Eq. (mrt_vm) */
@@ -172,6 +174,23 @@ static void nsbc(const or_sim* s, int x, int y, double g[9], const int known[9])
   }
   /* Eq. (nes_3): far-field criterion */
   for (int c = 0; c < 3; ++c) mc[c] = (1.0 - s->beta) * mp[c] + s->beta * s->m0[c];
+
+  /* A velocity (Dirichlet) edge: the paper only cites its scheme.  Reading
+   * taken: the same reconstruction with the velocity of m_c replaced by the
+   * prescribed one (density still predicted), so after the correction the
+   * node carries exactly that velocity.  At a corner the left/right edge's
+   * velocity wins over the bottom/top one. */
+  {
+    int side = -1;
+    if (x == 0 && s->velocity[0]) side = 0;
+    else if (x == s->nx - 1 && s->velocity[1]) side = 1;
+    else if (y == 0 && s->velocity[2]) side = 2;
+    else if (y == s->ny - 1 && s->velocity[3]) side = 3;
+    if (side >= 0) {
+      mc[1] = s->uw[side][0];
+      mc[2] = s->uw[side][1];
+    }
+  }
 
   /* Eqs. (nes_0), (nes_1): f_in = f_in^eq + f_out^neq, both equilibria at m_c */
   double feq[9];
@@ -284,6 +303,14 @@ void or_set_nsbc(or_sim* s, double gamma, double beta, double kappa, int grad_or
 void or_set_periodic(or_sim* s, int px, int py) {
   s->periodic[0] = px != 0;
   s->periodic[1] = py != 0;
+}
+
+/* side: 0 left (x = 0), 1 right, 2 bottom (y = 0), 3 top; on = 0 restores NSBC */
+void or_set_velocity_edge(or_sim* s, int side, int on, double ux, double uy) {
+  if (side < 0 || side > 3) return;
+  s->velocity[side] = on != 0;
+  s->uw[side][0] = ux;
+  s->uw[side][1] = uy;
 }
 
 /* collision = 0: BGK; collision = 1: MRT with the diagonal s[9] of Eq. (mrt_rm) */

@@ -26,6 +26,7 @@
 #include "lbm_kernels.cuh"
 
 int lbm_internal_fail(int code, const char* msg);
+int lbm_internal_set_edges(lbmk::Nsbc* p, const int32_t types[4], const double uw[8]);
 
 namespace {
 
@@ -134,15 +135,31 @@ __global__ void __launch_bounds__(BX) batch_step_kernel(const T* __restrict__ A,
         // 16-byte vectors, nvec per row; this item is vectors [w.y, w.y + w.z)
         const int nvec = (d.nx + V - 1) / V;
         const int warp0 = (int)threadIdx.x - lane;
+        if (pf == 1 && lane == 0) {
+          // whole-tile prefetch: the tile's vectors span one contiguous address
+          // range per plane (rows plus their padding); warp k asks the
+          // bulk-copy engine for planes k, k + BX/32, ... so every load of the
+          // later passes finds its line already in L2
+          const int ja = w.y, jb = w.y + w.z - 1;
+          const int ya = 1 + ja / nvec, yb = 1 + jb / nvec;
+          const long long a0 = (long long)ya * g.pitch + (long long)(ja - (ya - 1) * nvec) * V;
+          const long long a1 = (long long)yb * g.pitch + (long long)(jb - (yb - 1) * nvec + 1) * V;
+          const unsigned bytes = (unsigned)((a1 - a0) * (long long)sizeof(T));
+          for (int pl = warp0 / 32; pl < 9; pl += BX / 32) {
+            const long long sh = (pl == 3 || pl == 5 || pl == 7) ? -g.pitch : ((pl == 4 || pl == 6 || pl == 8) ? g.pitch : 0);
+            lbmk::prefetch_l2(a + pl * g.plane + a0 + sh, bytes);
+          }
+        }
         for (int base = 0; base < w.z; base += BX) {
           const int jr = base + (int)threadIdx.x;
           const bool valid = jr < w.z;
           const int j = w.y + (valid ? jr : 0);
           const int yy = 1 + j / nvec;
           const int x0 = (j - (yy - 1) * nvec) * V;
-          if (pf > 0 && lane == 0 && base + BX + warp0 < w.z) {
-            // next pass of this warp: pull its first row segment into L2
-            const int jn = w.y + base + BX + warp0;
+          if (pf > 1 && lane == 0 && w.y + base + pf * BX + warp0 < (d.ny - 2) * nvec) {
+            // the vectors this warp would meet pf passes later (possibly in
+            // the instance's next tile): pull their first row segment into L2
+            const int jn = w.y + base + pf * BX + warp0;
             const int yn = 1 + jn / nvec;
             const int cn = jn - (yn - 1) * nvec;
             const unsigned bytes = (unsigned)(min(32, nvec - cn) * 16);
@@ -440,6 +457,16 @@ int lbm_batch_set_nsbc(lbm_batch_t* b, double gamma, double beta, double kappa, 
   return LBM_OK;
 }
 
+int lbm_batch_set_edges(lbm_batch_t* b, const int32_t types[4], const double uw[8]) {
+  if (!b) return bfail(LBM_EINVAL, "lbm_batch_set_edges: NULL handle");
+  lbmk::Nsbc p = b->nsbc;
+  int rc = lbm_internal_set_edges(&p, types, uw);
+  if (rc) return rc;
+  b->nsbc = p;
+  drop_batch_graphs(b);
+  return LBM_OK;
+}
+
 int lbm_batch_set_collision(lbm_batch_t* b, int32_t model, double omega_e, double omega_eps, double omega_q) {
   if (!b) return bfail(LBM_EINVAL, "lbm_batch_set_collision: NULL handle");
   if (model != LBM_BGK && model != LBM_MRT) return bfail(LBM_EINVAL, "lbm_batch_set_collision: unknown model %d", model);
@@ -622,7 +649,7 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
       rc = build_items(b);
       if (rc) break;
       for (int mult : {-1, 1, 2, 4})  // -1: one block per item; k: k resident waves, persistent
-        for (int pf : {0, 1}) {
+        for (int pf : {0, 1, 2, 6}) {  // 1: whole-tile prefetch; k > 1: k passes ahead
           b->blocks = mult < 0 ? -1 : b->wave * mult;
           b->pf = pf;
           for (int s = 0; s < 2; ++s) enqueue_batch_step(b, s & 1, b->stream);

@@ -298,6 +298,9 @@ struct Nsbc {
   double gamma, beta, kappa;
   double m0[3];  // far-field (rho, ux, uy)
   int order;     // 1 or 2
+  int periodic_x, periodic_y;  // axes closed periodically instead of by NSBC edges
+  int vel[4];                  // edges (left, right, bottom, top) with a prescribed velocity
+  double uw[4][2];             // that velocity
 };
 
 // Node k of the perimeter (k < 2 nx + 2 (ny - 2)) -> coordinates and outward

@@ -168,9 +168,26 @@ __device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict
   const unsigned quad = 0xFu << ((threadIdx.x & 31) & ~3);
   int x, y, nxn, nyn;
   perimeter_node(node, g.nx, g.ny, x, y, nxn, nyn);
+  if (p.periodic_x) nxn = 0;  // a periodic axis has no boundary normal
+  if (p.periodic_y) nyn = 0;
+  const bool open = nxn != 0 || nyn != 0;
+
+  // pulled populations (wrapped on periodic axes); unknown where the source
+  // lies outside the domain.  Lane 0 issues these loads before the moment
+  // loads and shuffles so that both load rounds are in flight together.
+  C h[9];
+  bool known[9];
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    int sx = x - cx(i), sy = y - cy(i);
+    if (p.periodic_x) sx = sx < 0 ? sx + g.nx : (sx >= g.nx ? sx - g.nx : sx);
+    if (p.periodic_y) sy = sy < 0 ? sy + g.ny : (sy >= g.ny ? sy - g.ny : sy);
+    known[i] = sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny;
+    h[i] = (q == 0 && known[i]) ? S::ldg1(A + i * g.plane + (long long)sy * g.pitch + sx) : C(0);
+  }
 
   double m[3] = {0.0, 0.0, 0.0};
-  if (q <= p.order) node_dmoments(A, g, x - q * nxn, y - q * nyn, m);
+  if (open && q <= p.order) node_dmoments(A, g, x - q * nxn, y - q * nyn, m);
   double m1[3], m2[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -179,47 +196,51 @@ __device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict
   }
   if (q != 0) return;
 
-  // Eq. (nes_2): m_p = m_b - gamma d_n m along the outward unit normal;
-  // Eq. (nes_3): m_c = (1 - beta) m_p + beta m_0.
-  const double len = (nxn != 0 && nyn != 0) ? 1.4142135623730951 : 1.0;
-  const double m0[3] = {p.m0[0] - 1.0, p.m0[1], p.m0[2]};
-  double mc[3];  // (rho_c - 1, u_c)
+  if (open) {
+    // Eq. (nes_2): m_p = m_b - gamma d_n m along the outward unit normal;
+    // Eq. (nes_3): m_c = (1 - beta) m_p + beta m_0.
+    // 1 / |n| (GB300's FP64 divide is slow: multiply by the reciprocal)
+    const double inv_len = (nxn != 0 && nyn != 0) ? 0.70710678118654752 : 1.0;
+    const double m0[3] = {p.m0[0] - 1.0, p.m0[1], p.m0[2]};
+    double mc[3];  // (rho_c - 1, u_c)
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const double dn = p.order == 2 ? (3.0 * m[c] - 4.0 * m1[c] + m2[c]) / (2.0 * len) : (m[c] - m1[c]) / len;
-    const double mp = m[c] - p.gamma * dn;
-    mc[c] = (1.0 - p.beta) * mp + p.beta * m0[c];
-  }
+    for (int c = 0; c < 3; ++c) {
+      const double dn = p.order == 2 ? (3.0 * m[c] - 4.0 * m1[c] + m2[c]) * (0.5 * inv_len) : (m[c] - m1[c]) * inv_len;
+      const double mp = m[c] - p.gamma * dn;
+      mc[c] = (1.0 - p.beta) * mp + p.beta * m0[c];
+    }
+    // a velocity edge keeps the predicted density and imposes its velocity
+    // (left/right edges win at corners)
+    const int side = (x == 0 && p.vel[0])             ? 0
+                     : (x == g.nx - 1 && p.vel[1])    ? 1
+                     : (y == 0 && p.vel[2])           ? 2
+                     : (y == g.ny - 1 && p.vel[3])    ? 3
+                                                      : -1;
+    if (side >= 0) {
+      mc[1] = p.uw[side][0];
+      mc[2] = p.uw[side][1];
+    }
 
-  // pulled populations; unknown where the source lies outside the domain
-  C h[9];
-  bool known[9];
+    // Eqs. (nes_0), (nes_1): f_in = f_in^eq(m_c) + f_out - f_out^eq(m_c)
+    const C drho_c = C(mc[0]);
+    C e[9];
+    equilibrium(drho_c, C(mc[1]), C(mc[2]), e);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const int sx = x - cx(i), sy = y - cy(i);
-    known[i] = sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny;
-    h[i] = known[i] ? S::ldg1(A + i * g.plane + (long long)sy * g.pitch + sx) : C(0);
-  }
+    for (int i = 0; i < 9; ++i) {
+      const int o = opp(i);
+      if (!known[i]) h[i] = known[o] ? e[i] + (h[o] - e[o]) : e[i];
+    }
 
-  // Eqs. (nes_0), (nes_1): f_in = f_in^eq(m_c) + f_out - f_out^eq(m_c)
-  const C drho_c = C(mc[0]);
-  C e[9];
-  equilibrium(drho_c, C(mc[1]), C(mc[2]), e);
+    // Eq. (nes_4): f_i -= w_i (d_rho + kappa c_i . d(rho u))
+    C drho, jx, jy;
+    moments(h, drho, jx, jy);
+    const C d_rho = drho - drho_c;
+    const C d_jx = jx - C((1.0 + mc[0]) * mc[1]);
+    const C d_jy = jy - C((1.0 + mc[0]) * mc[2]);
+    const C kap = C(p.kappa);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    const int o = opp(i);
-    if (!known[i]) h[i] = known[o] ? e[i] + (h[o] - e[o]) : e[i];
+    for (int i = 0; i < 9; ++i) h[i] -= wt<C>(i) * (d_rho + kap * (C(cx(i)) * d_jx + C(cy(i)) * d_jy));
   }
-
-  // Eq. (nes_4): f_i -= w_i (d_rho + kappa c_i . d(rho u))
-  C drho, jx, jy;
-  moments(h, drho, jx, jy);
-  const C d_rho = drho - drho_c;
-  const C d_jx = jx - C((1.0 + mc[0]) * mc[1]);
-  const C d_jy = jy - C((1.0 + mc[0]) * mc[2]);
-  const C kap = C(p.kappa);
-#pragma unroll
-  for (int i = 0; i < 9; ++i) h[i] -= wt<C>(i) * (d_rho + kap * (C(cx(i)) * d_jx + C(cy(i)) * d_jy));
 
   collide<MODEL>(h, rates);
   const long long o = (long long)y * g.pitch + x;

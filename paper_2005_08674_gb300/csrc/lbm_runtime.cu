@@ -343,6 +343,42 @@ int lbm_set_nsbc(lbm_t* h, double gamma, double beta, double kappa, int32_t grad
   return LBM_OK;
 }
 
+}  // extern "C"
+
+// Shared with the batched mode: validate edge types and fill the NSBC block.
+int lbm_internal_set_edges(lbmk::Nsbc* p, const int32_t types[4], const double uw[8]) {
+  if (!types) return fail(LBM_EINVAL, "set_edges: NULL types");
+  for (int s = 0; s < 4; ++s)
+    if (types[s] < LBM_EDGE_NSBC || types[s] > LBM_EDGE_VELOCITY)
+      return fail(LBM_EINVAL, "set_edges: unknown edge type %d on side %d", types[s], s);
+  if ((types[0] == LBM_EDGE_PERIODIC) != (types[1] == LBM_EDGE_PERIODIC) ||
+      (types[2] == LBM_EDGE_PERIODIC) != (types[3] == LBM_EDGE_PERIODIC))
+    return fail(LBM_EINVAL, "set_edges: periodic edges come in pairs (left+right, bottom+top)");
+  for (int s = 0; s < 4; ++s)
+    if (types[s] == LBM_EDGE_VELOCITY && (!uw || !std::isfinite(uw[2 * s]) || !std::isfinite(uw[2 * s + 1])))
+      return fail(LBM_EINVAL, "set_edges: velocity edge %d needs a finite velocity", s);
+  p->periodic_x = types[0] == LBM_EDGE_PERIODIC;
+  p->periodic_y = types[2] == LBM_EDGE_PERIODIC;
+  for (int s = 0; s < 4; ++s) {
+    p->vel[s] = types[s] == LBM_EDGE_VELOCITY;
+    p->uw[s][0] = p->vel[s] ? uw[2 * s] : 0.0;
+    p->uw[s][1] = p->vel[s] ? uw[2 * s + 1] : 0.0;
+  }
+  return LBM_OK;
+}
+
+extern "C" {
+
+int lbm_set_edges(lbm_t* h, const int32_t types[4], const double uw[8]) {
+  if (!h) return fail(LBM_EINVAL, "lbm_set_edges: NULL handle");
+  lbmk::Nsbc p = h->nsbc;
+  int rc = lbm_internal_set_edges(&p, types, uw);
+  if (rc) return rc;
+  h->nsbc = p;
+  drop_graphs(h);
+  return LBM_OK;
+}
+
 int lbm_set_collision(lbm_t* h, int32_t model, double omega_e, double omega_eps, double omega_q) {
   if (!h) return fail(LBM_EINVAL, "lbm_set_collision: NULL handle");
   if (model != LBM_BGK && model != LBM_MRT) return fail(LBM_EINVAL, "lbm_set_collision: unknown model %d", model);

@@ -42,6 +42,8 @@ _SIGS = {
     "lbm_set_nsbc": (ctypes.c_int, [_vp, _dbl, _dbl, _dbl, _i32]),
     "lbm_set_precision": (ctypes.c_int, [_vp, _i32]),
     "lbm_set_collision": (ctypes.c_int, [_vp, _i32, _dbl, _dbl, _dbl]),
+    "lbm_set_edges": (ctypes.c_int, [_vp, _vp, _vp]),
+    "lbm_batch_set_edges": (ctypes.c_int, [_vp, _vp, _vp]),
     "lbm_set_stream": (ctypes.c_int, [_vp, _vp]),
     "lbm_buffer_bytes": (ctypes.c_size_t, [_vp]),
     "lbm_scratch_bytes": (ctypes.c_size_t, [_vp]),
@@ -130,6 +132,34 @@ def lbm_set_precision(h, storage):
 def lbm_set_collision(h, model, omega_e=1.0, omega_eps=1.0, omega_q=1.0):
     m = {"bgk": LBM_BGK, "mrt": LBM_MRT}.get(model, model)
     return _check(_L.lbm_set_collision(h, m, omega_e, omega_eps, omega_q))
+
+
+LBM_EDGE_NSBC, LBM_EDGE_PERIODIC, LBM_EDGE_VELOCITY = 0, 1, 2
+_EDGE = {"nsbc": LBM_EDGE_NSBC, "periodic": LBM_EDGE_PERIODIC, "velocity": LBM_EDGE_VELOCITY}
+
+
+def _edge_args(edges):
+    """edges: 4 entries (left, right, bottom, top), each 'nsbc', 'periodic' or
+    ('velocity', ux, uy)."""
+    types = (ctypes.c_int32 * 4)()
+    uw = (ctypes.c_double * 8)()
+    for s, e in enumerate(edges):
+        if isinstance(e, (tuple, list)):
+            types[s] = _EDGE[e[0]]
+            uw[2 * s], uw[2 * s + 1] = float(e[1]), float(e[2])
+        else:
+            types[s] = _EDGE[e]
+    return ctypes.cast(types, ctypes.c_void_p), ctypes.cast(uw, ctypes.c_void_p), (types, uw)
+
+
+def lbm_set_edges(h, edges):
+    t, u, _keep = _edge_args(edges)
+    return _check(_L.lbm_set_edges(h, t, u))
+
+
+def lbm_batch_set_edges(b, edges):
+    t, u, _keep = _edge_args(edges)
+    return _check(_L.lbm_batch_set_edges(b, t, u))
 
 
 def lbm_set_stream(h, stream_handle: int):
@@ -243,7 +273,7 @@ class Simulation:
 
     def __init__(self, nx, ny, tau, farfield_rho=1.0, farfield_u=(0.0, 0.0), storage="f32",
                  gamma=0.6, beta=0.0, kappa=3.0, grad_order=1, stream=None, collision="bgk",
-                 mrt_rates=(1.0, 1.0, 1.0)):
+                 mrt_rates=(1.0, 1.0, 1.0), edges=None):
         import torch
         self.nx, self.ny, self.tau = nx, ny, tau
         self.storage = storage
@@ -252,6 +282,8 @@ class Simulation:
             lbm_set_precision(self.h, storage)
             lbm_set_nsbc(self.h, gamma, beta, kappa, grad_order)
             lbm_set_collision(self.h, collision, *mrt_rates)
+            if edges is not None:
+                lbm_set_edges(self.h, edges)
             dev = torch.device("cuda", torch.cuda.current_device())
             self.stream = stream or torch.cuda.current_stream(dev)
             lbm_set_stream(self.h, self.stream.cuda_stream)
@@ -437,7 +469,7 @@ class Batch:
     """Independent instances stepped by one launch per step; torch allocates the pools."""
 
     def __init__(self, workloads, storage="f32", collision="bgk", mrt_rates=(1.0, 1.0, 1.0),
-                 gamma=0.6, beta=0.0, kappa=3.0, grad_order=1, stream=None):
+                 gamma=0.6, beta=0.0, kappa=3.0, grad_order=1, stream=None, edges=None):
         import torch
         self.shapes = [(w.nx, w.ny) for w in workloads]
         descs = [(w.nx, w.ny, w.tau, w.farfield_rho, w.farfield_u[0], w.farfield_u[1]) for w in workloads]
@@ -445,6 +477,8 @@ class Batch:
         try:
             lbm_batch_set_nsbc(self.b, gamma, beta, kappa, grad_order)
             lbm_batch_set_collision(self.b, collision, *mrt_rates)
+            if edges is not None:
+                lbm_batch_set_edges(self.b, edges)
             dev = torch.device("cuda", torch.cuda.current_device())
             self.stream = stream or torch.cuda.current_stream(dev)
             lbm_batch_set_stream(self.b, self.stream.cuda_stream)

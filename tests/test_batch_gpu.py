@@ -96,3 +96,17 @@ def test_full_batch_256_sampled(lbm):
             for a, c in zip(b.macros(k), ref):
                 assert np.array_equal(a, c), k
         assert all(b.unstable_nodes(k) == 0 for k in range(len(ws)))
+
+
+def test_batch_with_edge_types_bit_identical(lbm):
+    ws = small_batch()[:6]
+    edges = [("velocity", 0.03, 0.0), "nsbc", "periodic", "periodic"]
+    kw = dict(collision="mrt", mrt_rates=(1.4, 1.4, 1.2), edges=edges)
+    with lbm.Batch(ws, storage="f32", **kw) as b:
+        for k, w in enumerate(ws):
+            b.init(k, *w.fields())
+        b.step(33)
+        for k, w in enumerate(ws):
+            ref = single(lbm, w, "f32", 33, **kw)
+            for a, c in zip(b.macros(k), ref):
+                assert np.array_equal(a, c), w.name

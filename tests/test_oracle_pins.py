@@ -383,3 +383,47 @@ def test_mrt_viscosity_set_by_stress_rate():
     k = 2 * np.pi / L
     nu = math.log(a1 / a2) / (k * k * 400)
     assert abs(nu / (CS2 * (tau - 0.5)) - 1) < 0.01
+
+
+# --- edge types: periodic axes and a velocity (Dirichlet) edge -------------------
+
+def test_velocity_edge_imposes_its_velocity():
+    """The velocity edge ends each step carrying exactly the prescribed velocity
+    (the correction of Eq. nes_4 enforces rho_c u_w), on every node of that edge."""
+    nx, ny, uw = 16, 12, (0.05, 0.01)
+    o = oracle.Oracle(nx, ny, 0.62, periodic=(False, True), velocity_edges={0: uw})
+    o.init(*_smooth_fields(nx, ny, 13))
+    for _ in range(3):
+        rho, ux, uy = o.step(1).macros()
+        assert np.abs(ux[:, 0] - uw[0]).max() < 1e-15 and np.abs(uy[:, 0] - uw[1]).max() < 1e-15
+
+
+def test_uniform_stream_through_velocity_inlet_is_steady():
+    """f = f_eq(1, u_w) everywhere with a u_w inlet, NSBC outlet, periodic sides
+    is an exact fixed point."""
+    nx, ny, uw = 20, 9, (0.06, 0.0)
+    o = oracle.Oracle(nx, ny, 0.6, 1.0, uw, periodic=(False, True), velocity_edges={0: uw})
+    o.init(np.ones((ny, nx)), np.full((ny, nx), uw[0]), np.zeros((ny, nx)))
+    g = o.step(40).get_f()
+    assert np.abs(g - oracle.equilibrium(1.0, *uw)[:, None, None]).max() < 1e-15
+
+
+def test_paper_vortex_setup_is_fully_absorbed():
+    """Sec. 7's set-up: 128^2, u0 = 0.1, beta u0 = 0.05, R_c = 20, Re = 1000 (tau from
+    nu = u0 l / Re), velocity inlet on the left, NSBC on the right, periodic top and
+    bottom, MRT with omega_e = omega_eps = 1.4, omega_q = 1.2.  The paper reports the
+    vortex 'fully absorbed': after it has crossed the outlet, the disturbance energy
+    left in the domain is below 1e-4 of the initial one."""
+    n, u0 = 128, 0.1
+    tau = 0.5 + 3 * u0 * n / 1000
+    rates = [1, 1.4, 1.4, 1, 1.2, 1, 1.2, 1 / tau, 1 / tau]
+    f = inputs.convected_vortex(n, n, u0, 0.5 * u0, 20.0, n / 2, n / 2)
+    o = oracle.Oracle(n, n, tau, 1.0, (u0, 0.0), periodic=(False, True), collision="mrt", mrt_rates=rates,
+                      openmp=True, velocity_edges={0: (u0, 0.0)}).init(*f)
+
+    def disturbance(m):
+        return float(np.sum((m[1] - u0) ** 2 + m[2] ** 2))
+
+    e0 = disturbance(o.macros())
+    assert disturbance(o.step(400).macros()) > 0.5 * e0  # still inside
+    assert disturbance(o.step(1200).macros()) < 1e-4 * e0  # gone through the outlet

@@ -228,3 +228,61 @@ def test_instability_is_reported_not_faulted(lbm):
     out = sim.reduce(allow_unstable=True)
     assert out[3] > 0
     sim.close()
+
+
+# --- edge types: periodic axes, velocity edge; the paper's two test set-ups -----
+
+def _random_fields(nx, ny, seed):
+    rng = np.random.default_rng(seed)
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    rho = 1 + 1e-3 * np.sin(0.5 * x + 0.2 * y + rng.uniform(0, 6))
+    ux = 0.03 + 0.02 * np.cos(0.3 * x - 0.4 * y + rng.uniform(0, 6))
+    uy = 0.02 * np.sin(0.25 * x + 0.35 * y + rng.uniform(0, 6))
+    return rho, ux, uy
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("edges,periodic,vel", [
+    (["nsbc", "nsbc", "periodic", "periodic"], (False, True), {}),
+    (["periodic", "periodic", "nsbc", "nsbc"], (True, False), {}),
+    (["periodic", "periodic", "periodic", "periodic"], (True, True), {}),
+    ([("velocity", 0.04, 0.01), "nsbc", "periodic", "periodic"], (False, True), {0: (0.04, 0.01)}),
+    ([("velocity", 0.04, 0.0), "nsbc", ("velocity", 0.02, 0.0), "nsbc"], (False, False), {0: (0.04, 0.0), 2: (0.02, 0.0)}),
+])
+def test_edge_types(lbm, storage, edges, periodic, vel):
+    nx, ny = 97, 66
+    fields = _random_fields(nx, ny, 21)
+    w = inputs.Workload("edges", nx, ny, 0.6, 40, farfield_u=(0.03, 0.0))
+    ref = oracle_run(w, 40, fields=fields, beta=0.1, periodic=periodic, velocity_edges=vel)
+    got = gpu_run(lbm, w, storage, 40, fields=fields, beta=0.1, edges=edges)
+    err = max_err(got, ref)
+    assert err <= TOL[storage], err
+
+
+def test_paper_vortex_setup_f32(lbm):
+    """Sec. 7's set-up (velocity inlet, NSBC outlet, periodic sides, MRT 1.4/1.4/1.2,
+    Re 1000, 128^2) on the FP32 path, against the oracle after 1200 steps."""
+    n, u0 = 128, 0.1
+    tau = 0.5 + 3 * u0 * n / 1000
+    w = inputs.Workload("paper-vortex", n, n, tau, 1200, farfield_u=(u0, 0.0), kind="vortex",
+                        params=dict(u0=u0, beta_u0=0.5 * u0, rc=20.0, x0=n / 2, y0=n / 2))
+    ref = oracle_run(w, 1200, periodic=(False, True), velocity_edges={0: (u0, 0.0)}, collision="mrt",
+                     mrt_rates=_oracle_mrt_rates(PAPER_VORTEX_RATES, tau))
+    got = gpu_run(lbm, w, "f32", 1200, edges=[("velocity", u0, 0.0), "nsbc", "periodic", "periodic"],
+                  collision="mrt", mrt_rates=PAPER_VORTEX_RATES)
+    assert max_err(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_paper_plane_wave_setup(lbm, storage):
+    """Sec. 6's set-up: a Gaussian plane wave at 60 degrees on 128^2, zeta = 0.01,
+    lambda = l/32, NSBC on all edges (gamma 0.6, beta 0), MRT rates 1.9, viscosity
+    close to zero (tau = 0.5001 stands in for the paper's tau = 0.5, which has no
+    BGK/MRT stress rate)."""
+    n, tau = 128, 0.5001
+    w = inputs.Workload("paper-wave", n, n, tau, 240, kind="plane",
+                        params=dict(zeta=0.01, lam=n / 32, angle=60.0))
+    ref = oracle_run(w, 240, collision="mrt", mrt_rates=_oracle_mrt_rates(PAPER_WAVE_RATES, tau))
+    got = gpu_run(lbm, w, storage, 240, collision="mrt", mrt_rates=PAPER_WAVE_RATES)
+    err = max_err(got, ref)
+    assert err <= TOL[storage] * (10 if storage == "f32" else 1), err
