@@ -235,10 +235,10 @@ def run_batched(lbm, ws, bfields, storage, steps, warmup, world, peak, launch=No
     for k, f in enumerate(bfields):
         bt.init(k, *f)
     if launch:
-        tb, tr, tg, tp, ts = (list(launch) + [0])[:5]
-        bt.set_launch(tb, tr, tg, tp, ts)
+        tb, tr, tg, tp, ts, tt = (list(launch) + [0, 0])[:6]
+        bt.set_launch(tb, tr, tg, tp, ts, tt)
     else:
-        tb, tr, tg, tp, ts, _ = bt.autotune()
+        tb, tr, tg, tp, ts, tt, _ = bt.autotune()
     bt.step(warmup)
     torch.cuda.synchronize()
     a0 = torch.cuda.Event(enable_timing=True)
@@ -248,11 +248,13 @@ def run_batched(lbm, ws, bfields, storage, steps, warmup, world, peak, launch=No
     a1.record(bt.stream)
     torch.cuda.synchronize()
     bms = a0.elapsed_time(a1)
+    bt.status()  # raises if a bounded device-side wait gave up
     bad = sum(bt.unstable_nodes(k) for k in range(len(ws)))
     gbs = BYTES_PER_CELL[storage] * bt.cells * steps / (bms * 1e-3) / 1e9
     out = {"mlups": world * bt.cells * steps / (bms * 1e-3) / 1e6, "steps": steps, "ms_per_step": bms / steps,
            "instances": len(ws), "cells": bt.cells, "step_gbs": gbs, "step_frac": gbs / peak,
-           "launch": {"threads_x": tb, "rows": tr, "blocks": tg, "prefetch_rows": tp, "split": ts},
+           "launch": {"threads_x": tb, "rows": tr, "blocks": tg, "prefetch_rows": tp, "split": ts,
+                      "tma_tile": tt},
            "unstable_nodes": bad, "what": BATCH_WHAT}
     bt.close()
     del bt

@@ -38,6 +38,7 @@ extern "C" {
 #define LBM_ECUDA (-3)     /* a CUDA runtime call failed (message has the CUDA error) */
 #define LBM_EUNSTABLE (-4) /* non-finite or non-positive density found by lbm_reduce */
 #define LBM_ESTATE (-5)    /* call out of order (e.g. step before init) */
+#define LBM_ETIMEOUT (-6)  /* a bounded device-side wait gave up (see lbm_batch_status) */
 
 /* Storage of the populations in device memory.  Every type stores the
  * deviation f_i - w_i from the rest-state weights (a shift that keeps the
@@ -262,17 +263,26 @@ int lbm_batch_unstable_nodes(lbm_batch_t* b, int32_t k, int64_t* count);
  * thread = vector x rows); grid size `blocks` (-1 = one block per work item,
  * 0 = one resident wave of blocks looping over the list, > 0 = that many);
  * `prefetch_rows`: 0 = off, 1 = each tile asks the bulk-copy engine for its
- * whole footprint in L2 when it starts, k > 1 = each warp pulls the vectors
- * it meets k passes later (at most 64); `split` = 0 runs NSBC chunks and bulk tiles in ONE launch
+ * own footprint in L2 when it starts, k > 1 = for the footprint of the tile
+ * k items further down the list (at most 65536); `split` = 0 runs NSBC chunks and bulk tiles in ONE launch
  * per step, 1 runs the NSBC chunks as a second launch beside the bulk tiles
- * (the bulk launch then keeps the single-domain kernel's register budget). */
+ * (the bulk launch then keeps the single-domain kernel's register budget).
+ * `tma_tile` > 0 selects the shared-memory path instead: tiles of that many
+ * vectors (128 or 256, with threads_x 128, or 256 with 256) are staged by
+ * cp.async.bulk copies completing on an mbarrier, double-buffered in
+ * persistent blocks (one resident wave; `rows`, `blocks`, `prefetch_rows`
+ * and `split` are then ignored, the NSBC chunks run beside). */
 int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_t blocks, int32_t prefetch_rows,
-                         int32_t split);
-/* Time every compiled tile shape, grid size, prefetch setting and split on
- * the batch's own state (restored afterwards, through a temporary device
- * copy from cudaMallocAsync) and keep the fastest. */
+                         int32_t split, int32_t tma_tile);
+/* Time every compiled tile shape, grid size, prefetch setting and split, and
+ * the shared-memory path, on the batch's own state (restored afterwards,
+ * through a temporary device copy from cudaMallocAsync) and keep the fastest. */
 int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_t* blocks, int32_t* prefetch_rows,
-                       int32_t* split, double* ms_per_step);
+                       int32_t* split, int32_t* tma_tile, double* ms_per_step);
+/* LBM_ETIMEOUT if a staged-tile wait of the shared-memory path gave up since
+ * the batch was created (the step then left those tiles untouched); LBM_OK
+ * otherwise.  Synchronises. */
+int lbm_batch_status(lbm_batch_t* b);
 
 /* Per-launch timing.  While enabled, lbm_step launches every step directly
  * (no graph) on the handle's stream with CUDA events around the bulk

@@ -88,6 +88,8 @@ struct lbm_batch {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int wave = 1;                        // resident blocks on the device for the current shape
+  int tile = 0;                        // > 0: bulk tiles of this many vectors staged by bulk copies
+  int* d_err = nullptr;                // set by a kernel whose bounded wait gave up
   bool items_dirty = true;
   std::vector<char> initialised;
   int cur = 0;
@@ -106,6 +108,27 @@ void bdispatch(int storage, F&& f) {
     case LBM_F16: f(__half{}); break;
     case LBM_BF16: f(__nv_bfloat16{}); break;
     default: f(float{}); break;
+  }
+}
+
+// Whole-tile prefetch of bulk item w of instance d: the tile's vectors span
+// one contiguous address range per plane (its rows plus their padding); warp
+// `wid` asks the bulk-copy engine for planes wid, wid + BX/32, ... so the
+// tile's loads find their lines in L2.
+template <typename T, int BX>
+__device__ __forceinline__ void prefetch_tile(const T* __restrict__ A, const InstDev& d, const int4& w, int wid) {
+  constexpr int V = lbmk::Store<T>::V;
+  const int nvec = (d.nx + V - 1) / V;
+  const int ja = w.y, jb = w.y + w.z - 1;
+  const int ya = 1 + ja / nvec, yb = 1 + jb / nvec;
+  const long long a0 = (long long)ya * d.pitch + (long long)(ja - (ya - 1) * nvec) * V;
+  const long long a1 = (long long)yb * d.pitch + (long long)(jb - (yb - 1) * nvec + 1) * V;
+  const unsigned bytes = (unsigned)((a1 - a0) * (long long)sizeof(T));
+  const T* base = A + d.off + a0;
+  for (int pl = wid; pl < 9; pl += BX / 32) {
+    const long long sh = (pl == 3 || pl == 5 || pl == 7) ? -(long long)d.pitch
+                                                       : ((pl == 4 || pl == 6 || pl == 8) ? (long long)d.pitch : 0);
+    lbmk::prefetch_l2(base + pl * d.plane + sh, bytes);
   }
 }
 
@@ -135,20 +158,11 @@ __global__ void __launch_bounds__(BX) batch_step_kernel(const T* __restrict__ A,
         // 16-byte vectors, nvec per row; this item is vectors [w.y, w.y + w.z)
         const int nvec = (d.nx + V - 1) / V;
         const int warp0 = (int)threadIdx.x - lane;
-        if (pf == 1 && lane == 0) {
-          // whole-tile prefetch: the tile's vectors span one contiguous address
-          // range per plane (rows plus their padding); warp k asks the
-          // bulk-copy engine for planes k, k + BX/32, ... so every load of the
-          // later passes finds its line already in L2
-          const int ja = w.y, jb = w.y + w.z - 1;
-          const int ya = 1 + ja / nvec, yb = 1 + jb / nvec;
-          const long long a0 = (long long)ya * g.pitch + (long long)(ja - (ya - 1) * nvec) * V;
-          const long long a1 = (long long)yb * g.pitch + (long long)(jb - (yb - 1) * nvec + 1) * V;
-          const unsigned bytes = (unsigned)((a1 - a0) * (long long)sizeof(T));
-          for (int pl = warp0 / 32; pl < 9; pl += BX / 32) {
-            const long long sh = (pl == 3 || pl == 5 || pl == 7) ? -g.pitch : ((pl == 4 || pl == 6 || pl == 8) ? g.pitch : 0);
-            lbmk::prefetch_l2(a + pl * g.plane + a0 + sh, bytes);
-          }
+        if (pf == 1 && lane == 0) prefetch_tile<T, BX>(A, d, w, warp0 / 32);
+        if (pf > 1 && lane == 0 && it + pf < i1) {
+          // the tile pf items ahead (another block's, started a little later)
+          const int4 wn = items[it + pf];
+          if (wn.x >= 0) prefetch_tile<T, BX>(A, inst[wn.x], wn, warp0 / 32);
         }
         for (int base = 0; base < w.z; base += BX) {
           const int jr = base + (int)threadIdx.x;
@@ -156,25 +170,6 @@ __global__ void __launch_bounds__(BX) batch_step_kernel(const T* __restrict__ A,
           const int j = w.y + (valid ? jr : 0);
           const int yy = 1 + j / nvec;
           const int x0 = (j - (yy - 1) * nvec) * V;
-          if (pf > 1 && lane == 0 && w.y + base + pf * BX + warp0 < (d.ny - 2) * nvec) {
-            // the vectors this warp would meet pf passes later (possibly in
-            // the instance's next tile): pull their first row segment into L2
-            const int jn = w.y + base + pf * BX + warp0;
-            const int yn = 1 + jn / nvec;
-            const int cn = jn - (yn - 1) * nvec;
-            const unsigned bytes = (unsigned)(min(32, nvec - cn) * 16);
-            const long long q0 = (long long)yn * g.pitch + (long long)cn * V;
-            const long long P = g.plane;
-            lbmk::prefetch_l2(a + 0 * P + q0, bytes);
-            lbmk::prefetch_l2(a + 1 * P + q0, bytes);
-            lbmk::prefetch_l2(a + 2 * P + q0, bytes);
-            lbmk::prefetch_l2(a + 3 * P + q0 - g.pitch, bytes);
-            lbmk::prefetch_l2(a + 4 * P + q0 + g.pitch, bytes);
-            lbmk::prefetch_l2(a + 5 * P + q0 - g.pitch, bytes);
-            lbmk::prefetch_l2(a + 6 * P + q0 + g.pitch, bytes);
-            lbmk::prefetch_l2(a + 7 * P + q0 - g.pitch, bytes);
-            lbmk::prefetch_l2(a + 8 * P + q0 + g.pitch, bytes);
-          }
           lbmk::bulk_row<T, MODEL>(a, b, g, r, yy, x0, lane, 0, 0u, valid);
         }
         continue;
@@ -189,6 +184,199 @@ __global__ void __launch_bounds__(BX) batch_step_kernel(const T* __restrict__ A,
       if (node < w.y + w.z) lbmk::nsbc_node<T, MODEL>(a, b, g, q, r, node, (int)threadIdx.x & 3);
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Bulk tiles through shared memory (bulk-copy engine).  With the batch pitch
+// equal to nx rounded up to one 16-byte vector, a tile of vectors [j0, j1) of
+// an instance's flattened interior is ONE contiguous range per plane (shifted
+// by a row for the planes pulled from y - 1 / y + 1); the tile plus one
+// vector on each side (the x - 1 / x + 1 neighbours) arrives by nine
+// cp.async.bulk copies completing on an mbarrier.  Two buffers per block: the
+// next tile is in flight while the current one is collided, so the bytes in
+// flight are bounded by shared memory, not by registers.
+// ---------------------------------------------------------------------------
+constexpr int kTmaWaitLimit = 1 << 20;  // try_wait rounds before giving up (>= ~1 s)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+// Bounded wait for phase `parity` of the barrier; false after kTmaWaitLimit rounds.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (int i = 0; i < kTmaWaitLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// Row shift of the plane each direction is pulled from (Fig. 1 numbering).
+__device__ __forceinline__ int pull_row_shift(int i) { return (i == 3 || i == 5 || i == 7) ? -1 : ((i == 4 || i == 6 || i == 8) ? 1 : 0); }
+
+// Issue the nine copies of tile w into slot (9 planes of SLOT bytes each).
+template <typename T, int TILE>
+__device__ __forceinline__ void issue_tile(const T* __restrict__ A, const InstDev& d, const int4& w, unsigned char* slot,
+                                           uint64_t* bar) {
+  constexpr int V = lbmk::Store<T>::V;
+  constexpr int SLOT = (TILE + 2) * 16;
+  const long long plane_elems = (long long)d.ny * d.pitch;
+  long long lo[9], hi[9];
+  uint32_t total = 0;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const long long start = (long long)(1 + pull_row_shift(i)) * d.pitch + (long long)(w.y - 1) * V;
+    lo[i] = start < 0 ? 0 : start;
+    const long long end = start + (long long)(w.z + 2) * V;
+    hi[i] = end > plane_elems ? plane_elems : end;
+    total += (uint32_t)((hi[i] - lo[i]) * (long long)sizeof(T));
+  }
+  mbar_expect_tx(bar, total);
+#pragma unroll
+  for (int i = 0; i < 9; ++i) {
+    const long long start = (long long)(1 + pull_row_shift(i)) * d.pitch + (long long)(w.y - 1) * V;
+    bulk_copy_g2s(slot + i * SLOT + (lo[i] - start) * (long long)sizeof(T), A + d.off + i * d.plane + lo[i],
+                  (uint32_t)((hi[i] - lo[i]) * (long long)sizeof(T)), bar);
+  }
+}
+
+template <typename T, int BX, int MODEL, int TILE>
+__global__ void __launch_bounds__(BX) batch_tma_kernel(const T* __restrict__ A, T* __restrict__ B,
+                                                       const InstDev* __restrict__ inst,
+                                                       const int4* __restrict__ items, int i0, int i1, double s_e,
+                                                       double s_eps, double s_q, int* __restrict__ err) {
+  using S = lbmk::Store<T>;
+  using C = typename S::C;
+  constexpr int V = S::V;
+  constexpr int SLOT = (TILE + 2) * 16;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar[2];
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  uint32_t parity[2] = {0u, 0u};
+  int k = 0;
+  if (tid == 0 && i0 + (int)blockIdx.x < i1) {
+    const int4 w = items[i0 + blockIdx.x];
+    issue_tile<T, TILE>(A, inst[w.x], w, smem, &bar[0]);
+  }
+  for (int it = i0 + blockIdx.x; it < i1; it += gridDim.x, ++k) {
+    const int cur = k & 1;
+    const int nit = it + gridDim.x;
+    if (tid == 0 && nit < i1) {
+      // the other slot was released by the barrier that closed the last pass
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      const int4 wn = items[nit];
+      issue_tile<T, TILE>(A, inst[wn.x], wn, smem + (cur ^ 1) * 9 * SLOT, &bar[cur ^ 1]);
+    }
+    const int4 w = items[it];
+    const InstDev d = inst[w.x];
+    // thread 0 waits (bounded) and tells the block, so that the whole block
+    // takes the same way out if the copy never lands
+    __shared__ int landed;
+    if (tid == 0) landed = mbar_wait(&bar[cur], parity[cur]) ? 1 : 0;
+    __syncthreads();
+    if (!landed) {
+      // record it, give the copies in flight a bounded chance to finish, and
+      // leave without touching the tile
+      if (tid == 0) {
+        atomicExch(err, 1);
+        mbar_wait(&bar[cur], parity[cur]);
+        if (nit < i1) mbar_wait(&bar[cur ^ 1], parity[cur ^ 1]);
+      }
+      return;
+    }
+    mbar_wait(&bar[cur], parity[cur]);  // completes at once; orders this thread after the copy
+    parity[cur] ^= 1u;
+    const lbmk::Geom g{d.nx, d.ny, d.pitch, d.plane};
+    const lbmk::Rates<C> r{C(d.omega), C(s_e), C(s_eps), C(s_q)};
+    const unsigned char* sl = smem + cur * 9 * SLOT;
+    const int nvec = d.pitch / V;  // the batch pitch is a whole number of vectors
+    T* b = B + d.off;
+#pragma unroll 1
+    for (int u = tid; u < w.z; u += BX) {
+      const int j = w.y + u;
+      const int y = 1 + j / nvec;
+      const int x0 = (j - (y - 1) * nvec) * V;
+      C v[9][V], lf[9], rt[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const T* e = reinterpret_cast<const T*>(sl + i * SLOT) + (u + 1) * V;
+        S::lds(e, v[i]);
+        lf[i] = S::ld1s(e - 1);  // x0 - 1 of the same (shifted) row
+        rt[i] = S::ld1s(e + V);  // x0 + V
+      }
+      C o[9][V];
+#pragma unroll
+      for (int kk = 0; kk < V; ++kk) {
+        C h[9];
+        h[0] = v[0][kk];
+        h[1] = kk == 0 ? lf[1] : v[1][kk - 1];
+        h[2] = kk == V - 1 ? rt[2] : v[2][kk + 1];
+        h[3] = v[3][kk];
+        h[4] = v[4][kk];
+        h[5] = kk == 0 ? lf[5] : v[5][kk - 1];
+        h[6] = kk == V - 1 ? rt[6] : v[6][kk + 1];
+        h[7] = kk == V - 1 ? rt[7] : v[7][kk + 1];
+        h[8] = kk == 0 ? lf[8] : v[8][kk - 1];
+        lbmk::collide<MODEL>(h, r, C(S::kScale));
+#pragma unroll
+        for (int i = 0; i < 9; ++i) o[i][kk] = h[i];
+      }
+      const long long r0 = (long long)y * g.pitch + x0;
+      if (x0 >= 1 && x0 + V <= g.nx - 1) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) S::st(b + i * g.plane + r0, o[i]);
+      } else {
+#pragma unroll
+        for (int kk = 0; kk < V; ++kk) {
+          const int x = x0 + kk;
+          if (x >= 1 && x <= g.nx - 2) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) S::st1r(b + i * g.plane + r0 + kk, o[i][kk]);
+          }
+        }
+      }
+    }
+    __syncthreads();  // every thread is done with this slot
+  }
+}
+
+template <typename T, int BX, int MODEL, int TILE>
+void launch_tma(const lbm_batch_t* b, int from, cudaStream_t s, int grid, int i0, int i1, int* err) {
+  // the dynamic shared-memory limit was raised by wave_blocks() when the work
+  // list was built (never inside a stream capture)
+  constexpr int smem = 2 * 9 * (TILE + 2) * 16;
+  batch_tma_kernel<T, BX, MODEL, TILE><<<grid, BX, smem, s>>>(static_cast<const T*>(b->pool[from]),
+                                                              static_cast<T*>(b->pool[1 - from]), b->d_inst,
+                                                              b->d_items, i0, i1, b->s_e, b->s_eps, b->s_q, err);
 }
 
 template <typename T, int BX, int PART>
@@ -217,12 +405,38 @@ void with_bx(int bx, F&& f) {
   }
 }
 
+// (threads, tile) pairs compiled for the shared-memory bulk path
+template <typename F>
+void with_tma(int bx, int tile, F&& f) {
+  if (bx == 256)
+    f(std::integral_constant<int, 256>{}, std::integral_constant<int, 256>{});
+  else if (tile == 256)
+    f(std::integral_constant<int, 128>{}, std::integral_constant<int, 256>{});
+  else
+    f(std::integral_constant<int, 128>{}, std::integral_constant<int, 128>{});
+}
+
+bool tma_shape_ok(int bx, int tile) {
+  return (bx == 128 && (tile == 128 || tile == 256)) || (bx == 256 && tile == 256);
+}
+
 // resident blocks on the device for the launch that carries the bulk tiles
 int wave_blocks(const lbm_batch_t* b) {
   int per_sm = 0, sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
   bdispatch(b->storage, [&](auto tag) {
     using T = decltype(tag);
+    if (b->tile > 0) {
+      with_tma(b->bx, b->tile, [&](auto bxc, auto tc) {
+        constexpr int BX = decltype(bxc)::value, TILE = decltype(tc)::value;
+        constexpr int smem = 2 * 9 * (TILE + 2) * 16;
+        const void* k = b->collision == 1 ? (const void*)batch_tma_kernel<T, BX, 1, TILE>
+                                          : (const void*)batch_tma_kernel<T, BX, 0, TILE>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BX, smem);
+      });
+      return;
+    }
     with_bx(b->bx, [&](auto bxc) {
       constexpr int BX = decltype(bxc)::value;
       const void* k = b->split ? kernel_ptr<T, BX, 1>(b->collision) : kernel_ptr<T, BX, 0>(b->collision);
@@ -243,6 +457,27 @@ int grid_for_items(const lbm_batch_t* b, int n) {
 void enqueue_batch_step(const lbm_batch_t* b, int from, cudaStream_t s) {
   bdispatch(b->storage, [&](auto tag) {
     using T = decltype(tag);
+    if (b->tile > 0) {
+      // NSBC chunks beside the shared-memory bulk path (persistent, one wave)
+      const int n_edge = b->n_items - b->n_bulk_items;
+      cudaEventRecord(b->ev_fork, s);
+      cudaStreamWaitEvent(b->side, b->ev_fork, 0);
+      with_bx(b->bx, [&](auto bxc) {
+        constexpr int BX = decltype(bxc)::value;
+        launch_part<T, BX, 2>(b, from, b->side, std::max(1, n_edge), 0, n_edge);
+      });
+      with_tma(b->bx, b->tile, [&](auto bxc, auto tc) {
+        constexpr int BX = decltype(bxc)::value, TILE = decltype(tc)::value;
+        const int grid = std::max(1, std::min(b->n_bulk_items, b->wave));
+        if (b->collision == 1)
+          launch_tma<T, BX, 1, TILE>(b, from, s, grid, n_edge, b->n_items, b->d_err);
+        else
+          launch_tma<T, BX, 0, TILE>(b, from, s, grid, n_edge, b->n_items, b->d_err);
+      });
+      cudaEventRecord(b->ev_join, b->side);
+      cudaStreamWaitEvent(s, b->ev_join, 0);
+      return;
+    }
     with_bx(b->bx, [&](auto bxc) {
       constexpr int BX = decltype(bxc)::value;
       if (!b->split) {
@@ -291,7 +526,7 @@ int build_items(lbm_batch_t* b) {
     const InstDev& d = b->inst[k];
     const int nvec = (d.nx + V - 1) / V;
     const int total = (d.ny - 2) * nvec;  // interior rows flattened into 16-byte vectors
-    const int per_item = b->bx * b->rows;
+    const int per_item = b->tile > 0 ? b->tile : b->bx * b->rows;
     for (int j0 = 0; j0 < total; j0 += per_item) items.push_back(make_int4(k, j0, std::min(per_item, total - j0), 0));
   }
   const int n_bulk = (int)items.size() - n_edge;
@@ -318,6 +553,10 @@ int ensure_batch_memory(lbm_batch_t* b) {
     BATCH_CUDA(cudaMemset(b->pool[1], 0, pb));
     b->owns_pools = true;
     b->bound = true;
+  }
+  if (!b->d_err) {
+    BATCH_CUDA(cudaMalloc(&b->d_err, sizeof(int)));
+    BATCH_CUDA(cudaMemset(b->d_err, 0, sizeof(int)));
   }
   if (!b->d_inst) {
     BATCH_CUDA(cudaMalloc(&b->d_inst, b->inst.size() * sizeof(InstDev)));
@@ -388,7 +627,9 @@ lbm_batch_t* lbm_batch_create(int32_t count, const lbm_instance_desc* descs, int
     InstDev d{};
     d.nx = s.nx;
     d.ny = s.ny;
-    d.pitch = (int)round_up((size_t)s.nx, 64);
+    // one 16-byte vector of alignment: consecutive rows of a plane then form
+    // one contiguous run of vectors, so a tile is one copy per plane
+    d.pitch = (int)round_up((size_t)s.nx, 16 / b->elt);
     d.plane = (long long)(round_up((size_t)s.ny * d.pitch * b->elt, 256) / b->elt);
     d.off = off;
     d.omega = 1.0 / s.tau;
@@ -417,6 +658,7 @@ void lbm_batch_destroy(lbm_batch_t* b) {
   }
   cudaFree(b->d_inst);
   cudaFree(b->d_items);
+  cudaFree(b->d_err);
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->side) cudaStreamDestroy(b->side);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
@@ -603,24 +845,29 @@ int lbm_batch_unstable_nodes(lbm_batch_t* b, int32_t k, int64_t* count) {
 }
 
 int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_t blocks, int32_t prefetch_rows,
-                         int32_t split) {
+                         int32_t split, int32_t tma_tile) {
   if (!b) return bfail(LBM_EINVAL, "lbm_batch_set_launch: NULL handle");
-  if (!batch_shape_ok(threads_x, rows)) return bfail(LBM_EINVAL, "lbm_batch_set_launch: shape (%d, %d) not compiled", threads_x, rows);
+  if (tma_tile != 0 && !tma_shape_ok(threads_x, tma_tile))
+    return bfail(LBM_EINVAL, "lbm_batch_set_launch: staged tiles need (threads, tile) = (128, 128), (128, 256) or "
+                             "(256, 256), got (%d, %d)", threads_x, tma_tile);
+  if (tma_tile == 0 && !batch_shape_ok(threads_x, rows))
+    return bfail(LBM_EINVAL, "lbm_batch_set_launch: shape (%d, %d) not compiled", threads_x, rows);
   if (blocks < -1) return bfail(LBM_EINVAL, "lbm_batch_set_launch: blocks=%d < -1", blocks);
-  if (prefetch_rows < 0 || prefetch_rows > 64)
-    return bfail(LBM_EINVAL, "lbm_batch_set_launch: prefetch_rows=%d outside [0, 64]", prefetch_rows);
-  if (threads_x != b->bx || rows != b->rows || (split != 0) != b->split) b->items_dirty = true;
+  if (prefetch_rows < 0 || prefetch_rows > 65536)
+    return bfail(LBM_EINVAL, "lbm_batch_set_launch: prefetch=%d outside [0, 65536]", prefetch_rows);
   b->bx = threads_x;
-  b->rows = rows;
+  b->rows = tma_tile ? 1 : rows;
   b->blocks = blocks;
   b->pf = prefetch_rows;
-  b->split = split != 0;
+  b->split = tma_tile != 0 || split != 0;
+  b->tile = tma_tile;
+  b->items_dirty = true;
   drop_batch_graphs(b);
   return LBM_OK;
 }
 
 int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_t* blocks, int32_t* prefetch_rows,
-                       int32_t* split, double* ms_per_step) {
+                       int32_t* split, int32_t* tma_tile, double* ms_per_step) {
   if (!b) return bfail(LBM_EINVAL, "lbm_batch_autotune: NULL handle");
   for (int k = 0; k < b->count; ++k)
     if (!b->initialised[k]) return bfail(LBM_ESTATE, "lbm_batch_autotune: instance %d not initialised", k);
@@ -636,46 +883,70 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
   BATCH_CUDA(cudaEventCreate(&e1));
   const int reps = (int)std::max<long long>(4, std::min<long long>(32, (1LL << 28) / std::max(b->cells, 1LL)));
   float best = 1e30f;
-  int bb = b->bx, br = b->rows, bk = b->blocks, bp = b->pf;
+  int bb = b->bx, br = b->rows, bk = b->blocks, bp = b->pf, bt = b->tile;
   bool bs = b->split;
   int rc = LBM_OK;
-  for (int split : {0, 1})
-  for (int bx : kBatchBX)
-    for (int r : kBatchRows) {
-      b->bx = bx;
-      b->rows = r;
-      b->split = split != 0;
-      b->items_dirty = true;
-      rc = build_items(b);
-      if (rc) break;
-      for (int mult : {-1, 1, 2, 4})  // -1: one block per item; k: k resident waves, persistent
-        for (int pf : {0, 1, 2, 6}) {  // 1: whole-tile prefetch; k > 1: k passes ahead
-          b->blocks = mult < 0 ? -1 : b->wave * mult;
-          b->pf = pf;
-          for (int s = 0; s < 2; ++s) enqueue_batch_step(b, s & 1, b->stream);
-          cudaEventRecord(e0, b->stream);
-          for (int s = 0; s < reps; ++s) enqueue_batch_step(b, s & 1, b->stream);
-          cudaEventRecord(e1, b->stream);
-          BATCH_CUDA(cudaEventSynchronize(e1));
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          ms /= reps;
-          if (ms < best) {
-            best = ms;
-            bb = bx;
-            br = r;
-            bk = b->blocks;
-            bp = pf;
-            bs = b->split;
-          }
-        }
+  auto time_it = [&]() -> float {
+    for (int s = 0; s < 2; ++s) enqueue_batch_step(b, s & 1, b->stream);
+    cudaEventRecord(e0, b->stream);
+    for (int s = 0; s < reps; ++s) enqueue_batch_step(b, s & 1, b->stream);
+    cudaEventRecord(e1, b->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms / reps;
+  };
+  auto keep = [&](float ms) {
+    if (ms < best) {
+      best = ms;
+      bb = b->bx;
+      br = b->rows;
+      bk = b->blocks;
+      bp = b->pf;
+      bs = b->split;
+      bt = b->tile;
     }
+  };
+  // register path: fused or split, tile shape, grid, prefetch
+  for (int sp : {0, 1})
+    for (int bx : kBatchBX)
+      for (int r : kBatchRows) {
+        b->bx = bx;
+        b->rows = r;
+        b->split = sp != 0;
+        b->tile = 0;
+        b->items_dirty = true;
+        rc = build_items(b);
+        if (rc) break;
+        for (int mult : {-1, 1, 2})  // -1: one block per item; k: k resident waves, persistent
+          for (int pf : {0, 1, 256}) {  // 1: own tile at start; k > 1: the tile k items ahead
+            b->blocks = mult < 0 ? -1 : b->wave * mult;
+            b->pf = pf;
+            keep(time_it());
+          }
+      }
+  // shared-memory path: tiles staged by bulk copies, persistent blocks
+  const int tma_pairs[3][2] = {{128, 128}, {128, 256}, {256, 256}};
+  for (const auto& tp : tma_pairs) {
+    if (rc) break;
+    b->bx = tp[0];
+    b->rows = 1;
+    b->tile = tp[1];
+    b->split = true;
+    b->blocks = 0;
+    b->pf = 0;
+    b->items_dirty = true;
+    rc = build_items(b);
+    if (rc) break;
+    keep(time_it());
+  }
   if (!rc) rc = batch_check_launch();
   b->bx = bb;
   b->rows = br;
   b->blocks = bk;
   b->pf = bp;
   b->split = bs;
+  b->tile = bt;
   b->items_dirty = true;
   int rc2 = build_items(b);
   BATCH_CUDA(cudaMemcpyAsync(b->pool[b->cur], backup, pb, cudaMemcpyDeviceToDevice, b->stream));
@@ -690,7 +961,18 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
   if (blocks) *blocks = bk;
   if (prefetch_rows) *prefetch_rows = bp;
   if (split) *split = bs ? 1 : 0;
+  if (tma_tile) *tma_tile = bt;
   if (ms_per_step) *ms_per_step = best;
+  return LBM_OK;
+}
+
+int lbm_batch_status(lbm_batch_t* b) {
+  if (!b) return bfail(LBM_EINVAL, "lbm_batch_status: NULL handle");
+  if (!b->d_err) return LBM_OK;
+  int h = 0;
+  BATCH_CUDA(cudaMemcpyAsync(&h, b->d_err, sizeof h, cudaMemcpyDeviceToHost, b->stream));
+  BATCH_CUDA(cudaStreamSynchronize(b->stream));
+  if (h) return bfail(LBM_ETIMEOUT, "lbm_batch_status: a staged-tile copy did not complete within its wait limit");
   return LBM_OK;
 }
 

@@ -52,6 +52,13 @@ struct Store<double> {
     __stcs(reinterpret_cast<double2*>(p), make_double2(o[0], o[1]));
   }
   static constexpr double kScale = 1.0;
+  // shared-memory copies of the stored values (tiles staged by bulk copies)
+  __device__ static void lds(const double* p, C (&o)[V]) {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    o[0] = t.x;
+    o[1] = t.y;
+  }
+  __device__ static C ld1s(const double* p) { return *p; }
   __device__ static C ld1(const double* p) { return __ldcs(p); }
   __device__ static C ldg1(const double* p) { return __ldg(p); }
   __device__ static void st1(double* p, C v) { *p = v; }
@@ -74,6 +81,14 @@ struct Store<float> {
     __stcs(reinterpret_cast<float4*>(p), make_float4(o[0], o[1], o[2], o[3]));
   }
   static constexpr float kScale = 1.0f;
+  __device__ static void lds(const float* p, C (&o)[V]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    o[0] = t.x;
+    o[1] = t.y;
+    o[2] = t.z;
+    o[3] = t.w;
+  }
+  __device__ static C ld1s(const float* p) { return *p; }
   __device__ static C ld1(const float* p) { return __ldcs(p); }
   __device__ static C ldg1(const float* p) { return __ldg(p); }
   __device__ static void st1(float* p, C v) { *p = v; }
@@ -117,6 +132,19 @@ struct Store<__half> {
     }
     __stcs(reinterpret_cast<uint4*>(p), make_uint4(w[0], w[1], w[2], w[3]));
   }
+  __device__ static void lds(const __half* p, C (&o)[V]) {
+    const uint4 t = *reinterpret_cast<const uint4*>(p);
+    const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      __half2 h2;
+      memcpy(&h2, &w[k], 4);
+      const float2 f = __half22float2(h2);
+      o[2 * k] = f.x;
+      o[2 * k + 1] = f.y;
+    }
+  }
+  __device__ static C ld1s(const __half* p) { return __half2float(*p); }
   __device__ static C ld1(const __half* p) { return __half2float(*p); }
   __device__ static void st1r(__half* p, C v) { *p = __float2half_rn(v); }
   __device__ static C ldg1(const __half* p) { return __half2float(__ldg(p)) * kHalfUnscale; }
@@ -150,6 +178,19 @@ struct Store<__nv_bfloat16> {
     __stcs(reinterpret_cast<uint4*>(p), make_uint4(w[0], w[1], w[2], w[3]));
   }
   static constexpr float kScale = 1.0f;
+  __device__ static void lds(const __nv_bfloat16* p, C (&o)[V]) {
+    const uint4 t = *reinterpret_cast<const uint4*>(p);
+    const uint32_t w[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      __nv_bfloat162 b2;
+      memcpy(&b2, &w[k], 4);
+      const float2 f = __bfloat1622float2(b2);
+      o[2 * k] = f.x;
+      o[2 * k + 1] = f.y;
+    }
+  }
+  __device__ static C ld1s(const __nv_bfloat16* p) { return __bfloat162float(*p); }
   __device__ static C ld1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
   __device__ static C ldg1(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
   __device__ static void st1(__nv_bfloat16* p, C v) { *p = __float2bfloat16_rn(v); }
@@ -345,7 +386,7 @@ __device__ __forceinline__ void node_moments_f64(const T* __restrict__ A, const 
 // float rounding of the perturbation itself.
 template <typename T>
 __device__ __forceinline__ void node_dmoments(const T* __restrict__ A, const Geom& g, int x, int y,
-                                              double (&m)[3]) {
+                                              typename Store<T>::C (&m)[3]) {
   using S = Store<T>;
   using C = typename S::C;
   const long long o = (long long)y * g.pitch + x;
@@ -355,9 +396,9 @@ __device__ __forceinline__ void node_dmoments(const T* __restrict__ A, const Geo
   C drho, jx, jy;
   moments(h, drho, jx, jy);
   const C inv = C(1) / (C(1) + drho);
-  m[0] = (double)drho;
-  m[1] = (double)(jx * inv);
-  m[2] = (double)(jy * inv);
+  m[0] = drho;
+  m[1] = jx * inv;
+  m[2] = jy * inv;
 }
 
 }  // namespace lbmk

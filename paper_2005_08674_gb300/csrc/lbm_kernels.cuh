@@ -186,29 +186,41 @@ __device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict
     h[i] = (q == 0 && known[i]) ? S::ldg1(A + i * g.plane + (long long)sy * g.pitch + sx) : C(0);
   }
 
-  double m[3] = {0.0, 0.0, 0.0};
-  if (open && q <= p.order) node_dmoments(A, g, x - q * nxn, y - q * nyn, m);
-  double m1[3], m2[3];
+  // lane q forms (rho - 1, ux, uy) at b - q n in the compute type; the quad
+  // then transposes them so that lane c (c < 3) holds component c at b,
+  // b - n, b - 2n and predicts and blends that component in FP64 -- three
+  // lanes share the FP64 work (GB300's FP64 pipe is narrow) -- and lane 0
+  // gathers the three blended components.
+  C mq[3] = {C(0), C(0), C(0)};
+  if (open && q <= p.order) node_dmoments(A, g, x - q * nxn, y - q * nyn, mq);
+  C t0[3], t1[3], t2[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    m1[c] = __shfl_down_sync(quad, m[c], 1, 4);
-    m2[c] = __shfl_down_sync(quad, m[c], 2, 4);
+    t0[c] = __shfl_sync(quad, mq[c], 0, 4);
+    t1[c] = __shfl_sync(quad, mq[c], 1, 4);
+    t2[c] = __shfl_sync(quad, mq[c], 2, 4);
   }
+  const int cq = q < 3 ? q : 0;
+  C mine = C(0);
+  {
+    // Eq. (nes_2): m_p = m_b - gamma d_n m along the outward unit normal;
+    // Eq. (nes_3): m_c = (1 - beta) m_p + beta m_0; component cq.
+    const double mb = (double)(cq == 0 ? t0[0] : (cq == 1 ? t0[1] : t0[2]));
+    const double m1 = (double)(cq == 0 ? t1[0] : (cq == 1 ? t1[1] : t1[2]));
+    const double m2 = (double)(cq == 0 ? t2[0] : (cq == 1 ? t2[1] : t2[2]));
+    const double m0 = cq == 0 ? p.m0[0] - 1.0 : p.m0[cq];
+    // 1 / |n| (GB300's FP64 divide is slow: multiply by the reciprocal)
+    const double inv_len = (nxn != 0 && nyn != 0) ? 0.70710678118654752 : 1.0;
+    const double dn = p.order == 2 ? (3.0 * mb - 4.0 * m1 + m2) * (0.5 * inv_len) : (mb - m1) * inv_len;
+    const double mp = mb - p.gamma * dn;
+    mine = C((1.0 - p.beta) * mp + p.beta * m0);
+  }
+  C mc[3];  // (rho_c - 1, u_c)
+#pragma unroll
+  for (int c = 0; c < 3; ++c) mc[c] = __shfl_sync(quad, mine, c, 4);
   if (q != 0) return;
 
   if (open) {
-    // Eq. (nes_2): m_p = m_b - gamma d_n m along the outward unit normal;
-    // Eq. (nes_3): m_c = (1 - beta) m_p + beta m_0.
-    // 1 / |n| (GB300's FP64 divide is slow: multiply by the reciprocal)
-    const double inv_len = (nxn != 0 && nyn != 0) ? 0.70710678118654752 : 1.0;
-    const double m0[3] = {p.m0[0] - 1.0, p.m0[1], p.m0[2]};
-    double mc[3];  // (rho_c - 1, u_c)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const double dn = p.order == 2 ? (3.0 * m[c] - 4.0 * m1[c] + m2[c]) * (0.5 * inv_len) : (m[c] - m1[c]) * inv_len;
-      const double mp = m[c] - p.gamma * dn;
-      mc[c] = (1.0 - p.beta) * mp + p.beta * m0[c];
-    }
     // a velocity edge keeps the predicted density and imposes its velocity
     // (left/right edges win at corners)
     const int side = (x == 0 && p.vel[0])             ? 0
@@ -217,14 +229,14 @@ __device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict
                      : (y == g.ny - 1 && p.vel[3])    ? 3
                                                       : -1;
     if (side >= 0) {
-      mc[1] = p.uw[side][0];
-      mc[2] = p.uw[side][1];
+      mc[1] = C(p.uw[side][0]);
+      mc[2] = C(p.uw[side][1]);
     }
 
     // Eqs. (nes_0), (nes_1): f_in = f_in^eq(m_c) + f_out - f_out^eq(m_c)
-    const C drho_c = C(mc[0]);
+    const C drho_c = mc[0];
     C e[9];
-    equilibrium(drho_c, C(mc[1]), C(mc[2]), e);
+    equilibrium(drho_c, mc[1], mc[2], e);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const int o = opp(i);
@@ -235,8 +247,8 @@ __device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict
     C drho, jx, jy;
     moments(h, drho, jx, jy);
     const C d_rho = drho - drho_c;
-    const C d_jx = jx - C((1.0 + mc[0]) * mc[1]);
-    const C d_jy = jy - C((1.0 + mc[0]) * mc[2]);
+    const C d_jx = jx - (C(1) + mc[0]) * mc[1];
+    const C d_jy = jy - (C(1) + mc[0]) * mc[2];
     const C kap = C(p.kappa);
 #pragma unroll
     for (int i = 0; i < 9; ++i) h[i] -= wt<C>(i) * (d_rho + kap * (C(cx(i)) * d_jx + C(cy(i)) * d_jy));

@@ -76,8 +76,9 @@ _SIGS = {
     "lbm_batch_steps_done": (ctypes.c_int64, [_vp]),
     "lbm_batch_get_macros": (ctypes.c_int, [_vp, _i32, _vp, _vp, _vp]),
     "lbm_batch_unstable_nodes": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(ctypes.c_int64)]),
-    "lbm_batch_set_launch": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32, _i32]),
-    "lbm_batch_autotune": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p, _dp]),
+    "lbm_batch_set_launch": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32, _i32, _i32]),
+    "lbm_batch_autotune": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _dp]),
+    "lbm_batch_status": (ctypes.c_int, [_vp]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -452,17 +453,20 @@ def lbm_batch_unstable_nodes(b, k) -> int:
 
 
 def lbm_batch_set_launch(b, threads_x: int, rows: int, blocks: int = -1, prefetch_rows: int = 0,
-                         split: int = 0):
-    return _check(_L.lbm_batch_set_launch(b, threads_x, rows, blocks, prefetch_rows, split))
+                         split: int = 0, tma_tile: int = 0):
+    return _check(_L.lbm_batch_set_launch(b, threads_x, rows, blocks, prefetch_rows, split, tma_tile))
 
 
 def lbm_batch_autotune(b):
-    """(threads_x, rows, blocks, prefetch_rows, split, ms_per_step) of the fastest batched launch."""
-    bx, rows, blk, pf, sp, ms = (ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(),
-                                 ctypes.c_int32(), ctypes.c_double())
-    _check(_L.lbm_batch_autotune(b, ctypes.byref(bx), ctypes.byref(rows), ctypes.byref(blk), ctypes.byref(pf),
-                                 ctypes.byref(sp), ctypes.byref(ms)))
-    return bx.value, rows.value, blk.value, pf.value, sp.value, ms.value
+    """(threads_x, rows, blocks, prefetch_rows, split, tma_tile, ms_per_step) of the fastest batched launch."""
+    v = [ctypes.c_int32() for _ in range(6)]
+    ms = ctypes.c_double()
+    _check(_L.lbm_batch_autotune(b, *[ctypes.byref(x) for x in v], ctypes.byref(ms)))
+    return tuple(x.value for x in v) + (ms.value,)
+
+
+def lbm_batch_status(b):
+    return _check(_L.lbm_batch_status(b))
 
 
 class Batch:
@@ -535,6 +539,9 @@ class Batch:
     def autotune(self):
         return lbm_batch_autotune(self.b)
 
-    def set_launch(self, threads_x, rows, blocks=-1, prefetch_rows=0, split=0):
-        lbm_batch_set_launch(self.b, threads_x, rows, blocks, prefetch_rows, split)
+    def set_launch(self, threads_x, rows, blocks=-1, prefetch_rows=0, split=0, tma_tile=0):
+        lbm_batch_set_launch(self.b, threads_x, rows, blocks, prefetch_rows, split, tma_tile)
         return self
+
+    def status(self):
+        return lbm_batch_status(self.b)

@@ -62,14 +62,14 @@ def test_batch_f64_matches_oracle(lbm):
             assert err <= 1e-12, (w.name, err)
 
 
-@pytest.mark.parametrize("shape", [(64, 1, 0, 0, 0), (128, 2, 0, 1, 1), (256, 4, 152, 0, 0), (64, 4, 7, 1, 1),
-                                   (128, 4, -1, 1, 0), (256, 1, -1, 0, 1)])
+@pytest.mark.parametrize("shape", [(64, 1, 0, 0, 0, 0), (128, 2, 0, 1, 1, 0), (256, 4, 152, 0, 0, 0), (64, 4, 7, 64, 1, 0), (128, 1, 0, 0, 1, 128), (128, 1, 0, 0, 1, 256), (256, 1, 0, 0, 1, 256),
+                                   (128, 4, -1, 1, 0, 0), (256, 1, -1, 0, 1, 0)])
 def test_batch_launch_shapes_agree(lbm, shape):
     """Every tile shape, grid size (one block per item, persistent waves, a
     grid far smaller than the work list) and prefetch gives the same bits."""
     ws = small_batch()
     outs = []
-    for sh in [(128, 1, -1, 0, 0), shape]:
+    for sh in [(128, 1, -1, 0, 0, 0), shape]:
         with lbm.Batch(ws, storage="f32") as b:
             for k, w in enumerate(ws):
                 b.init(k, *w.fields())
