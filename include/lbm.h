@@ -267,11 +267,13 @@ int lbm_batch_unstable_nodes(lbm_batch_t* b, int32_t k, int64_t* count);
  * k items further down the list (at most 65536); `split` = 0 runs NSBC chunks and bulk tiles in ONE launch
  * per step, 1 runs the NSBC chunks as a second launch beside the bulk tiles
  * (the bulk launch then keeps the single-domain kernel's register budget).
- * `tma_tile` > 0 selects the shared-memory path instead: tiles of that many
- * vectors (128 or 256, with threads_x 128, or 256 with 256) are staged by
- * cp.async.bulk copies completing on an mbarrier, double-buffered in
- * persistent blocks (one resident wave; `rows`, `blocks`, `prefetch_rows`
- * and `split` are then ignored, the NSBC chunks run beside). */
+ * `tma_tile` > 0 selects the shared-memory path instead: ONE persistent
+ * launch per step whose blocks take NSBC chunks and bulk tiles from a shared
+ * counter; tiles of `tma_tile` vectors (128 or 256, with threads_x 128, or
+ * 256 with 256) are staged by cp.async.bulk copies completing on an
+ * mbarrier, the next tile's copy in flight while the current item is
+ * worked on.  `blocks` (0 = one resident wave) sets the grid; `rows`,
+ * `prefetch_rows` and `split` are ignored. */
 int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_t blocks, int32_t prefetch_rows,
                          int32_t split, int32_t tma_tile);
 /* Time every compiled tile shape, grid size, prefetch setting and split, and

@@ -89,7 +89,7 @@ struct lbm_batch {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int wave = 1;                        // resident blocks on the device for the current shape
   int tile = 0;                        // > 0: bulk tiles of this many vectors staged by bulk copies
-  int* d_err = nullptr;                // set by a kernel whose bounded wait gave up
+  int* d_err = nullptr;                // [0] work counter, [1] blocks done, [2] a bounded wait gave up
   bool items_dirty = true;
   std::vector<char> initialised;
   int cur = 0;
@@ -263,17 +263,93 @@ __device__ __forceinline__ void issue_tile(const T* __restrict__ A, const InstDe
   }
 }
 
+// Collide the nodes of a staged bulk tile (slot `sl`) and store them to B.
+// 16-bit storages are collided in half vectors (4 nodes per thread) so the
+// per-thread register footprint matches the f32 path.
 template <typename T, int BX, int MODEL, int TILE>
-__global__ void __launch_bounds__(BX) batch_tma_kernel(const T* __restrict__ A, T* __restrict__ B,
-                                                       const InstDev* __restrict__ inst,
-                                                       const int4* __restrict__ items, int i0, int i1, double s_e,
-                                                       double s_eps, double s_q, int* __restrict__ err) {
+__device__ __forceinline__ void collide_tile(const unsigned char* sl, const InstDev& d, const int4& w,
+                                             T* __restrict__ B, const lbmk::Rates<typename lbmk::Store<T>::C>& r) {
   using S = lbmk::Store<T>;
   using C = typename S::C;
   constexpr int V = S::V;
   constexpr int SLOT = (TILE + 2) * 16;
+  constexpr int SPLIT = sizeof(T) == 2 ? 2 : 1;
+  constexpr int CPT = V / SPLIT;
+  const int nvec = d.pitch / V;  // the batch pitch is a whole number of vectors
+  T* b = B + d.off;
+#pragma unroll 1
+  for (int u2 = threadIdx.x; u2 < w.z * SPLIT; u2 += BX) {
+    const int u = u2 / SPLIT, part = u2 - u * SPLIT;
+    const int j = w.y + u;
+    const int y = 1 + j / nvec;
+    const int x0 = (j - (y - 1) * nvec) * V + part * CPT;
+    C v[9][CPT], lf[9], rt[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const T* e = reinterpret_cast<const T*>(sl + i * SLOT) + (u + 1) * V + part * CPT;
+      if constexpr (SPLIT == 1)
+        S::lds(e, v[i]);
+      else
+        S::ldsp(e, v[i]);
+      lf[i] = S::ld1s(e - 1);    // x0 - 1 of the same (shifted) row
+      rt[i] = S::ld1s(e + CPT);  // x0 + CPT
+    }
+    C o[9][CPT];
+#pragma unroll
+    for (int kk = 0; kk < CPT; ++kk) {
+      C h[9];
+      h[0] = v[0][kk];
+      h[1] = kk == 0 ? lf[1] : v[1][kk - 1];
+      h[2] = kk == CPT - 1 ? rt[2] : v[2][kk + 1];
+      h[3] = v[3][kk];
+      h[4] = v[4][kk];
+      h[5] = kk == 0 ? lf[5] : v[5][kk - 1];
+      h[6] = kk == CPT - 1 ? rt[6] : v[6][kk + 1];
+      h[7] = kk == CPT - 1 ? rt[7] : v[7][kk + 1];
+      h[8] = kk == 0 ? lf[8] : v[8][kk - 1];
+      lbmk::collide<MODEL>(h, r, C(S::kScale));
+#pragma unroll
+      for (int i = 0; i < 9; ++i) o[i][kk] = h[i];
+    }
+    const long long r0 = (long long)y * d.pitch + x0;
+    if (x0 >= 1 && x0 + CPT <= d.nx - 1) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        if constexpr (SPLIT == 1)
+          S::st(b + i * d.plane + r0, o[i]);
+        else
+          S::stp(b + i * d.plane + r0, o[i]);
+      }
+    } else {
+#pragma unroll
+      for (int kk = 0; kk < CPT; ++kk) {
+        const int x = x0 + kk;
+        if (x >= 1 && x <= d.nx - 2) {
+#pragma unroll
+          for (int i = 0; i < 9; ++i) S::st1r(b + i * d.plane + r0 + kk, o[i][kk]);
+        }
+      }
+    }
+  }
+}
+
+// The whole step of every instance in ONE persistent launch: blocks take
+// work items from a shared counter (sched[0]) -- NSBC chunks, computed from
+// global memory, and bulk tiles, staged into shared memory by the bulk-copy
+// engine.  While a block works on its current item, the copy for the next
+// bulk tile it took is already in flight (two slots).  The last block out
+// resets the counters for the next step.  sched[2] is set if a bounded wait
+// on a copy gave up.
+template <typename T, int BX, int MODEL, int TILE>
+__global__ void __launch_bounds__(BX) batch_tma_kernel(const T* __restrict__ A, T* __restrict__ B,
+                                                       const InstDev* __restrict__ inst,
+                                                       const int4* __restrict__ items, int n_items, lbmk::Nsbc p,
+                                                       double s_e, double s_eps, double s_q, int* __restrict__ sched) {
+  using C = typename lbmk::Store<T>::C;
+  constexpr int SLOT = (TILE + 2) * 16;
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int s_cur, s_cur_slot, s_next, s_next_slot, s_ok;
   const int tid = threadIdx.x;
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -282,101 +358,93 @@ __global__ void __launch_bounds__(BX) batch_tma_kernel(const T* __restrict__ A, 
   }
   __syncthreads();
   uint32_t parity[2] = {0u, 0u};
-  int k = 0;
-  if (tid == 0 && i0 + (int)blockIdx.x < i1) {
-    const int4 w = items[i0 + blockIdx.x];
-    issue_tile<T, TILE>(A, inst[w.x], w, smem, &bar[0]);
+  int ns = 0;  // thread 0: slot the next copy goes to
+  if (tid == 0) {
+    const int c = atomicAdd(&sched[0], 1);
+    s_cur = c;
+    s_cur_slot = -1;
+    if (c < n_items) {
+      const int4 w = items[c];
+      if (w.x >= 0) {
+        issue_tile<T, TILE>(A, inst[w.x], w, smem + ns * 9 * SLOT, &bar[ns]);
+        s_cur_slot = ns;
+        ns ^= 1;
+      }
+    }
   }
-  for (int it = i0 + blockIdx.x; it < i1; it += gridDim.x, ++k) {
-    const int cur = k & 1;
-    const int nit = it + gridDim.x;
-    if (tid == 0 && nit < i1) {
-      // the other slot was released by the barrier that closed the last pass
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      const int4 wn = items[nit];
-      issue_tile<T, TILE>(A, inst[wn.x], wn, smem + (cur ^ 1) * 9 * SLOT, &bar[cur ^ 1]);
-    }
-    const int4 w = items[it];
-    const InstDev d = inst[w.x];
-    // thread 0 waits (bounded) and tells the block, so that the whole block
-    // takes the same way out if the copy never lands
-    __shared__ int landed;
-    if (tid == 0) landed = mbar_wait(&bar[cur], parity[cur]) ? 1 : 0;
-    __syncthreads();
-    if (!landed) {
-      // record it, give the copies in flight a bounded chance to finish, and
-      // leave without touching the tile
-      if (tid == 0) {
-        atomicExch(err, 1);
-        mbar_wait(&bar[cur], parity[cur]);
-        if (nit < i1) mbar_wait(&bar[cur ^ 1], parity[cur ^ 1]);
-      }
-      return;
-    }
-    mbar_wait(&bar[cur], parity[cur]);  // completes at once; orders this thread after the copy
-    parity[cur] ^= 1u;
-    const lbmk::Geom g{d.nx, d.ny, d.pitch, d.plane};
-    const lbmk::Rates<C> r{C(d.omega), C(s_e), C(s_eps), C(s_q)};
-    const unsigned char* sl = smem + cur * 9 * SLOT;
-    const int nvec = d.pitch / V;  // the batch pitch is a whole number of vectors
-    T* b = B + d.off;
-#pragma unroll 1
-    for (int u = tid; u < w.z; u += BX) {
-      const int j = w.y + u;
-      const int y = 1 + j / nvec;
-      const int x0 = (j - (y - 1) * nvec) * V;
-      C v[9][V], lf[9], rt[9];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const T* e = reinterpret_cast<const T*>(sl + i * SLOT) + (u + 1) * V;
-        S::lds(e, v[i]);
-        lf[i] = S::ld1s(e - 1);  // x0 - 1 of the same (shifted) row
-        rt[i] = S::ld1s(e + V);  // x0 + V
-      }
-      C o[9][V];
-#pragma unroll
-      for (int kk = 0; kk < V; ++kk) {
-        C h[9];
-        h[0] = v[0][kk];
-        h[1] = kk == 0 ? lf[1] : v[1][kk - 1];
-        h[2] = kk == V - 1 ? rt[2] : v[2][kk + 1];
-        h[3] = v[3][kk];
-        h[4] = v[4][kk];
-        h[5] = kk == 0 ? lf[5] : v[5][kk - 1];
-        h[6] = kk == V - 1 ? rt[6] : v[6][kk + 1];
-        h[7] = kk == V - 1 ? rt[7] : v[7][kk + 1];
-        h[8] = kk == 0 ? lf[8] : v[8][kk - 1];
-        lbmk::collide<MODEL>(h, r, C(S::kScale));
-#pragma unroll
-        for (int i = 0; i < 9; ++i) o[i][kk] = h[i];
-      }
-      const long long r0 = (long long)y * g.pitch + x0;
-      if (x0 >= 1 && x0 + V <= g.nx - 1) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) S::st(b + i * g.plane + r0, o[i]);
-      } else {
-#pragma unroll
-        for (int kk = 0; kk < V; ++kk) {
-          const int x = x0 + kk;
-          if (x >= 1 && x <= g.nx - 2) {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) S::st1r(b + i * g.plane + r0 + kk, o[i][kk]);
-          }
+  __syncthreads();
+  for (;;) {
+    const int cur = s_cur, cslot = s_cur_slot;
+    if (cur >= n_items) break;  // uniform: read after a barrier
+    __syncthreads();            // everyone has read s_cur / s_cur_slot
+    if (tid == 0) {
+      const int c = atomicAdd(&sched[0], 1);
+      s_next = c;
+      s_next_slot = -1;
+      if (c < n_items) {
+        const int4 wn = items[c];
+        if (wn.x >= 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          issue_tile<T, TILE>(A, inst[wn.x], wn, smem + ns * 9 * SLOT, &bar[ns]);
+          s_next_slot = ns;
+          ns ^= 1;
         }
       }
     }
-    __syncthreads();  // every thread is done with this slot
+    const int4 w = items[cur];
+    const bool edge = w.x < 0;
+    const InstDev d = inst[edge ? ~w.x : w.x];
+    const lbmk::Rates<C> r{C(d.omega), C(s_e), C(s_eps), C(s_q)};
+    if (edge) {
+      lbmk::Nsbc q = p;
+      q.m0[0] = d.m0[0];
+      q.m0[1] = d.m0[1];
+      q.m0[2] = d.m0[2];
+      const lbmk::Geom g{d.nx, d.ny, d.pitch, d.plane};
+      const int node = w.y + (tid >> 2);
+      if (node < w.y + w.z) lbmk::nsbc_node<T, MODEL>(A + d.off, B + d.off, g, q, r, node, tid & 3);
+    } else {
+      // thread 0 waits (bounded) and tells the block, so that the whole block
+      // takes the same way out if the copy never lands
+      if (tid == 0) s_ok = mbar_wait(&bar[cslot], parity[cslot]) ? 1 : 0;
+      __syncthreads();
+      if (!s_ok) {
+        if (tid == 0) {
+          atomicExch(&sched[2], 1);
+          mbar_wait(&bar[cslot], parity[cslot]);
+          if (s_next_slot >= 0) mbar_wait(&bar[s_next_slot], parity[s_next_slot]);
+        }
+        break;
+      }
+      mbar_wait(&bar[cslot], parity[cslot]);  // completes at once; orders this thread after the copy
+      parity[cslot] ^= 1u;
+      collide_tile<T, BX, MODEL, TILE>(smem + cslot * 9 * SLOT, d, w, B, r);
+    }
+    __syncthreads();  // done with the current slot; s_next visible
+    if (tid == 0) {
+      s_cur = s_next;
+      s_cur_slot = s_next_slot;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&sched[1], 1) == (int)gridDim.x - 1) {
+      sched[0] = 0;
+      sched[1] = 0;
+    }
   }
 }
 
 template <typename T, int BX, int MODEL, int TILE>
-void launch_tma(const lbm_batch_t* b, int from, cudaStream_t s, int grid, int i0, int i1, int* err) {
+void launch_tma(const lbm_batch_t* b, int from, cudaStream_t s, int grid) {
   // the dynamic shared-memory limit was raised by wave_blocks() when the work
   // list was built (never inside a stream capture)
   constexpr int smem = 2 * 9 * (TILE + 2) * 16;
   batch_tma_kernel<T, BX, MODEL, TILE><<<grid, BX, smem, s>>>(static_cast<const T*>(b->pool[from]),
                                                               static_cast<T*>(b->pool[1 - from]), b->d_inst,
-                                                              b->d_items, i0, i1, b->s_e, b->s_eps, b->s_q, err);
+                                                              b->d_items, b->n_items, b->nsbc, b->s_e, b->s_eps,
+                                                              b->s_q, b->d_err);
 }
 
 template <typename T, int BX, int PART>
@@ -458,24 +526,15 @@ void enqueue_batch_step(const lbm_batch_t* b, int from, cudaStream_t s) {
   bdispatch(b->storage, [&](auto tag) {
     using T = decltype(tag);
     if (b->tile > 0) {
-      // NSBC chunks beside the shared-memory bulk path (persistent, one wave)
-      const int n_edge = b->n_items - b->n_bulk_items;
-      cudaEventRecord(b->ev_fork, s);
-      cudaStreamWaitEvent(b->side, b->ev_fork, 0);
-      with_bx(b->bx, [&](auto bxc) {
-        constexpr int BX = decltype(bxc)::value;
-        launch_part<T, BX, 2>(b, from, b->side, std::max(1, n_edge), 0, n_edge);
-      });
+      // the whole step in one persistent launch (NSBC chunks and staged tiles)
       with_tma(b->bx, b->tile, [&](auto bxc, auto tc) {
         constexpr int BX = decltype(bxc)::value, TILE = decltype(tc)::value;
-        const int grid = std::max(1, std::min(b->n_bulk_items, b->wave));
+        const int grid = std::max(1, std::min(b->n_items, b->blocks > 0 ? b->blocks : b->wave));
         if (b->collision == 1)
-          launch_tma<T, BX, 1, TILE>(b, from, s, grid, n_edge, b->n_items, b->d_err);
+          launch_tma<T, BX, 1, TILE>(b, from, s, grid);
         else
-          launch_tma<T, BX, 0, TILE>(b, from, s, grid, n_edge, b->n_items, b->d_err);
+          launch_tma<T, BX, 0, TILE>(b, from, s, grid);
       });
-      cudaEventRecord(b->ev_join, b->side);
-      cudaStreamWaitEvent(s, b->ev_join, 0);
       return;
     }
     with_bx(b->bx, [&](auto bxc) {
@@ -530,6 +589,20 @@ int build_items(lbm_batch_t* b) {
     for (int j0 = 0; j0 < total; j0 += per_item) items.push_back(make_int4(k, j0, std::min(per_item, total - j0), 0));
   }
   const int n_bulk = (int)items.size() - n_edge;
+  if (b->tile > 0 && n_edge > 0) {
+    // one dynamically scheduled list: spread the NSBC chunks evenly among the
+    // staged tiles so that their latency overlaps with copies in flight
+    std::vector<int4> mixed;
+    mixed.reserve(items.size());
+    long long e = 0;
+    for (int t = 0; t < n_bulk; ++t) {
+      mixed.push_back(items[n_edge + t]);
+      const long long want = (long long)(t + 1) * n_edge / n_bulk;
+      for (; e < want; ++e) mixed.push_back(items[e]);
+    }
+    for (; e < n_edge; ++e) mixed.push_back(items[e]);
+    items.swap(mixed);
+  }
   if (b->d_items) cudaFree(b->d_items);
   b->d_items = nullptr;
   BATCH_CUDA(cudaMalloc(&b->d_items, items.size() * sizeof(int4)));
@@ -555,8 +628,8 @@ int ensure_batch_memory(lbm_batch_t* b) {
     b->bound = true;
   }
   if (!b->d_err) {
-    BATCH_CUDA(cudaMalloc(&b->d_err, sizeof(int)));
-    BATCH_CUDA(cudaMemset(b->d_err, 0, sizeof(int)));
+    BATCH_CUDA(cudaMalloc(&b->d_err, 4 * sizeof(int)));  // work counter, blocks done, error flag
+    BATCH_CUDA(cudaMemset(b->d_err, 0, 4 * sizeof(int)));
   }
   if (!b->d_inst) {
     BATCH_CUDA(cudaMalloc(&b->d_inst, b->inst.size() * sizeof(InstDev)));
@@ -859,7 +932,7 @@ int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_
   b->rows = tma_tile ? 1 : rows;
   b->blocks = blocks;
   b->pf = prefetch_rows;
-  b->split = tma_tile != 0 || split != 0;
+  b->split = tma_tile == 0 && split != 0;
   b->tile = tma_tile;
   b->items_dirty = true;
   drop_batch_graphs(b);
@@ -932,7 +1005,7 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
     b->bx = tp[0];
     b->rows = 1;
     b->tile = tp[1];
-    b->split = true;
+    b->split = false;
     b->blocks = 0;
     b->pf = 0;
     b->items_dirty = true;
@@ -970,7 +1043,7 @@ int lbm_batch_status(lbm_batch_t* b) {
   if (!b) return bfail(LBM_EINVAL, "lbm_batch_status: NULL handle");
   if (!b->d_err) return LBM_OK;
   int h = 0;
-  BATCH_CUDA(cudaMemcpyAsync(&h, b->d_err, sizeof h, cudaMemcpyDeviceToHost, b->stream));
+  BATCH_CUDA(cudaMemcpyAsync(&h, b->d_err + 2, sizeof h, cudaMemcpyDeviceToHost, b->stream));
   BATCH_CUDA(cudaStreamSynchronize(b->stream));
   if (h) return bfail(LBM_ETIMEOUT, "lbm_batch_status: a staged-tile copy did not complete within its wait limit");
   return LBM_OK;

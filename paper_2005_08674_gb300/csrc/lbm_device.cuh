@@ -145,6 +145,25 @@ struct Store<__half> {
     }
   }
   __device__ static C ld1s(const __half* p) { return __half2float(*p); }
+  // half vectors (4 nodes, 8 bytes): shared-memory load and streaming store
+  __device__ static void ldsp(const __half* p, C (&o)[4]) {
+    const uint2 t = *reinterpret_cast<const uint2*>(p);
+    __half2 a, b;
+    memcpy(&a, &t.x, 4);
+    memcpy(&b, &t.y, 4);
+    const float2 fa = __half22float2(a), fb = __half22float2(b);
+    o[0] = fa.x;
+    o[1] = fa.y;
+    o[2] = fb.x;
+    o[3] = fb.y;
+  }
+  __device__ static void stp(__half* p, const C (&o)[4]) {
+    const __half2 a = __floats2half2_rn(o[0], o[1]), b = __floats2half2_rn(o[2], o[3]);
+    uint2 t;
+    memcpy(&t.x, &a, 4);
+    memcpy(&t.y, &b, 4);
+    __stcs(reinterpret_cast<uint2*>(p), t);
+  }
   __device__ static C ld1(const __half* p) { return __half2float(*p); }
   __device__ static void st1r(__half* p, C v) { *p = __float2half_rn(v); }
   __device__ static C ldg1(const __half* p) { return __half2float(__ldg(p)) * kHalfUnscale; }
@@ -191,6 +210,24 @@ struct Store<__nv_bfloat16> {
     }
   }
   __device__ static C ld1s(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+  __device__ static void ldsp(const __nv_bfloat16* p, C (&o)[4]) {
+    const uint2 t = *reinterpret_cast<const uint2*>(p);
+    __nv_bfloat162 a, b;
+    memcpy(&a, &t.x, 4);
+    memcpy(&b, &t.y, 4);
+    const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+    o[0] = fa.x;
+    o[1] = fa.y;
+    o[2] = fb.x;
+    o[3] = fb.y;
+  }
+  __device__ static void stp(__nv_bfloat16* p, const C (&o)[4]) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(o[0], o[1]), b = __floats2bfloat162_rn(o[2], o[3]);
+    uint2 t;
+    memcpy(&t.x, &a, 4);
+    memcpy(&t.y, &b, 4);
+    __stcs(reinterpret_cast<uint2*>(p), t);
+  }
   __device__ static C ld1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
   __device__ static C ldg1(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
   __device__ static void st1(__nv_bfloat16* p, C v) { *p = __float2bfloat16_rn(v); }
