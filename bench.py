@@ -427,6 +427,30 @@ def run_ours(args, rank, world, local_rank):
             s2.close()
             del s2
             torch.cuda.empty_cache()
+        # the convected-vortex and small-pulse workloads at their own sizes
+        # (their populations fit in the 129 MB L2, so these are not HBM rates)
+        from paper_2005_08674_gb300 import inputs as _inp
+        for label, wl, st, kw in (
+                ("vortex-400_mrt_f32", _inp.vortex_400(), "f32",
+                 dict(collision="mrt", mrt_rates=(1.4, 1.4, 1.2))),
+                ("pulse-200_f64", _inp.pulse_200(), "f64", {})):
+            s3 = lbm.Simulation(wl.nx, wl.ny, wl.tau, wl.farfield_rho, wl.farfield_u, storage=st, **kw)
+            s3.init(*wl.fields())
+            s3.autotune()
+            s3.step(args.warmup)
+            torch.cuda.synchronize()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(s3.stream)
+            s3.step(wl.steps)
+            a1.record(s3.stream)
+            torch.cuda.synchronize()
+            vms = a0.elapsed_time(a1)
+            variants[label] = {"mlups": world * wl.cells * wl.steps / (vms * 1e-3) / 1e6, "steps": wl.steps,
+                               "cells": wl.cells, "storage": st,
+                               "note": f"{lbm.lbm_buffer_bytes(s3.h) / 1e6:.1f} MB per buffer: L2-resident"}
+            s3.close()
+            del s3
         # batched: 256 independent instances, one persistent launch per step
         from paper_2005_08674_gb300 import inputs
         ws = inputs.batch_instances()

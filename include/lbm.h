@@ -162,6 +162,14 @@ int lbm_get_macros_device(lbm_t* h, double* d_rho, double* d_ux, double* d_uy);
 int lbm_get_populations(lbm_t* h, double* f);
 int lbm_set_populations(lbm_t* h, const double* f);
 
+/* Checkpoint / resume: the current population buffer exactly as stored
+ * (lbm_buffer_bytes() bytes, the handle's storage type and layout) to or
+ * from HOST memory, with the step count.  A state loaded into a handle of
+ * the same size, storage and parameters continues bit for bit like the run
+ * it was saved from.  Both synchronise. */
+int lbm_save_state(lbm_t* h, void* host, size_t bytes, int64_t* steps);
+int lbm_load_state(lbm_t* h, const void* host, size_t bytes, int64_t steps);
+
 /* FP64 reductions over all nodes, used for the reflection measure and as an
  * instability check.  If ref_rho is non-NULL, ref_* are DEVICE [.][ref_pitch]
  * double fields whose element [0] is aligned with node (0, 0) of this
@@ -285,6 +293,14 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
  * the batch was created (the step then left those tiles untouched); LBM_OK
  * otherwise.  Synchronises. */
 int lbm_batch_status(lbm_batch_t* b);
+
+/* Failure-detection check of the bounded device-side wait used by the
+ * shared-memory path: one block waits on an mbarrier that nothing arrives
+ * on, gives up after budget_cycles SM clock cycles (at most 4e9), and
+ * returns normally.  Returns LBM_ETIMEOUT when the wait gave up (the
+ * expected outcome), LBM_OK if it did not, LBM_ECUDA on a CUDA error.
+ * Allocates and frees one int of device memory; synchronises. */
+int lbm_wait_selftest(int64_t budget_cycles);
 
 /* Per-launch timing.  While enabled, lbm_step launches every step directly
  * (no graph) on the handle's stream with CUDA events around the bulk

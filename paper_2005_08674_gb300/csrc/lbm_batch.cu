@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(BX) batch_step_kernel(const T* __restrict__ A,
 // next tile is in flight while the current one is collided, so the bytes in
 // flight are bounded by shared memory, not by registers.
 // ---------------------------------------------------------------------------
-constexpr int kTmaWaitLimit = 1 << 20;  // try_wait rounds before giving up (>= ~1 s)
+constexpr long long kTmaWaitCycles = 2000000000LL;  // ~1 s of SM clock before a wait gives up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -212,10 +212,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
-// Bounded wait for phase `parity` of the barrier; false after kTmaWaitLimit rounds.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// Bounded wait for phase `parity` of the barrier: false once `budget` SM
+// clock cycles have passed without the phase completing.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget = kTmaWaitCycles) {
   const uint32_t a = smem_u32(bar);
-  for (int i = 0; i < kTmaWaitLimit; ++i) {
+  const long long t0 = clock64();
+  do {
     uint32_t done;
     asm volatile(
         "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
@@ -223,8 +225,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
-  }
+  } while (clock64() - t0 < budget);
   return false;
+}
+
+// A wait on a barrier nothing ever arrives on: it must give up after its
+// budget and report it through *flag (the kernel then returns normally).
+__global__ void wait_selftest_kernel(long long budget, int* flag) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *flag = mbar_wait(&bar, 0u, budget) ? 2 : 1;
 }
 
 __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -1036,6 +1050,24 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
   if (split) *split = bs ? 1 : 0;
   if (tma_tile) *tma_tile = bt;
   if (ms_per_step) *ms_per_step = best;
+  return LBM_OK;
+}
+
+int lbm_wait_selftest(int64_t budget_cycles) {
+  if (budget_cycles <= 0 || budget_cycles > 4000000000LL)
+    return bfail(LBM_EINVAL, "lbm_wait_selftest: budget %lld outside (0, 4e9] cycles", (long long)budget_cycles);
+  int* d = nullptr;
+  BATCH_CUDA(cudaMalloc(&d, sizeof(int)));
+  cudaError_t e = cudaMemset(d, 0, sizeof(int));
+  int h = 0;
+  if (e == cudaSuccess) {
+    wait_selftest_kernel<<<1, 32>>>(budget_cycles, d);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return bfail(LBM_ECUDA, "lbm_wait_selftest: %s", cudaGetErrorString(e));
+  if (h == 1) return bfail(LBM_ETIMEOUT, "lbm_wait_selftest: the bounded wait gave up as it should");
   return LBM_OK;
 }
 

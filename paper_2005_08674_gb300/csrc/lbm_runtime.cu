@@ -569,6 +569,32 @@ int lbm_set_populations(lbm_t* h, const double* f) {
   return LBM_OK;
 }
 
+int lbm_save_state(lbm_t* h, void* host, size_t bytes, int64_t* steps) {
+  if (!h || !host) return fail(LBM_EINVAL, "lbm_save_state: NULL argument");
+  if (!h->initialised) return fail(LBM_ESTATE, "lbm_save_state: call lbm_init first");
+  if (bytes != lbm_buffer_bytes(h))
+    return fail(LBM_EINVAL, "lbm_save_state: %zu bytes given, the state is %zu", bytes, lbm_buffer_bytes(h));
+  LBM_CUDA(cudaMemcpyAsync(host, h->buf[h->cur], bytes, cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  if (steps) *steps = h->steps;
+  return LBM_OK;
+}
+
+int lbm_load_state(lbm_t* h, const void* host, size_t bytes, int64_t steps) {
+  if (!h || !host) return fail(LBM_EINVAL, "lbm_load_state: NULL argument");
+  if (bytes != lbm_buffer_bytes(h))
+    return fail(LBM_EINVAL, "lbm_load_state: %zu bytes given, the state is %zu", bytes, lbm_buffer_bytes(h));
+  int rc = ensure_memory(h);
+  if (rc) return rc;
+  h->cur = 0;
+  LBM_CUDA(cudaMemcpyAsync(h->buf[0], host, bytes, cudaMemcpyHostToDevice, h->stream));
+  LBM_CUDA(cudaMemcpyAsync(h->buf[1], h->buf[0], bytes, cudaMemcpyDeviceToDevice, h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  h->initialised = true;
+  h->steps = steps;
+  return LBM_OK;
+}
+
 int lbm_reduce(lbm_t* h, const double* ref_rho, const double* ref_ux, const double* ref_uy, int32_t ref_pitch,
                double out[4]) {
   if (!h || !out) return fail(LBM_EINVAL, "lbm_reduce: NULL argument");

@@ -16,7 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblbm.so")
 
-LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE = 0, -1, -2, -3, -4, -5
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2, 3
 LBM_BGK, LBM_MRT = 0, 1
 STORAGE = {"f64": LBM_F64, "f32": LBM_F32, "f16": LBM_F16, "bf16": LBM_BF16}
@@ -57,6 +57,8 @@ _SIGS = {
     "lbm_get_populations": (ctypes.c_int, [_vp, _vp]),
     "lbm_set_populations": (ctypes.c_int, [_vp, _vp]),
     "lbm_reduce": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _dp]),
+    "lbm_save_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int64)]),
+    "lbm_load_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int64]),
     "lbm_set_launch": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
     "lbm_autotune": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _dp]),
     "lbm_reduce_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _dp]),
@@ -79,6 +81,7 @@ _SIGS = {
     "lbm_batch_set_launch": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32, _i32, _i32]),
     "lbm_batch_autotune": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _dp]),
     "lbm_batch_status": (ctypes.c_int, [_vp]),
+    "lbm_wait_selftest": (ctypes.c_int, [ctypes.c_int64]),
     "lbm_last_error": (ctypes.c_char_p, []),
 }
 for _name, (_res, _args) in _SIGS.items():
@@ -227,6 +230,19 @@ def lbm_reduce(h, ref_rho: int = 0, ref_ux: int = 0, ref_uy: int = 0, ref_pitch:
         return list(out)
     _check(rc)
     return list(out)
+
+
+def lbm_save_state(h):
+    """(raw state bytes as a numpy uint8 array, step count)."""
+    buf = np.empty(lbm_buffer_bytes(h), dtype=np.uint8)
+    steps = ctypes.c_int64()
+    _check(_L.lbm_save_state(h, _hp(buf), buf.nbytes, ctypes.byref(steps)))
+    return buf, steps.value
+
+
+def lbm_load_state(h, buf, steps: int = 0):
+    buf = np.ascontiguousarray(buf, dtype=np.uint8)
+    return _check(_L.lbm_load_state(h, _hp(buf), buf.nbytes, int(steps)))
 
 
 def lbm_reduce_noalloc(h, ref_rho: int = 0, ref_ux: int = 0, ref_uy: int = 0, ref_pitch: int = 0,
@@ -467,6 +483,11 @@ def lbm_batch_autotune(b):
 
 def lbm_batch_status(b):
     return _check(_L.lbm_batch_status(b))
+
+
+def lbm_wait_selftest(budget_cycles: int) -> int:
+    """Status code of the bounded-wait check (LBM_ETIMEOUT expected)."""
+    return int(_L.lbm_wait_selftest(int(budget_cycles)))
 
 
 class Batch:

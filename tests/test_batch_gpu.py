@@ -110,3 +110,20 @@ def test_batch_with_edge_types_bit_identical(lbm):
             ref = single(lbm, w, "f32", 33, **kw)
             for a, c in zip(b.macros(k), ref):
                 assert np.array_equal(a, c), w.name
+
+
+def test_bounded_wait_gives_up_and_context_survives(lbm):
+    """Failure detection without a fault: a wait on a barrier nothing arrives on
+    gives up after its budget (~1 ms here) and reports LBM_ETIMEOUT; the context
+    stays usable and a staged-tile batch then steps normally with a clean status."""
+    assert lbm.lbm_wait_selftest(2_000_000) == lbm.LBM_ETIMEOUT
+    ws = small_batch()[:4]
+    with lbm.Batch(ws, storage="f32") as b:
+        for k, w in enumerate(ws):
+            b.init(k, *w.fields())
+        b.set_launch(128, 1, 0, 0, 0, 128)
+        b.step(20)
+        b.status()
+        ref = single(lbm, ws[0], "f32", 20)
+        for a, c in zip(b.macros(0), ref):
+            assert np.array_equal(a, c)
