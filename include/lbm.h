@@ -280,8 +280,12 @@ int lbm_batch_unstable_nodes(lbm_batch_t* b, int32_t k, int64_t* count);
  * counter; tiles of `tma_tile` vectors (128 or 256, with threads_x 128, or
  * 256 with 256) are staged by cp.async.bulk copies completing on an
  * mbarrier, the next tile's copy in flight while the current item is
- * worked on.  `blocks` (0 = one resident wave) sets the grid; `rows`,
- * `prefetch_rows` and `split` are ignored. */
+ * worked on.  `blocks` (0 = one resident wave) sets the grid;
+ * `prefetch_rows` and `split` are ignored, and `rows` is 1 or 2 there.
+ * `tma_tile` = 128 with threads_x = 128 and `rows` = 3 or 4 selects the
+ * producer/consumer form: one extra warp per block claims items and keeps
+ * `rows` tiles in flight, the 128 consumer threads work on them in order
+ * (no block-wide barrier per item).  LBM_EINVAL for a shape not compiled. */
 int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_t blocks, int32_t prefetch_rows,
                          int32_t split, int32_t tma_tile);
 /* Time every compiled tile shape, grid size, prefetch setting and split, and

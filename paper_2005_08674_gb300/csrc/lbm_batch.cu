@@ -206,6 +206,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(smem_u32(bar)),
                "r"(bytes)
@@ -461,6 +465,116 @@ void launch_tma(const lbm_batch_t* b, int from, cudaStream_t s, int grid) {
                                                               b->s_q, b->d_err);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-specialised form of the same step: the last warp of each block is a
+// producer whose lane 0 claims work items from the counter and keeps up to
+// STAGES of them in flight (bulk tiles by cp.async.bulk onto the stage's
+// `full` barrier, NSBC chunks by a plain arrival); the NC consumer threads
+// take the stages in order, work on them (tiles from shared memory, NSBC
+// chunks from global memory) and release each stage on its `empty` barrier
+// (one arrival per consumer warp).  No block-wide barrier inside the loop;
+// every wait is bounded, and on give-up a thread records the flag and leaves.
+// ---------------------------------------------------------------------------
+template <typename T, int NC, int MODEL, int TILE, int STAGES>
+__global__ void __launch_bounds__(NC + 32) batch_ws_kernel(const T* __restrict__ A, T* __restrict__ B,
+                                                           const InstDev* __restrict__ inst,
+                                                           const int4* __restrict__ items, int n_items, lbmk::Nsbc p,
+                                                           double s_e, double s_eps, double s_q,
+                                                           int* __restrict__ sched) {
+  using C = typename lbmk::Store<T>::C;
+  constexpr int SLOT = (TILE + 2) * 16;
+  constexpr int NCW = NC / 32;
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
+  __shared__ int4 ring[STAGES];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NCW);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();  // the only block-wide barrier
+
+  if (warp == NCW) {
+    // producer
+    if (lane == 0) {
+      uint32_t ephase[STAGES];
+      for (int s = 0; s < STAGES; ++s) ephase[s] = 0u;
+      int s = 0, produced = 0;
+      for (;;) {
+        const int c = atomicAdd(&sched[0], 1);
+        if (produced >= STAGES) {  // stage s was used before: wait until its consumers released it
+          if (!mbar_wait(&empty[s], ephase[s])) {
+            atomicExch(&sched[2], 1);
+            break;
+          }
+          ephase[s] ^= 1u;
+        }
+        if (c >= n_items) {
+          ring[s] = make_int4(0, 0, 0, -1);  // end of work for this block's consumers
+          mbar_arrive(&full[s]);
+          break;
+        }
+        const int4 w = items[c];
+        ring[s] = w;
+        if (w.x >= 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          issue_tile<T, TILE>(A, inst[w.x], w, smem + s * 9 * SLOT, &full[s]);
+        } else {
+          mbar_arrive(&full[s]);
+        }
+        s = s + 1 == STAGES ? 0 : s + 1;
+        ++produced;
+      }
+      __threadfence();
+      if (atomicAdd(&sched[1], 1) == (int)gridDim.x - 1) {
+        sched[0] = 0;
+        sched[1] = 0;
+      }
+    }
+    return;
+  }
+
+  // consumers
+  uint32_t fphase[STAGES];
+  for (int s = 0; s < STAGES; ++s) fphase[s] = 0u;
+  for (int s = 0;; s = s + 1 == STAGES ? 0 : s + 1) {
+    if (!mbar_wait(&full[s], fphase[s])) {
+      atomicExch(&sched[2], 1);
+      return;
+    }
+    fphase[s] ^= 1u;
+    const int4 w = ring[s];
+    if (w.w < 0) break;
+    const bool edge = w.x < 0;
+    const InstDev d = inst[edge ? ~w.x : w.x];
+    const lbmk::Rates<C> r{C(d.omega), C(s_e), C(s_eps), C(s_q)};
+    if (edge) {
+      lbmk::Nsbc q = p;
+      q.m0[0] = d.m0[0];
+      q.m0[1] = d.m0[1];
+      q.m0[2] = d.m0[2];
+      const lbmk::Geom g{d.nx, d.ny, d.pitch, d.plane};
+      const int node = w.y + (tid >> 2);
+      if (node < w.y + w.z) lbmk::nsbc_node<T, MODEL>(A + d.off, B + d.off, g, q, r, node, tid & 3);
+    } else {
+      collide_tile<T, NC, MODEL, TILE>(smem + s * 9 * SLOT, d, w, B, r);
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+}
+
+template <typename T, int NC, int MODEL, int TILE, int STAGES>
+void launch_ws(const lbm_batch_t* b, int from, cudaStream_t s, int grid) {
+  constexpr int smem = STAGES * 9 * (TILE + 2) * 16;  // limit raised by wave_blocks()
+  batch_ws_kernel<T, NC, MODEL, TILE, STAGES><<<grid, NC + 32, smem, s>>>(
+      static_cast<const T*>(b->pool[from]), static_cast<T*>(b->pool[1 - from]), b->d_inst, b->d_items, b->n_items,
+      b->nsbc, b->s_e, b->s_eps, b->s_q, b->d_err);
+}
+
 template <typename T, int BX, int PART>
 const void* kernel_ptr(int model) {
   return model == 1 ? (const void*)batch_step_kernel<T, BX, 1, PART> : (const void*)batch_step_kernel<T, BX, 0, PART>;
@@ -502,12 +616,32 @@ bool tma_shape_ok(int bx, int tile) {
   return (bx == 128 && (tile == 128 || tile == 256)) || (bx == 256 && tile == 256);
 }
 
+// stages compiled for the warp-specialised path (128 consumer threads, tiles of 128 vectors)
+template <typename F>
+void with_ws(int stages, F&& f) {
+  if (stages >= 4)
+    f(std::integral_constant<int, 4>{});
+  else
+    f(std::integral_constant<int, 3>{});
+}
+
 // resident blocks on the device for the launch that carries the bulk tiles
 int wave_blocks(const lbm_batch_t* b) {
   int per_sm = 0, sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
   bdispatch(b->storage, [&](auto tag) {
     using T = decltype(tag);
+    if (b->tile > 0 && b->rows >= 3) {
+      with_ws(b->rows, [&](auto sc) {
+        constexpr int STAGES = decltype(sc)::value;
+        constexpr int smem = STAGES * 9 * (128 + 2) * 16;
+        const void* k = b->collision == 1 ? (const void*)batch_ws_kernel<T, 128, 1, 128, STAGES>
+                                          : (const void*)batch_ws_kernel<T, 128, 0, 128, STAGES>;
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128 + 32, smem);
+      });
+      return;
+    }
     if (b->tile > 0) {
       with_tma(b->bx, b->tile, [&](auto bxc, auto tc) {
         constexpr int BX = decltype(bxc)::value, TILE = decltype(tc)::value;
@@ -539,6 +673,18 @@ int grid_for_items(const lbm_batch_t* b, int n) {
 void enqueue_batch_step(const lbm_batch_t* b, int from, cudaStream_t s) {
   bdispatch(b->storage, [&](auto tag) {
     using T = decltype(tag);
+    if (b->tile > 0 && b->rows >= 3) {
+      // one persistent launch, producer warp + consumer warps
+      with_ws(b->rows, [&](auto sc) {
+        constexpr int STAGES = decltype(sc)::value;
+        const int grid = std::max(1, std::min(b->n_items, b->blocks > 0 ? b->blocks : b->wave));
+        if (b->collision == 1)
+          launch_ws<T, 128, 1, 128, STAGES>(b, from, s, grid);
+        else
+          launch_ws<T, 128, 0, 128, STAGES>(b, from, s, grid);
+      });
+      return;
+    }
     if (b->tile > 0) {
       // the whole step in one persistent launch (NSBC chunks and staged tiles)
       with_tma(b->bx, b->tile, [&](auto bxc, auto tc) {
@@ -937,13 +1083,17 @@ int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_
   if (tma_tile != 0 && !tma_shape_ok(threads_x, tma_tile))
     return bfail(LBM_EINVAL, "lbm_batch_set_launch: staged tiles need (threads, tile) = (128, 128), (128, 256) or "
                              "(256, 256), got (%d, %d)", threads_x, tma_tile);
+  const bool ws = tma_tile != 0 && rows >= 3;
+  if (ws && (threads_x != 128 || tma_tile != 128 || rows > 4))
+    return bfail(LBM_EINVAL, "lbm_batch_set_launch: the producer/consumer path takes (threads, tile) = (128, 128) "
+                             "and 3 or 4 stages, got (%d, %d, %d)", threads_x, tma_tile, rows);
   if (tma_tile == 0 && !batch_shape_ok(threads_x, rows))
     return bfail(LBM_EINVAL, "lbm_batch_set_launch: shape (%d, %d) not compiled", threads_x, rows);
   if (blocks < -1) return bfail(LBM_EINVAL, "lbm_batch_set_launch: blocks=%d < -1", blocks);
   if (prefetch_rows < 0 || prefetch_rows > 65536)
     return bfail(LBM_EINVAL, "lbm_batch_set_launch: prefetch=%d outside [0, 65536]", prefetch_rows);
   b->bx = threads_x;
-  b->rows = tma_tile ? 1 : rows;
+  b->rows = tma_tile ? (ws ? rows : 1) : rows;
   b->blocks = blocks;
   b->pf = prefetch_rows;
   b->split = tma_tile == 0 && split != 0;
@@ -1019,6 +1169,20 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
     b->bx = tp[0];
     b->rows = 1;
     b->tile = tp[1];
+    b->split = false;
+    b->blocks = 0;
+    b->pf = 0;
+    b->items_dirty = true;
+    rc = build_items(b);
+    if (rc) break;
+    keep(time_it());
+  }
+  // producer/consumer path: one issuing warp, 3 or 4 tile stages
+  for (int st : {3, 4}) {
+    if (rc) break;
+    b->bx = 128;
+    b->rows = st;
+    b->tile = 128;
     b->split = false;
     b->blocks = 0;
     b->pf = 0;

@@ -35,12 +35,16 @@ def single(lbm, w, storage, steps, **kw):
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("collision", ["bgk", "mrt"])
-def test_batch_bit_identical_to_single_runs(lbm, storage, collision):
+@pytest.mark.parametrize("launch", [None, (128, 3, 0, 0, 0, 128)])
+def test_batch_bit_identical_to_single_runs(lbm, storage, collision, launch):
+    """Default launch and the producer/consumer form (3 staged tiles)."""
     ws = small_batch()
     kw = dict(collision=collision, mrt_rates=(1.4, 1.4, 1.2), beta=0.05)
     with lbm.Batch(ws, storage=storage, **kw) as b:
         for k, w in enumerate(ws):
             b.init(k, *w.fields())
+        if launch:
+            b.set_launch(*launch)
         b.step(37)  # two graph replays of 16 and five direct launches
         for k, w in enumerate(ws):
             ref = single(lbm, w, storage, 37, **kw)
@@ -63,7 +67,8 @@ def test_batch_f64_matches_oracle(lbm):
 
 
 @pytest.mark.parametrize("shape", [(64, 1, 0, 0, 0, 0), (128, 2, 0, 1, 1, 0), (256, 4, 152, 0, 0, 0), (64, 4, 7, 64, 1, 0), (128, 1, 0, 0, 1, 128), (128, 1, 0, 0, 1, 256), (256, 1, 0, 0, 1, 256),
-                                   (128, 4, -1, 1, 0, 0), (256, 1, -1, 0, 1, 0)])
+                                   (128, 4, -1, 1, 0, 0), (256, 1, -1, 0, 1, 0),
+                                   (128, 3, 0, 0, 0, 128), (128, 4, 0, 0, 0, 128), (128, 3, 5, 0, 0, 128)])
 def test_batch_launch_shapes_agree(lbm, shape):
     """Every tile shape, grid size (one block per item, persistent waves, a
     grid far smaller than the work list) and prefetch gives the same bits."""
