@@ -487,6 +487,7 @@ __global__ void __launch_bounds__(NC + 32) batch_ws_kernel(const T* __restrict__
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
   __shared__ int4 ring[STAGES];
+  __shared__ InstDev rinst[STAGES];  // the item's instance, read once by the producer
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -500,17 +501,16 @@ __global__ void __launch_bounds__(NC + 32) batch_ws_kernel(const T* __restrict__
   if (warp == NCW) {
     // producer
     if (lane == 0) {
-      uint32_t ephase[STAGES];
-      for (int s = 0; s < STAGES; ++s) ephase[s] = 0u;
+      uint32_t ephase = 0u;  // bit s: parity of the next completion of empty[s]
       int s = 0, produced = 0;
       for (;;) {
         const int c = atomicAdd(&sched[0], 1);
         if (produced >= STAGES) {  // stage s was used before: wait until its consumers released it
-          if (!mbar_wait(&empty[s], ephase[s])) {
+          if (!mbar_wait(&empty[s], (ephase >> s) & 1u)) {
             atomicExch(&sched[2], 1);
             break;
           }
-          ephase[s] ^= 1u;
+          ephase ^= 1u << s;
         }
         if (c >= n_items) {
           ring[s] = make_int4(0, 0, 0, -1);  // end of work for this block's consumers
@@ -518,10 +518,12 @@ __global__ void __launch_bounds__(NC + 32) batch_ws_kernel(const T* __restrict__
           break;
         }
         const int4 w = items[c];
+        const InstDev d = inst[w.x < 0 ? ~w.x : w.x];
         ring[s] = w;
+        rinst[s] = d;
         if (w.x >= 0) {
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          issue_tile<T, TILE>(A, inst[w.x], w, smem + s * 9 * SLOT, &full[s]);
+          issue_tile<T, TILE>(A, d, w, smem + s * 9 * SLOT, &full[s]);
         } else {
           mbar_arrive(&full[s]);
         }
@@ -538,18 +540,17 @@ __global__ void __launch_bounds__(NC + 32) batch_ws_kernel(const T* __restrict__
   }
 
   // consumers
-  uint32_t fphase[STAGES];
-  for (int s = 0; s < STAGES; ++s) fphase[s] = 0u;
+  uint32_t fphase = 0u;  // bit s: parity of the next completion of full[s]
   for (int s = 0;; s = s + 1 == STAGES ? 0 : s + 1) {
-    if (!mbar_wait(&full[s], fphase[s])) {
+    if (!mbar_wait(&full[s], (fphase >> s) & 1u)) {
       atomicExch(&sched[2], 1);
       return;
     }
-    fphase[s] ^= 1u;
+    fphase ^= 1u << s;
     const int4 w = ring[s];
     if (w.w < 0) break;
     const bool edge = w.x < 0;
-    const InstDev d = inst[edge ? ~w.x : w.x];
+    const InstDev d = rinst[s];
     const lbmk::Rates<C> r{C(d.omega), C(s_e), C(s_eps), C(s_q)};
     if (edge) {
       lbmk::Nsbc q = p;

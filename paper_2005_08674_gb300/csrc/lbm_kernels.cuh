@@ -208,7 +208,8 @@ __device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict
     const double mb = (double)(cq == 0 ? t0[0] : (cq == 1 ? t0[1] : t0[2]));
     const double m1 = (double)(cq == 0 ? t1[0] : (cq == 1 ? t1[1] : t1[2]));
     const double m2 = (double)(cq == 0 ? t2[0] : (cq == 1 ? t2[1] : t2[2]));
-    const double m0 = cq == 0 ? p.m0[0] - 1.0 : p.m0[cq];
+    // (static indices only, so a copy of p stays in registers)
+    const double m0 = cq == 0 ? p.m0[0] - 1.0 : (cq == 1 ? p.m0[1] : p.m0[2]);
     // 1 / |n| (GB300's FP64 divide is slow: multiply by the reciprocal)
     const double inv_len = (nxn != 0 && nyn != 0) ? 0.70710678118654752 : 1.0;
     const double dn = p.order == 2 ? (3.0 * mb - 4.0 * m1 + m2) * (0.5 * inv_len) : (mb - m1) * inv_len;
@@ -229,8 +230,8 @@ __device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict
                      : (y == g.ny - 1 && p.vel[3])    ? 3
                                                       : -1;
     if (side >= 0) {
-      mc[1] = C(p.uw[side][0]);
-      mc[2] = C(p.uw[side][1]);
+      mc[1] = C(side == 0 ? p.uw[0][0] : side == 1 ? p.uw[1][0] : side == 2 ? p.uw[2][0] : p.uw[3][0]);
+      mc[2] = C(side == 0 ? p.uw[0][1] : side == 1 ? p.uw[1][1] : side == 2 ? p.uw[2][1] : p.uw[3][1]);
     }
 
     // Eqs. (nes_0), (nes_1): f_in = f_in^eq(m_c) + f_out - f_out^eq(m_c)
