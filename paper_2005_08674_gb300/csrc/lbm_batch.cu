@@ -475,7 +475,7 @@ void launch_tma(const lbm_batch_t* b, int from, cudaStream_t s, int grid) {
 // (one arrival per consumer warp).  No block-wide barrier inside the loop;
 // every wait is bounded, and on give-up a thread records the flag and leaves.
 // ---------------------------------------------------------------------------
-template <typename T, int NC, int MODEL, int TILE, int STAGES>
+template <typename T, int NC, int MODEL, int TILE, int STAGES, int K>
 __global__ void __launch_bounds__(NC + 32) batch_ws_kernel(const T* __restrict__ A, T* __restrict__ B,
                                                            const InstDev* __restrict__ inst,
                                                            const int4* __restrict__ items, int n_items, lbmk::Nsbc p,
@@ -558,8 +558,16 @@ __global__ void __launch_bounds__(NC + 32) batch_ws_kernel(const T* __restrict__
       q.m0[1] = d.m0[1];
       q.m0[2] = d.m0[2];
       const lbmk::Geom g{d.nx, d.ny, d.pitch, d.plane};
-      const int node = w.y + (tid >> 2);
-      if (node < w.y + w.z) lbmk::nsbc_node<T, MODEL>(A + d.off, B + d.off, g, q, r, node, tid & 3);
+      // K nodes per lane quad: node w.y + quad + (NC / 4) k of the chunk
+      int node[K];
+      bool valid[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int n = (tid >> 2) + (NC / 4) * k;
+        valid[k] = n < w.z;
+        node[k] = w.y + (valid[k] ? n : 0);
+      }
+      lbmk::nsbc_nodes<T, MODEL, K>(A + d.off, B + d.off, g, q, r, node, valid, tid & 3);
     } else {
       collide_tile<T, NC, MODEL, TILE>(smem + s * 9 * SLOT, d, w, B, r);
     }
@@ -568,10 +576,10 @@ __global__ void __launch_bounds__(NC + 32) batch_ws_kernel(const T* __restrict__
   }
 }
 
-template <typename T, int NC, int MODEL, int TILE, int STAGES>
+template <typename T, int NC, int MODEL, int TILE, int STAGES, int K>
 void launch_ws(const lbm_batch_t* b, int from, cudaStream_t s, int grid) {
   constexpr int smem = STAGES * 9 * (TILE + 2) * 16;  // limit raised by wave_blocks()
-  batch_ws_kernel<T, NC, MODEL, TILE, STAGES><<<grid, NC + 32, smem, s>>>(
+  batch_ws_kernel<T, NC, MODEL, TILE, STAGES, K><<<grid, NC + 32, smem, s>>>(
       static_cast<const T*>(b->pool[from]), static_cast<T*>(b->pool[1 - from]), b->d_inst, b->d_items, b->n_items,
       b->nsbc, b->s_e, b->s_eps, b->s_q, b->d_err);
 }
@@ -617,13 +625,26 @@ bool tma_shape_ok(int bx, int tile) {
   return (bx == 128 && (tile == 128 || tile == 256)) || (bx == 256 && tile == 256);
 }
 
-// stages compiled for the warp-specialised path (128 consumer threads, tiles of 128 vectors)
+// Shapes compiled for the producer/consumer path (128 consumer threads,
+// tiles of 128 vectors): 3 or 4 stages, 1, 2 or 4 perimeter nodes per lane
+// quad (the `prefetch_rows` field carries the latter; 0 means 1).
+int ws_nodes_per_quad(int pf) { return pf == 2 || pf == 4 ? pf : 1; }
+
 template <typename F>
-void with_ws(int stages, F&& f) {
+void with_ws(int stages, int pf, F&& f) {
+  const int k = ws_nodes_per_quad(pf);
+  auto pick_k = [&](auto sc) {
+    if (k == 4)
+      f(sc, std::integral_constant<int, 4>{});
+    else if (k == 2)
+      f(sc, std::integral_constant<int, 2>{});
+    else
+      f(sc, std::integral_constant<int, 1>{});
+  };
   if (stages >= 4)
-    f(std::integral_constant<int, 4>{});
+    pick_k(std::integral_constant<int, 4>{});
   else
-    f(std::integral_constant<int, 3>{});
+    pick_k(std::integral_constant<int, 3>{});
 }
 
 // resident blocks on the device for the launch that carries the bulk tiles
@@ -633,11 +654,11 @@ int wave_blocks(const lbm_batch_t* b) {
   bdispatch(b->storage, [&](auto tag) {
     using T = decltype(tag);
     if (b->tile > 0 && b->rows >= 3) {
-      with_ws(b->rows, [&](auto sc) {
-        constexpr int STAGES = decltype(sc)::value;
+      with_ws(b->rows, b->pf, [&](auto sc, auto kc) {
+        constexpr int STAGES = decltype(sc)::value, K = decltype(kc)::value;
         constexpr int smem = STAGES * 9 * (128 + 2) * 16;
-        const void* k = b->collision == 1 ? (const void*)batch_ws_kernel<T, 128, 1, 128, STAGES>
-                                          : (const void*)batch_ws_kernel<T, 128, 0, 128, STAGES>;
+        const void* k = b->collision == 1 ? (const void*)batch_ws_kernel<T, 128, 1, 128, STAGES, K>
+                                          : (const void*)batch_ws_kernel<T, 128, 0, 128, STAGES, K>;
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128 + 32, smem);
       });
@@ -676,13 +697,13 @@ void enqueue_batch_step(const lbm_batch_t* b, int from, cudaStream_t s) {
     using T = decltype(tag);
     if (b->tile > 0 && b->rows >= 3) {
       // one persistent launch, producer warp + consumer warps
-      with_ws(b->rows, [&](auto sc) {
-        constexpr int STAGES = decltype(sc)::value;
+      with_ws(b->rows, b->pf, [&](auto sc, auto kc) {
+        constexpr int STAGES = decltype(sc)::value, K = decltype(kc)::value;
         const int grid = std::max(1, std::min(b->n_items, b->blocks > 0 ? b->blocks : b->wave));
         if (b->collision == 1)
-          launch_ws<T, 128, 1, 128, STAGES>(b, from, s, grid);
+          launch_ws<T, 128, 1, 128, STAGES, K>(b, from, s, grid);
         else
-          launch_ws<T, 128, 0, 128, STAGES>(b, from, s, grid);
+          launch_ws<T, 128, 0, 128, STAGES, K>(b, from, s, grid);
       });
       return;
     }
@@ -715,6 +736,14 @@ void enqueue_batch_step(const lbm_batch_t* b, int from, cudaStream_t s) {
   });
 }
 
+// Row of perimeter node n (bottom row, top row, left column, right column;
+// the order the device side walks the perimeter in)
+int perimeter_row(int n, int nx, int ny) {
+  if (n < 2 * nx) return n >= nx ? ny - 1 : 0;
+  n -= 2 * nx;
+  return 1 + (n >= ny - 2 ? n - (ny - 2) : n);
+}
+
 void drop_batch_graphs(lbm_batch_t* b) {
   for (auto& g : b->graph)
     if (g) {
@@ -723,9 +752,10 @@ void drop_batch_graphs(lbm_batch_t* b) {
     }
 }
 
-// Work list for the current shape: NSBC chunks first (latency-bound; they
-// start early and overlap with the bandwidth-bound tiles), then bulk tiles,
-// largest instances first.
+// Work list for the current shape.  Register path: NSBC chunks first
+// (latency-bound; they start early and overlap with the bandwidth-bound
+// tiles), then bulk tiles, largest instances first.  Staged-tile paths: one
+// interleaved list (below).
 int build_items(lbm_batch_t* b) {
   if (!b->items_dirty) return LBM_OK;
   const int V = (int)(16 / b->elt);
@@ -735,7 +765,9 @@ int build_items(lbm_batch_t* b) {
     return (long long)b->inst[i].nx * b->inst[i].ny > (long long)b->inst[j].nx * b->inst[j].ny;
   });
   std::vector<int4> items;
-  const int chunk = b->bx / 4;
+  // NSBC chunk: one node per quad of lanes, or one per consumer thread in the
+  // producer/consumer form
+  const int chunk = b->bx / 4 * (b->tile > 0 && b->rows >= 3 ? ws_nodes_per_quad(b->pf) : 1);
   for (int k : order) {
     const InstDev& d = b->inst[k];
     const int perim = 2 * d.nx + 2 * (d.ny - 2);
@@ -751,17 +783,40 @@ int build_items(lbm_batch_t* b) {
   }
   const int n_bulk = (int)items.size() - n_edge;
   if (b->tile > 0 && n_edge > 0) {
-    // one dynamically scheduled list: spread the NSBC chunks evenly among the
-    // staged tiles so that their latency overlaps with copies in flight
+    // One dynamically scheduled list in memory order: instance after
+    // instance (largest first), tiles in row order, and each NSBC chunk right
+    // after the tile that stages the last row it reads (rows y - 1 .. y + 2
+    // around its nodes), so that its scattered loads find those rows in L2
+    // and its partial-sector stores meet the tile's there.  (Spreading the
+    // chunks evenly over the whole list instead, or each instance's items
+    // over the whole step, costs 10-15 % in measured step time.)
+    std::vector<std::vector<int4>> per(b->count);
+    size_t e = 0, t = (size_t)n_edge;
+    for (int k : order) {
+      const InstDev& d = b->inst[k];
+      const int nvec = (d.nx + V - 1) / V;
+      std::vector<std::pair<int, int4>> chunks;  // (last row read, chunk)
+      for (; e < (size_t)n_edge && ~items[e].x == k; ++e) {
+        int last = 0;
+        for (int n = items[e].y; n < items[e].y + items[e].z; ++n)
+          last = std::max(last, std::min(perimeter_row(n, d.nx, d.ny) + 2, d.ny - 1));
+        chunks.push_back({last, items[e]});
+      }
+      std::stable_sort(chunks.begin(), chunks.end(),
+                       [](const std::pair<int, int4>& x, const std::pair<int, int4>& y) { return x.first < y.first; });
+      std::vector<int4>& out = per[k];
+      size_t c = 0;
+      for (; t < items.size() && items[t].x == k; ++t) {
+        const int first_row = 1 + items[t].y / nvec;
+        for (; c < chunks.size() && chunks[c].first < first_row; ++c) out.push_back(chunks[c].second);
+        out.push_back(items[t]);
+      }
+      for (; c < chunks.size(); ++c) out.push_back(chunks[c].second);
+    }
     std::vector<int4> mixed;
     mixed.reserve(items.size());
-    long long e = 0;
-    for (int t = 0; t < n_bulk; ++t) {
-      mixed.push_back(items[n_edge + t]);
-      const long long want = (long long)(t + 1) * n_edge / n_bulk;
-      for (; e < want; ++e) mixed.push_back(items[e]);
-    }
-    for (; e < n_edge; ++e) mixed.push_back(items[e]);
+    for (int k : order)
+      for (const int4& w : per[k]) mixed.push_back(w);
     items.swap(mixed);
   }
   if (b->d_items) cudaFree(b->d_items);
@@ -1088,6 +1143,9 @@ int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_
   if (ws && (threads_x != 128 || tma_tile != 128 || rows > 4))
     return bfail(LBM_EINVAL, "lbm_batch_set_launch: the producer/consumer path takes (threads, tile) = (128, 128) "
                              "and 3 or 4 stages, got (%d, %d, %d)", threads_x, tma_tile, rows);
+  if (ws && prefetch_rows != 0 && prefetch_rows != 1 && prefetch_rows != 2 && prefetch_rows != 4)
+    return bfail(LBM_EINVAL, "lbm_batch_set_launch: the producer/consumer path takes 1, 2 or 4 perimeter nodes per "
+                             "lane quad, got %d", prefetch_rows);
   if (tma_tile == 0 && !batch_shape_ok(threads_x, rows))
     return bfail(LBM_EINVAL, "lbm_batch_set_launch: shape (%d, %d) not compiled", threads_x, rows);
   if (blocks < -1) return bfail(LBM_EINVAL, "lbm_batch_set_launch: blocks=%d < -1", blocks);
@@ -1178,20 +1236,22 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
     if (rc) break;
     keep(time_it());
   }
-  // producer/consumer path: one issuing warp, 3 or 4 tile stages
-  for (int st : {3, 4}) {
-    if (rc) break;
-    b->bx = 128;
-    b->rows = st;
-    b->tile = 128;
-    b->split = false;
-    b->blocks = 0;
-    b->pf = 0;
-    b->items_dirty = true;
-    rc = build_items(b);
-    if (rc) break;
-    keep(time_it());
-  }
+  // producer/consumer path: one issuing warp, 3 or 4 tile stages, 1, 2 or 4
+  // perimeter nodes per lane quad
+  for (int st : {3, 4})
+    for (int kq : {1, 2, 4}) {
+      if (rc) break;
+      b->bx = 128;
+      b->rows = st;
+      b->tile = 128;
+      b->split = false;
+      b->blocks = 0;
+      b->pf = kq;
+      b->items_dirty = true;
+      rc = build_items(b);
+      if (rc) break;
+      keep(time_it());
+    }
   if (!rc) rc = batch_check_launch();
   b->bx = bb;
   b->rows = br;

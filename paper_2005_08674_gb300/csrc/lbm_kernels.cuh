@@ -151,77 +151,74 @@ __global__ void __launch_bounds__(BX) bulk_kernel(const T* __restrict__ A, T* __
 }
 
 // ---------------------------------------------------------------------------
-// NSBC: four lanes per perimeter node.  Lane q loads the node b - q n and
-// forms its moments (q = 0, 1, and 2 for the second-order difference) as
-// (rho - 1, ux, uy) in the compute type; lane 0 gathers them by shuffles
-// within its quad, predicts and blends m_c in double (the prediction is
-// linear, so predicting rho - 1 is predicting rho), then rebuilds, corrects
-// and collides the node in the compute type.
+// NSBC.  The moments (rho - 1, ux, uy) are formed in the compute type at
+// b, b - n and (second-order difference) b - 2n; m_c is predicted and
+// blended in double (the prediction is linear, so predicting rho - 1 is
+// predicting rho); the node is then rebuilt, corrected and collided in the
+// compute type.
 // ---------------------------------------------------------------------------
-// Node `node` of the perimeter, handled by the four lanes of one quad
-// (q = lane & 3); all four lanes must call this together.
-template <typename T, int MODEL>
-__device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict__ B, const Geom& g, const Nsbc& p,
-                                          const Rates<typename Store<T>::C>& rates, int node, int q) {
+// Perimeter node `node`: coordinates and outward normal (zero along a
+// periodic axis, which has no boundary there).
+struct EdgeNode {
+  int x, y, nxn, nyn;
+  bool open;  // an NSBC / velocity edge node (not closed periodically)
+};
+
+__device__ __forceinline__ EdgeNode edge_node(int node, const Geom& g, const Nsbc& p) {
+  EdgeNode e;
+  perimeter_node(node, g.nx, g.ny, e.x, e.y, e.nxn, e.nyn);
+  if (p.periodic_x) e.nxn = 0;
+  if (p.periodic_y) e.nyn = 0;
+  e.open = e.nxn != 0 || e.nyn != 0;
+  return e;
+}
+
+// Pulled populations of the node (wrapped on periodic axes); unknown where
+// the source lies outside the domain (zero there, or everywhere if !load).
+template <typename T>
+__device__ __forceinline__ void edge_pull(const T* __restrict__ A, const Geom& g, const Nsbc& p, const EdgeNode& e,
+                                          bool load, typename Store<T>::C (&h)[9], bool (&known)[9]) {
   using S = Store<T>;
   using C = typename S::C;
-  const unsigned quad = 0xFu << ((threadIdx.x & 31) & ~3);
-  int x, y, nxn, nyn;
-  perimeter_node(node, g.nx, g.ny, x, y, nxn, nyn);
-  if (p.periodic_x) nxn = 0;  // a periodic axis has no boundary normal
-  if (p.periodic_y) nyn = 0;
-  const bool open = nxn != 0 || nyn != 0;
-
-  // pulled populations (wrapped on periodic axes); unknown where the source
-  // lies outside the domain.  Lane 0 issues these loads before the moment
-  // loads and shuffles so that both load rounds are in flight together.
-  C h[9];
-  bool known[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
-    int sx = x - cx(i), sy = y - cy(i);
+    int sx = e.x - cx(i), sy = e.y - cy(i);
     if (p.periodic_x) sx = sx < 0 ? sx + g.nx : (sx >= g.nx ? sx - g.nx : sx);
     if (p.periodic_y) sy = sy < 0 ? sy + g.ny : (sy >= g.ny ? sy - g.ny : sy);
     known[i] = sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny;
-    h[i] = (q == 0 && known[i]) ? S::ldg1(A + i * g.plane + (long long)sy * g.pitch + sx) : C(0);
+    h[i] = (load && known[i]) ? S::ldg1(A + i * g.plane + (long long)sy * g.pitch + sx) : C(0);
   }
+}
 
-  // lane q forms (rho - 1, ux, uy) at b - q n in the compute type; the quad
-  // then transposes them so that lane c (c < 3) holds component c at b,
-  // b - n, b - 2n and predicts and blends that component in FP64 -- three
-  // lanes share the FP64 work (GB300's FP64 pipe is narrow) -- and lane 0
-  // gathers the three blended components.
-  C mq[3] = {C(0), C(0), C(0)};
-  if (open && q <= p.order) node_dmoments(A, g, x - q * nxn, y - q * nyn, mq);
-  C t0[3], t1[3], t2[3];
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    t0[c] = __shfl_sync(quad, mq[c], 0, 4);
-    t1[c] = __shfl_sync(quad, mq[c], 1, 4);
-    t2[c] = __shfl_sync(quad, mq[c], 2, 4);
-  }
-  const int cq = q < 3 ? q : 0;
-  C mine = C(0);
-  {
-    // Eq. (nes_2): m_p = m_b - gamma d_n m along the outward unit normal;
-    // Eq. (nes_3): m_c = (1 - beta) m_p + beta m_0; component cq.
-    const double mb = (double)(cq == 0 ? t0[0] : (cq == 1 ? t0[1] : t0[2]));
-    const double m1 = (double)(cq == 0 ? t1[0] : (cq == 1 ? t1[1] : t1[2]));
-    const double m2 = (double)(cq == 0 ? t2[0] : (cq == 1 ? t2[1] : t2[2]));
-    // (static indices only, so a copy of p stays in registers)
-    const double m0 = cq == 0 ? p.m0[0] - 1.0 : (cq == 1 ? p.m0[1] : p.m0[2]);
-    // 1 / |n| (GB300's FP64 divide is slow: multiply by the reciprocal)
-    const double inv_len = (nxn != 0 && nyn != 0) ? 0.70710678118654752 : 1.0;
-    const double dn = p.order == 2 ? (3.0 * mb - 4.0 * m1 + m2) * (0.5 * inv_len) : (mb - m1) * inv_len;
-    const double mp = mb - p.gamma * dn;
-    mine = C((1.0 - p.beta) * mp + p.beta * m0);
-  }
-  C mc[3];  // (rho_c - 1, u_c)
-#pragma unroll
-  for (int c = 0; c < 3; ++c) mc[c] = __shfl_sync(quad, mine, c, 4);
-  if (q != 0) return;
+// Eq. (nes_2): m_p = m_b - gamma d_n m, d_n along the outward unit normal by
+// the one-sided difference of the given order (1 / |n| = 1/sqrt(2) at
+// corners); Eq. (nes_3): m_c = (1 - beta) m_p + beta m_0.  Component c of
+// (rho - 1, ux, uy) from its values at b, b - n, b - 2n, in FP64 with every
+// rounding explicit (no contraction left to the compiler), so that every
+// caller gets the same bits.  GB300's FP64 divide is slow: no divides.
+template <typename C>
+__device__ __forceinline__ C edge_predict(C vb, C v1, C v2, int c, bool diagonal, const Nsbc& p) {
+  const double mb = (double)vb, m1 = (double)v1, m2 = (double)v2;
+  const double m0 = c == 0 ? p.m0[0] - 1.0 : (c == 1 ? p.m0[1] : p.m0[2]);  // static indices only
+  const double inv_len = diagonal ? 0.70710678118654752 : 1.0;
+  const double dn = p.order == 2 ? __dmul_rn(__fma_rn(3.0, mb, __fma_rn(-4.0, m1, m2)), 0.5 * inv_len)
+                                 : __dmul_rn(__dsub_rn(mb, m1), inv_len);
+  const double mp = __fma_rn(-p.gamma, dn, mb);
+  return C(__fma_rn(1.0 - p.beta, mp, __dmul_rn(p.beta, m0)));
+}
 
-  if (open) {
+// The rest of the node, given its pulled populations and the blended
+// (rho_c - 1, u_c): velocity override, reconstruction of the unknown
+// populations, correction, collision and the store.
+template <typename T, int MODEL>
+__device__ __forceinline__ void edge_finish(T* __restrict__ B, const Geom& g, const Nsbc& p,
+                                            const Rates<typename Store<T>::C>& rates, const EdgeNode& en,
+                                            typename Store<T>::C (&h)[9], const bool (&known)[9],
+                                            typename Store<T>::C (&mc)[3]) {
+  using S = Store<T>;
+  using C = typename S::C;
+  const int x = en.x, y = en.y;
+  if (en.open) {
     // a velocity edge keeps the predicted density and imposes its velocity
     // (left/right edges win at corners)
     const int side = (x == 0 && p.vel[0])             ? 0
@@ -259,6 +256,71 @@ __device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict
   const long long o = (long long)y * g.pitch + x;
 #pragma unroll
   for (int i = 0; i < 9; ++i) S::st1(B + i * g.plane + o, h[i]);
+}
+
+// K perimeter nodes, each handled by the four lanes of one quad (q = lane &
+// 3); all four lanes must call this together with the same nodes.  Lane q
+// forms (rho - 1, ux, uy) at b - q n in the compute type; the quad then
+// transposes them so that lane c (c < 3) holds component c at b, b - n,
+// b - 2n and predicts and blends that component in FP64 -- three lanes share
+// the FP64 work (GB300's FP64 pipe is narrow) -- and lane 0 gathers the three
+// blended components and finishes the node.  Every load of the K nodes is
+// issued before the first is used (one round trip for all of them); nodes
+// with valid[k] false are computed (from in-range addresses) but not stored.
+template <typename T, int MODEL, int K>
+__device__ __forceinline__ void nsbc_nodes(const T* __restrict__ A, T* __restrict__ B, const Geom& g, const Nsbc& p,
+                                           const Rates<typename Store<T>::C>& rates, const int (&node)[K],
+                                           const bool (&valid)[K], int q) {
+  using S = Store<T>;
+  using C = typename S::C;
+  const unsigned quad = 0xFu << ((threadIdx.x & 31) & ~3);
+  EdgeNode en[K];
+  C h[K][9], v[K][9];
+  bool known[K][9];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    en[k] = edge_node(node[k], g, p);
+    edge_pull(A, g, p, en[k], q == 0, h[k], known[k]);  // lane 0: the pulled populations
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {  // lane q: the node b - q n (zeros if not needed)
+    const bool want = en[k].open && q <= p.order;
+    const long long o = (long long)(en[k].y - q * en[k].nyn) * g.pitch + (en[k].x - q * en[k].nxn);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[k][i] = want ? S::ldg1(A + i * g.plane + o) : C(0);
+  }
+  const int cq = q < 3 ? q : 0;
+  C mc[K][3];  // (rho_c - 1, u_c)
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    C mq[3];
+    dmoments_of(v[k], mq);  // all zeros from zero populations
+    C t0[3], t1[3], t2[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      t0[c] = __shfl_sync(quad, mq[c], 0, 4);
+      t1[c] = __shfl_sync(quad, mq[c], 1, 4);
+      t2[c] = __shfl_sync(quad, mq[c], 2, 4);
+    }
+    const C mine = edge_predict(cq == 0 ? t0[0] : (cq == 1 ? t0[1] : t0[2]),
+                                cq == 0 ? t1[0] : (cq == 1 ? t1[1] : t1[2]),
+                                cq == 0 ? t2[0] : (cq == 1 ? t2[1] : t2[2]), cq,
+                                en[k].nxn != 0 && en[k].nyn != 0, p);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) mc[k][c] = __shfl_sync(quad, mine, c, 4);
+  }
+  if (q != 0) return;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+    if (valid[k]) edge_finish<T, MODEL>(B, g, p, rates, en[k], h[k], known[k], mc[k]);
+}
+
+template <typename T, int MODEL>
+__device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict__ B, const Geom& g, const Nsbc& p,
+                                          const Rates<typename Store<T>::C>& rates, int node, int q) {
+  const int n[1] = {node};
+  const bool ok[1] = {true};
+  nsbc_nodes<T, MODEL, 1>(A, B, g, p, rates, n, ok, q);
 }
 
 template <typename T, int MODEL>
