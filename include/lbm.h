@@ -285,7 +285,11 @@ int lbm_batch_unstable_nodes(lbm_batch_t* b, int32_t k, int64_t* count);
  * `tma_tile` = 128 with threads_x = 128 and `rows` = 3 or 4 selects the
  * producer/consumer form: one extra warp per block claims items and keeps
  * `rows` tiles in flight, the 128 consumer threads work on them in order
- * (no block-wide barrier per item).  LBM_EINVAL for a shape not compiled. */
+ * (no block-wide barrier per item); there `prefetch_rows` is the number of
+ * perimeter nodes each quad of lanes handles per NSBC chunk (0 or 1, or 2).
+ * Staged-tile work lists run instance after instance in memory order, each
+ * NSBC chunk right after the tile that stages its rows.  LBM_EINVAL for a
+ * shape not compiled. */
 int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_t blocks, int32_t prefetch_rows,
                          int32_t split, int32_t tma_tile);
 /* Time every compiled tile shape, grid size, prefetch setting and split, and

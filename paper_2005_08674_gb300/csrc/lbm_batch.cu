@@ -476,7 +476,7 @@ void launch_tma(const lbm_batch_t* b, int from, cudaStream_t s, int grid) {
 // every wait is bounded, and on give-up a thread records the flag and leaves.
 // ---------------------------------------------------------------------------
 template <typename T, int NC, int MODEL, int TILE, int STAGES, int K>
-__global__ void __launch_bounds__(NC + 32) batch_ws_kernel(const T* __restrict__ A, T* __restrict__ B,
+__global__ void __launch_bounds__(NC + 32, 4) batch_ws_kernel(const T* __restrict__ A, T* __restrict__ B,
                                                            const InstDev* __restrict__ inst,
                                                            const int4* __restrict__ items, int n_items, lbmk::Nsbc p,
                                                            double s_e, double s_eps, double s_q,
@@ -626,17 +626,15 @@ bool tma_shape_ok(int bx, int tile) {
 }
 
 // Shapes compiled for the producer/consumer path (128 consumer threads,
-// tiles of 128 vectors): 3 or 4 stages, 1, 2 or 4 perimeter nodes per lane
-// quad (the `prefetch_rows` field carries the latter; 0 means 1).
-int ws_nodes_per_quad(int pf) { return pf == 2 || pf == 4 ? pf : 1; }
+// tiles of 128 vectors): 3 or 4 stages, 1 or 2 perimeter nodes per lane quad
+// (the `prefetch_rows` field carries the latter; 0 means 1).
+int ws_nodes_per_quad(int pf) { return pf == 2 ? 2 : 1; }
 
 template <typename F>
 void with_ws(int stages, int pf, F&& f) {
   const int k = ws_nodes_per_quad(pf);
   auto pick_k = [&](auto sc) {
-    if (k == 4)
-      f(sc, std::integral_constant<int, 4>{});
-    else if (k == 2)
+    if (k == 2)
       f(sc, std::integral_constant<int, 2>{});
     else
       f(sc, std::integral_constant<int, 1>{});
@@ -1143,8 +1141,8 @@ int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_
   if (ws && (threads_x != 128 || tma_tile != 128 || rows > 4))
     return bfail(LBM_EINVAL, "lbm_batch_set_launch: the producer/consumer path takes (threads, tile) = (128, 128) "
                              "and 3 or 4 stages, got (%d, %d, %d)", threads_x, tma_tile, rows);
-  if (ws && prefetch_rows != 0 && prefetch_rows != 1 && prefetch_rows != 2 && prefetch_rows != 4)
-    return bfail(LBM_EINVAL, "lbm_batch_set_launch: the producer/consumer path takes 1, 2 or 4 perimeter nodes per "
+  if (ws && prefetch_rows != 0 && prefetch_rows != 1 && prefetch_rows != 2)
+    return bfail(LBM_EINVAL, "lbm_batch_set_launch: the producer/consumer path takes 1 or 2 perimeter nodes per "
                              "lane quad, got %d", prefetch_rows);
   if (tma_tile == 0 && !batch_shape_ok(threads_x, rows))
     return bfail(LBM_EINVAL, "lbm_batch_set_launch: shape (%d, %d) not compiled", threads_x, rows);
@@ -1236,10 +1234,10 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
     if (rc) break;
     keep(time_it());
   }
-  // producer/consumer path: one issuing warp, 3 or 4 tile stages, 1, 2 or 4
+  // producer/consumer path: one issuing warp, 3 or 4 tile stages, 1 or 2
   // perimeter nodes per lane quad
   for (int st : {3, 4})
-    for (int kq : {1, 2, 4}) {
+    for (int kq : {1, 2}) {
       if (rc) break;
       b->bx = 128;
       b->rows = st;

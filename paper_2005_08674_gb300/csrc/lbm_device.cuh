@@ -418,10 +418,9 @@ __device__ __forceinline__ void node_moments_f64(const T* __restrict__ A, const 
   m[2] = jy / rho;
 }
 
-// (rho - 1, ux, uy) at node (x, y) in the compute type of the storage: the
-// shifted populations keep d_rho free of cancellation, so float is exact to
-// float rounding of the perturbation itself.
-// (rho - 1, ux, uy) of a node's shifted populations (physical units).
+// (rho - 1, ux, uy) of a node's shifted populations (physical units) in the
+// compute type of the storage: the shifted populations keep d_rho free of
+// cancellation, so float is exact to float rounding of the perturbation.
 template <typename C>
 __device__ __forceinline__ void dmoments_of(const C (&h)[9], C (&m)[3]) {
   C drho, jx, jy;
@@ -430,18 +429,6 @@ __device__ __forceinline__ void dmoments_of(const C (&h)[9], C (&m)[3]) {
   m[0] = drho;
   m[1] = jx * inv;
   m[2] = jy * inv;
-}
-
-template <typename T>
-__device__ __forceinline__ void node_dmoments(const T* __restrict__ A, const Geom& g, int x, int y,
-                                              typename Store<T>::C (&m)[3]) {
-  using S = Store<T>;
-  using C = typename S::C;
-  const long long o = (long long)y * g.pitch + x;
-  C h[9];
-#pragma unroll
-  for (int i = 0; i < 9; ++i) h[i] = S::ldg1(A + i * g.plane + o);
-  dmoments_of(h, m);
 }
 
 }  // namespace lbmk

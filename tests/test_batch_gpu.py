@@ -68,7 +68,7 @@ def test_batch_f64_matches_oracle(lbm):
 
 @pytest.mark.parametrize("shape", [(64, 1, 0, 0, 0, 0), (128, 2, 0, 1, 1, 0), (256, 4, 152, 0, 0, 0), (64, 4, 7, 64, 1, 0), (128, 1, 0, 0, 1, 128), (128, 1, 0, 0, 1, 256), (256, 1, 0, 0, 1, 256),
                                    (128, 4, -1, 1, 0, 0), (256, 1, -1, 0, 1, 0),
-                                   (128, 3, 0, 0, 0, 128), (128, 4, 0, 0, 0, 128), (128, 3, 5, 0, 0, 128)])
+                                   (128, 3, 0, 0, 0, 128), (128, 4, 0, 2, 0, 128), (128, 3, 5, 2, 0, 128)])
 def test_batch_launch_shapes_agree(lbm, shape):
     """Every tile shape, grid size (one block per item, persistent waves, a
     grid far smaller than the work list) and prefetch gives the same bits."""
