@@ -262,6 +262,29 @@ def run_batched(lbm, ws, bfields, storage, steps, warmup, world, peak, launch=No
     return out
 
 
+def run_one_at_a_time(lbm, ws, bfields, storage, steps):
+    """The same instances stepped one after another as single domains (graph
+    replays, default launch shape): MLUPS over the summed device times."""
+    import torch
+    total_ms, cells = 0.0, 0
+    for w, f in zip(ws, bfields):
+        s = lbm.Simulation(w.nx, w.ny, w.tau, w.farfield_rho, w.farfield_u, storage=storage)
+        s.init(*f)
+        s.step(16)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(s.stream)
+        s.step(steps)
+        a1.record(s.stream)
+        torch.cuda.synchronize()
+        total_ms += a0.elapsed_time(a1)
+        cells += w.nx * w.ny
+        s.close()
+    torch.cuda.empty_cache()
+    return {"mlups": cells * steps / (total_ms * 1e-3) / 1e6, "steps_each": steps,
+            "what": "each instance alone as a single domain (CUDA graphs of 16 steps), device times summed"}
+
+
 def run_batched_only(args, rank, world, local_rank):
     """--batched-only: the batched workload alone (for profiling runs)."""
     import torch
@@ -458,6 +481,9 @@ def run_ours(args, rank, world, local_rank):
         bsteps = min(args.steps, 1000)
         for st in ("f32", "f16"):
             variants[f"batched_{st}"] = run_batched(lbm, ws, bfields, st, bsteps, args.warmup, world, peak)
+            one = run_one_at_a_time(lbm, ws, bfields, st, 64)
+            one["batched_speedup"] = variants[f"batched_{st}"]["mlups"] / world / one["mlups"]
+            variants[f"batched_{st}"]["one_at_a_time"] = one
         del bfields
         if line is not None:
             line["variants"] = variants
