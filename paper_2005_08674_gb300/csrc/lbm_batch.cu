@@ -1030,13 +1030,11 @@ int lbm_batch_init(lbm_batch_t* b, int32_t k, const double* rho, const double* u
   const double* src[3] = {rho, ux, uy};
   for (int c = 0; c < 3; ++c)
     BATCH_CUDA(cudaMemcpyAsync(bscratch(b, c), src[c], bytes, cudaMemcpyHostToDevice, b->stream));
-  const long long n = (long long)d.ny * d.pitch;
-  const int grid = (int)std::min<long long>(152LL * 32, (n + 255) / 256);
   bdispatch(b->storage, [&](auto tag) {
     using T = decltype(tag);
     for (int p = 0; p < 2; ++p)
-      lbmk::init_kernel<T><<<grid, 256, 0, b->stream>>>(static_cast<T*>(b->pool[p]) + d.off, inst_geom(d),
-                                                        bscratch(b, 0), bscratch(b, 1), bscratch(b, 2));
+      lbmk::init_kernel<T><<<lbmk::rows_grid(d.pitch, d.ny), 256, 0, b->stream>>>(
+          static_cast<T*>(b->pool[p]) + d.off, inst_geom(d), bscratch(b, 0), bscratch(b, 1), bscratch(b, 2), 0, d.ny);
   });
   rc = batch_check_launch();
   if (rc) return rc;
@@ -1091,11 +1089,11 @@ int lbm_batch_get_macros(lbm_batch_t* b, int32_t k, double* rho, double* ux, dou
   if (!b->initialised[k]) return bfail(LBM_ESTATE, "lbm_batch_get_macros: instance %d not initialised", k);
   const InstDev& d = b->inst[k];
   const long long n = (long long)d.nx * d.ny;
-  const int grid = (int)std::min<long long>(152LL * 32, (n + 255) / 256);
   bdispatch(b->storage, [&](auto tag) {
     using T = decltype(tag);
-    lbmk::macros_kernel<T><<<grid, 256, 0, b->stream>>>(static_cast<const T*>(b->pool[b->cur]) + d.off, inst_geom(d),
-                                                        bscratch(b, 0), bscratch(b, 1), bscratch(b, 2));
+    lbmk::macros_kernel<T><<<lbmk::rows_grid(d.nx, d.ny), 256, 0, b->stream>>>(
+        static_cast<const T*>(b->pool[b->cur]) + d.off, inst_geom(d), bscratch(b, 0), bscratch(b, 1), bscratch(b, 2),
+        0, d.ny);
   });
   int rc = batch_check_launch();
   if (rc) return rc;

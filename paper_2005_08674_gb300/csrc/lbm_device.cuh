@@ -413,9 +413,10 @@ __device__ __forceinline__ void node_moments_f64(const T* __restrict__ A, const 
   double drho, jx, jy;
   moments(h, drho, jx, jy);
   const double rho = 1.0 + drho;
+  const double inv = 1.0 / rho;  // one FP64 divide (GB300's FP64 pipe is narrow)
   m[0] = rho;
-  m[1] = jx / rho;
-  m[2] = jy / rho;
+  m[1] = jx * inv;
+  m[2] = jy * inv;
 }
 
 // (rho - 1, ux, uy) of a node's shifted populations (physical units) in the

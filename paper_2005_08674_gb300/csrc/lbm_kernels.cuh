@@ -334,40 +334,51 @@ __global__ void __launch_bounds__(128) nsbc_kernel(const T* __restrict__ A, T* _
 }
 
 // ---------------------------------------------------------------------------
-// Initialisation at equilibrium (Eq. feq_1) from double fields [ny][nx];
-// padding columns are zeroed.
+// Initialisation at equilibrium (Eq. feq_1) of rows [y0, y1) from double
+// fields [ny][nx]; padding columns are zeroed.  The shifted equilibrium is
+// formed in the compute type of the storage (double for f64 storage).
+// Grid: x over the pitch, blockIdx.y striding over the rows (no divisions).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void init_kernel(T* __restrict__ A, Geom g, const double* __restrict__ rho,
-                            const double* __restrict__ ux, const double* __restrict__ uy) {
+                            const double* __restrict__ ux, const double* __restrict__ uy, int y0, int y1) {
   using S = Store<T>;
-  const long long n = (long long)g.ny * g.pitch;
-  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(idx / g.pitch), x = (int)(idx % g.pitch);
-    double e[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  using C = typename S::C;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.pitch) return;
+  for (int y = y0 + (int)blockIdx.y; y < y1; y += (int)gridDim.y) {
+    C e[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) e[i] = C(0);
     if (x < g.nx) {
       const long long k = (long long)y * g.nx + x;
-      equilibrium(rho[k] - 1.0, ux[k], uy[k], e);
+      equilibrium(C(rho[k] - 1.0), C(ux[k]), C(uy[k]), e);
     }
+    const long long idx = (long long)y * g.pitch + x;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) A[i * g.plane + idx] = S::cvt(typename S::C(e[i]));
+    for (int i = 0; i < 9; ++i) A[i * g.plane + idx] = S::cvt(e[i]);
   }
 }
 
-// Macroscopic fields (double) of the stored state.
+// Macroscopic fields (double) of rows [y0, y1) of the stored state; same grid.
 template <typename T>
 __global__ void macros_kernel(const T* __restrict__ A, Geom g, double* __restrict__ rho, double* __restrict__ ux,
-                              double* __restrict__ uy) {
-  const long long n = (long long)g.ny * g.nx;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-    const int y = (int)(k / g.nx), x = (int)(k % g.nx);
+                              double* __restrict__ uy, int y0, int y1) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= g.nx) return;
+  for (int y = y0 + (int)blockIdx.y; y < y1; y += (int)gridDim.y) {
     double m[3];
     node_moments_f64(A, g, x, y, m);
+    const long long k = (long long)y * g.nx + x;
     rho[k] = m[0];
     ux[k] = m[1];
     uy[k] = m[2];
   }
+}
+
+// Grid for init_kernel / macros_kernel over `width` columns and `rows` rows.
+inline dim3 rows_grid(int width, int rows) {
+  return dim3((unsigned)((width + 255) / 256), (unsigned)(rows < 1 ? 1 : (rows > 2048 ? 2048 : rows)));
 }
 
 // One population plane <-> absolute double field [ny][nx].

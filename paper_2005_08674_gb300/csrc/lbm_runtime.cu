@@ -79,6 +79,7 @@ struct lbm {
   cudaStream_t stream = nullptr;
   cudaStream_t cap = nullptr, side = nullptr;  // capture stream and NSBC branch
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_chunk[8] = {};  // row chunks of the host transfers (lbm_init, lbm_get_macros)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // by starting buffer
   int bx = 128, rows = 1, pf = 0;  // bulk launch shape and L2 prefetch distance (rows)
   int device = 0;
@@ -133,6 +134,7 @@ int ensure_streams(lbm_t* h) {
     LBM_CUDA(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
     LBM_CUDA(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
     LBM_CUDA(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    for (auto& e : h->ev_chunk) LBM_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   }
   return LBM_OK;
 }
@@ -194,6 +196,26 @@ void dispatch(int storage, F&& f) {
     case LBM_BF16: f(__nv_bfloat16{}); break;
     default: f(float{}); break;
   }
+}
+
+// Equilibrium initialisation of rows [y0, y1) of both buffers (the other
+// buffer's padding columns start defined too) from device fields [ny][nx].
+void enqueue_init_rows(const lbm_t* h, const double* d_rho, const double* d_ux, const double* d_uy, int y0, int y1) {
+  dispatch(h->storage, [&](auto tag) {
+    using T = decltype(tag);
+    const dim3 grid = lbmk::rows_grid(h->pitch, y1 - y0);
+    for (int b = 0; b < 2; ++b)
+      lbmk::init_kernel<T><<<grid, 256, 0, h->stream>>>(static_cast<T*>(h->buf[b]), geom(h), d_rho, d_ux, d_uy, y0,
+                                                        y1);
+  });
+}
+
+void enqueue_macros_rows(const lbm_t* h, double* d_rho, double* d_ux, double* d_uy, int y0, int y1) {
+  dispatch(h->storage, [&](auto tag) {
+    using T = decltype(tag);
+    lbmk::macros_kernel<T><<<lbmk::rows_grid(h->nx, y1 - y0), 256, 0, h->stream>>>(
+        static_cast<const T*>(h->buf[h->cur]), geom(h), d_rho, d_ux, d_uy, y0, y1);
+  });
 }
 
 // One step from buffer `from` to 1 - from.  With `fork`, the NSBC kernel runs
@@ -327,6 +349,7 @@ void lbm_destroy(lbm_t* h) {
     cudaStreamDestroy(h->side);
     cudaEventDestroy(h->ev_fork);
     cudaEventDestroy(h->ev_join);
+    for (cudaEvent_t e : h->ev_chunk) cudaEventDestroy(e);
   }
   delete h;
 }
@@ -438,15 +461,7 @@ int lbm_init_device(lbm_t* h, const double* d_rho, const double* d_ux, const dou
   int rc = ensure_memory(h);
   if (rc) return rc;
   h->cur = 0;
-  const long long n = (long long)h->ny * h->pitch;
-  dispatch(h->storage, [&](auto tag) {
-    using T = decltype(tag);
-    lbmk::init_kernel<T><<<grid_for(n, 256), 256, 0, h->stream>>>(static_cast<T*>(h->buf[0]), geom(h), d_rho, d_ux,
-                                                                   d_uy);
-    // the other buffer's boundary-free padding and untouched nodes start defined
-    lbmk::init_kernel<T><<<grid_for(n, 256), 256, 0, h->stream>>>(static_cast<T*>(h->buf[1]), geom(h), d_rho, d_ux,
-                                                                   d_uy);
-  });
+  enqueue_init_rows(h, d_rho, d_ux, d_uy, 0, h->ny);
   rc = check_launch();
   if (rc) return rc;
   h->initialised = true;
@@ -458,12 +473,29 @@ int lbm_init(lbm_t* h, const double* rho, const double* ux, const double* uy) {
   if (!h || !rho || !ux || !uy) return fail(LBM_EINVAL, "lbm_init: NULL argument");
   int rc = ensure_memory(h);
   if (rc) return rc;
-  const size_t bytes = (size_t)h->nx * h->ny * sizeof(double);
-  const double* src[3] = {rho, ux, uy};
-  for (int c = 0; c < 3; ++c)
-    LBM_CUDA(cudaMemcpyAsync(scratch_field(h, c), src[c], bytes, cudaMemcpyHostToDevice, h->stream));
-  rc = lbm_init_device(h, scratch_field(h, 0), scratch_field(h, 1), scratch_field(h, 2));
+  rc = ensure_streams(h);
   if (rc) return rc;
+  // the copy of row chunk c (side stream, copy engine) overlaps the
+  // initialisation of chunk c - 1 (the handle's stream)
+  const double* src[3] = {rho, ux, uy};
+  LBM_CUDA(cudaEventRecord(h->ev_fork, h->stream));  // earlier work on the scratch area first
+  LBM_CUDA(cudaStreamWaitEvent(h->side, h->ev_fork, 0));
+  h->cur = 0;
+  constexpr int K = (int)(sizeof(h->ev_chunk) / sizeof(h->ev_chunk[0]));
+  for (int c = 0; c < K; ++c) {
+    const int y0 = (int)((long long)h->ny * c / K), y1 = (int)((long long)h->ny * (c + 1) / K);
+    if (y1 <= y0) continue;
+    const size_t off = (size_t)y0 * h->nx, bytes = (size_t)(y1 - y0) * h->nx * sizeof(double);
+    for (int f = 0; f < 3; ++f)
+      LBM_CUDA(cudaMemcpyAsync(scratch_field(h, f) + off, src[f] + off, bytes, cudaMemcpyHostToDevice, h->side));
+    LBM_CUDA(cudaEventRecord(h->ev_chunk[c], h->side));
+    LBM_CUDA(cudaStreamWaitEvent(h->stream, h->ev_chunk[c], 0));
+    enqueue_init_rows(h, scratch_field(h, 0), scratch_field(h, 1), scratch_field(h, 2), y0, y1);
+  }
+  rc = check_launch();
+  if (rc) return rc;
+  h->initialised = true;
+  h->steps = 0;
   LBM_CUDA(cudaStreamSynchronize(h->stream));
   return LBM_OK;
 }
@@ -507,24 +539,34 @@ int64_t lbm_steps_done(const lbm_t* h) { return h ? h->steps : -1; }
 int lbm_get_macros_device(lbm_t* h, double* d_rho, double* d_ux, double* d_uy) {
   if (!h || !d_rho || !d_ux || !d_uy) return fail(LBM_EINVAL, "lbm_get_macros_device: NULL argument");
   if (!h->initialised) return fail(LBM_ESTATE, "lbm_get_macros_device: call lbm_init first");
-  const long long n = (long long)h->nx * h->ny;
-  dispatch(h->storage, [&](auto tag) {
-    using T = decltype(tag);
-    lbmk::macros_kernel<T><<<grid_for(n, 256), 256, 0, h->stream>>>(static_cast<const T*>(h->buf[h->cur]), geom(h),
-                                                                     d_rho, d_ux, d_uy);
-  });
+  enqueue_macros_rows(h, d_rho, d_ux, d_uy, 0, h->ny);
   return check_launch();
 }
 
 int lbm_get_macros(lbm_t* h, double* rho, double* ux, double* uy) {
   if (!h || !rho || !ux || !uy) return fail(LBM_EINVAL, "lbm_get_macros: NULL argument");
-  int rc = lbm_get_macros_device(h, scratch_field(h, 0), scratch_field(h, 1), scratch_field(h, 2));
+  if (!h->initialised) return fail(LBM_ESTATE, "lbm_get_macros: call lbm_init first");
+  int rc = ensure_streams(h);
   if (rc) return rc;
-  const size_t bytes = (size_t)h->nx * h->ny * sizeof(double);
+  // the macros of row chunk c (the handle's stream) overlap the copy-out of
+  // chunk c - 1 (side stream, copy engine)
   double* dst[3] = {rho, ux, uy};
-  for (int c = 0; c < 3; ++c)
-    LBM_CUDA(cudaMemcpyAsync(dst[c], scratch_field(h, c), bytes, cudaMemcpyDeviceToHost, h->stream));
-  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  constexpr int K = (int)(sizeof(h->ev_chunk) / sizeof(h->ev_chunk[0]));
+  for (int c = 0; c < K; ++c) {
+    const int y0 = (int)((long long)h->ny * c / K), y1 = (int)((long long)h->ny * (c + 1) / K);
+    if (y1 <= y0) continue;
+    enqueue_macros_rows(h, scratch_field(h, 0), scratch_field(h, 1), scratch_field(h, 2), y0, y1);
+    LBM_CUDA(cudaEventRecord(h->ev_chunk[c], h->stream));
+    LBM_CUDA(cudaStreamWaitEvent(h->side, h->ev_chunk[c], 0));
+    const size_t off = (size_t)y0 * h->nx, bytes = (size_t)(y1 - y0) * h->nx * sizeof(double);
+    for (int f = 0; f < 3; ++f)
+      LBM_CUDA(cudaMemcpyAsync(dst[f] + off, scratch_field(h, f) + off, bytes, cudaMemcpyDeviceToHost, h->side));
+  }
+  rc = check_launch();
+  if (rc) return rc;
+  LBM_CUDA(cudaEventRecord(h->ev_join, h->side));  // later work on the handle's stream waits for the copies
+  LBM_CUDA(cudaStreamWaitEvent(h->stream, h->ev_join, 0));
+  LBM_CUDA(cudaStreamSynchronize(h->side));
   return LBM_OK;
 }
 
