@@ -1032,9 +1032,9 @@ int lbm_batch_init(lbm_batch_t* b, int32_t k, const double* rho, const double* u
     BATCH_CUDA(cudaMemcpyAsync(bscratch(b, c), src[c], bytes, cudaMemcpyHostToDevice, b->stream));
   bdispatch(b->storage, [&](auto tag) {
     using T = decltype(tag);
-    for (int p = 0; p < 2; ++p)
-      lbmk::init_kernel<T><<<lbmk::rows_grid(d.pitch, d.ny), 256, 0, b->stream>>>(
-          static_cast<T*>(b->pool[p]) + d.off, inst_geom(d), bscratch(b, 0), bscratch(b, 1), bscratch(b, 2), 0, d.ny);
+    lbmk::init_kernel<T><<<lbmk::rows_grid(d.pitch, d.ny), 256, 0, b->stream>>>(
+        static_cast<T*>(b->pool[0]) + d.off, static_cast<T*>(b->pool[1]) + d.off, inst_geom(d), bscratch(b, 0),
+        bscratch(b, 1), bscratch(b, 2), 0, d.ny);
   });
   rc = batch_check_launch();
   if (rc) return rc;

@@ -334,29 +334,34 @@ __global__ void __launch_bounds__(128) nsbc_kernel(const T* __restrict__ A, T* _
 }
 
 // ---------------------------------------------------------------------------
-// Initialisation at equilibrium (Eq. feq_1) of rows [y0, y1) from double
-// fields [ny][nx]; padding columns are zeroed.  The shifted equilibrium is
-// formed in the compute type of the storage (double for f64 storage).
-// Grid: x over the pitch, blockIdx.y striding over the rows (no divisions).
+// Initialisation at equilibrium (Eq. feq_1) of rows [y0, y1) of A (and of
+// A2 if not null) from double fields [ny][nx]; padding columns are zeroed.
+// The equilibrium is formed in double and rounded once to the storage type
+// (forming it in float measurably changed the 16-bit runs' reflection
+// figures).  Grid: x over the pitch, blockIdx.y striding over the rows.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void init_kernel(T* __restrict__ A, Geom g, const double* __restrict__ rho,
+__global__ void init_kernel(T* __restrict__ A, T* __restrict__ A2, Geom g, const double* __restrict__ rho,
                             const double* __restrict__ ux, const double* __restrict__ uy, int y0, int y1) {
   using S = Store<T>;
   using C = typename S::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= g.pitch) return;
   for (int y = y0 + (int)blockIdx.y; y < y1; y += (int)gridDim.y) {
-    C e[9];
+    double e[9];
 #pragma unroll
-    for (int i = 0; i < 9; ++i) e[i] = C(0);
+    for (int i = 0; i < 9; ++i) e[i] = 0.0;
     if (x < g.nx) {
       const long long k = (long long)y * g.nx + x;
-      equilibrium(C(rho[k] - 1.0), C(ux[k]), C(uy[k]), e);
+      equilibrium(rho[k] - 1.0, ux[k], uy[k], e);
     }
     const long long idx = (long long)y * g.pitch + x;
 #pragma unroll
-    for (int i = 0; i < 9; ++i) A[i * g.plane + idx] = S::cvt(e[i]);
+    for (int i = 0; i < 9; ++i) {
+      const T v = S::cvt(C(e[i]));
+      A[i * g.plane + idx] = v;
+      if (A2) A2[i * g.plane + idx] = v;
+    }
   }
 }
 
@@ -435,23 +440,25 @@ __global__ void __launch_bounds__(NT) reduce_kernel(const T* __restrict__ A, Geo
   __shared__ double smem[NT / 32];
   const double cs2 = 1.0 / 3.0;
   double s[4] = {0.0, 0.0, 0.0, 0.0};
-  const long long n = (long long)g.ny * g.nx;
-  for (long long k = blockIdx.x * (long long)NT + threadIdx.x; k < n; k += (long long)gridDim.x * NT) {
-    const int y = (int)(k / g.nx), x = (int)(k % g.nx);
-    double m[3];
-    node_moments_f64(A, g, x, y, m);
-    double rr = rho_ff, ur = uxf, vr = uyf;
-    if (ref.rho) {
-      const long long r = (long long)y * ref.pitch + x;
-      rr = ref.rho[r];
-      ur = ref.ux[r];
-      vr = ref.uy[r];
+  const double e_rho = 0.5 * cs2 / rho_ff;  // no FP64 divide per node
+  // rows over blocks, columns over threads (no integer divisions per node)
+  for (int y = blockIdx.x; y < g.ny; y += gridDim.x) {
+    for (int x = threadIdx.x; x < g.nx; x += NT) {
+      double m[3];
+      node_moments_f64(A, g, x, y, m);
+      double rr = rho_ff, ur = uxf, vr = uyf;
+      if (ref.rho) {
+        const long long r = (long long)y * ref.pitch + x;
+        rr = ref.rho[r];
+        ur = ref.ux[r];
+        vr = ref.uy[r];
+      }
+      const double dr = m[0] - rr, du = m[1] - ur, dv = m[2] - vr;
+      s[0] += m[0];
+      s[1] += e_rho * dr * dr + 0.5 * rho_ff * (du * du + dv * dv);
+      s[2] += 0.5 * m[0] * (m[1] * m[1] + m[2] * m[2]);
+      s[3] += (isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]) && m[0] > 0.0) ? 0.0 : 1.0;
     }
-    const double dr = m[0] - rr, du = m[1] - ur, dv = m[2] - vr;
-    s[0] += m[0];
-    s[1] += 0.5 * (cs2 * dr * dr / rho_ff + rho_ff * (du * du + dv * dv));
-    s[2] += 0.5 * m[0] * (m[1] * m[1] + m[2] * m[2]);
-    s[3] += (isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]) && m[0] > 0.0) ? 0.0 : 1.0;
   }
 #pragma unroll
   for (int c = 0; c < 4; ++c) {

@@ -203,10 +203,8 @@ void dispatch(int storage, F&& f) {
 void enqueue_init_rows(const lbm_t* h, const double* d_rho, const double* d_ux, const double* d_uy, int y0, int y1) {
   dispatch(h->storage, [&](auto tag) {
     using T = decltype(tag);
-    const dim3 grid = lbmk::rows_grid(h->pitch, y1 - y0);
-    for (int b = 0; b < 2; ++b)
-      lbmk::init_kernel<T><<<grid, 256, 0, h->stream>>>(static_cast<T*>(h->buf[b]), geom(h), d_rho, d_ux, d_uy, y0,
-                                                        y1);
+    lbmk::init_kernel<T><<<lbmk::rows_grid(h->pitch, y1 - y0), 256, 0, h->stream>>>(
+        static_cast<T*>(h->buf[0]), static_cast<T*>(h->buf[1]), geom(h), d_rho, d_ux, d_uy, y0, y1);
   });
 }
 
