@@ -266,7 +266,9 @@ int lbm_batch_get_macros(lbm_batch_t* b, int32_t k, double* rho, double* ux, dou
 /* Number of nodes of instance k with non-finite or non-positive density
  * (FP64 reduction); synchronises. */
 int lbm_batch_unstable_nodes(lbm_batch_t* b, int32_t k, int64_t* count);
-/* Work split: a bulk tile is threads_x (64, 128, 256) x `rows` (1, 2, 4)
+/* Launch shape of the batched step.  Default (no call): the
+ * producer/consumer form described last, (128, 3, 0, 1, 0, 128).
+ * Register path (tma_tile = 0): a bulk tile is threads_x (64, 128, 256) x `rows` (1, 2, 4)
  * 16-byte vectors of an instance's interior rows laid end to end (nodes per
  * thread = vector x rows); grid size `blocks` (-1 = one block per work item,
  * 0 = one resident wave of blocks looping over the list, > 0 = that many);

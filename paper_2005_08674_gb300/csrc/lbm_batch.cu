@@ -1,18 +1,24 @@
 // lbm_batch.cu -- many independent D2Q9 + NSBC simulations of uneven sizes
 // advanced by ONE persistent launch per step.
 //
-// Every instance keeps its own 9-plane layout (pitch = nx rounded up to 64,
-// planes 256-byte aligned) inside two shared pools A and B.  A work list of
-// int4 items drives the kernel: NSBC chunks (~instance, first perimeter
-// node, count) of threads_x / 4 nodes, then bulk tiles (instance, first
-// vector, count) of up to threads_x * rows 16-byte vectors of the instance's
-// interior rows flattened end to end (so narrow instances leave no lanes
-// idle; a warp may straddle two rows).  Blocks take items round-robin (or
-// one item each); bulk tiles and NSBC chunks of one step read only
-// pool A and write disjoint nodes of pool B, so no synchronisation is needed
-// inside the launch.  Each item runs the same device code as the single-domain
+// Every instance keeps its own 9-plane layout (pitch = nx rounded up to one
+// 16-byte vector, planes 256-byte aligned) inside two shared pools A and B.
+// A work list of int4 items drives the launch: NSBC chunks (~instance, first
+// perimeter node, count) and bulk tiles (instance, first vector, count) of
+// 16-byte vectors of the instance's interior rows flattened end to end (so
+// narrow instances leave no lanes idle).  Items of one step read only pool A
+// and write disjoint nodes of pool B, so no synchronisation is needed inside
+// the launch.  Each item runs the same device code as the single-domain
 // kernels (bulk_row, nsbc_node), so an instance's results are bit-identical
 // to a single-domain run with the same storage and collision model.
+//
+// Three forms, chosen by lbm_batch_set_launch or the autotuner:
+//   batch_ws_kernel   (default) producer warp + consumer warps: tiles staged
+//                     into shared memory by bulk copies, 3-4 stages in flight;
+//   batch_tma_kernel  the same staging with the whole block taking turns;
+//   batch_step_kernel tiles straight from global memory (register path).
+// The staged forms take items from a counter in device memory, in memory
+// order with each NSBC chunk after the tile that stages its rows.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -82,13 +88,15 @@ struct lbm_batch {
   InstDev* d_inst = nullptr;
   int4* d_items = nullptr;
   int n_items = 0, n_bulk_items = 0;
-  int bx = 128, rows = 1, blocks = -1;  // blocks: -1 one per item, 0 one resident wave, > 0 as given
-  int pf = 0;                           // L2 prefetch distance in rows inside bulk tiles
+  // launch shape; the default is the producer/consumer form (128 consumer
+  // threads, 3 stages of 128-vector tiles, one NSBC node per lane quad)
+  int bx = 128, rows = 3, blocks = 0;  // blocks: -1 one per item, 0 one resident wave, > 0 as given
+  int pf = 1;                          // register path: L2 prefetch distance; producer/consumer: nodes per quad
   bool split = false;                   // NSBC chunks in their own concurrent launch
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int wave = 1;                        // resident blocks on the device for the current shape
-  int tile = 0;                        // > 0: bulk tiles of this many vectors staged by bulk copies
+  int tile = 128;                      // > 0: bulk tiles of this many vectors staged by bulk copies
   int* d_err = nullptr;                // [0] work counter, [1] blocks done, [2] a bounded wait gave up
   bool items_dirty = true;
   std::vector<char> initialised;

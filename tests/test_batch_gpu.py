@@ -35,9 +35,9 @@ def single(lbm, w, storage, steps, **kw):
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 @pytest.mark.parametrize("collision", ["bgk", "mrt"])
-@pytest.mark.parametrize("launch", [None, (128, 3, 0, 0, 0, 128)])
+@pytest.mark.parametrize("launch", [None, (128, 1, -1, 0, 0, 0)])
 def test_batch_bit_identical_to_single_runs(lbm, storage, collision, launch):
-    """Default launch and the producer/consumer form (3 staged tiles)."""
+    """Default launch (the producer/consumer form) and the register path."""
     ws = small_batch()
     kw = dict(collision=collision, mrt_rates=(1.4, 1.4, 1.2), beta=0.05)
     with lbm.Batch(ws, storage=storage, **kw) as b:
