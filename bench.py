@@ -1,9 +1,11 @@
 #!/usr/bin/env python
 """D2Q9 + NSBC throughput on one GB300: MLUPS and the HBM roofline.
 
-One "step" is one lattice-Boltzmann time step of the whole domain: the fused
-pull-stream + BGK collide kernel over the interior and the NSBC kernel over
-the perimeter.  Default workload: 8192 x 8192 nodes, tau 0.55, four Gaussian
+One "step" is one lattice-Boltzmann time step of the whole domain: either
+the staged step kernel (one producer/consumer launch: interior tiles staged
+into shared memory by bulk copies, and the NSBC perimeter chunks) or the fused
+pull-stream + BGK collide kernel over the interior with the NSBC kernel over
+the perimeter beside it, whichever the autotuner finds faster.  Default workload: 8192 x 8192 nodes, tau 0.55, four Gaussian
 acoustic pulses (amplitude 1e-3, half-width 64) at seeded centres, NSBC on
 all four edges, FP32 shifted storage.
 
@@ -45,7 +47,9 @@ def parse():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
-    p.add_argument("--launch", default="", help="bulk launch shape 'threads_x,rows' instead of autotuning")
+    p.add_argument("--launch", default="",
+                   help="'threads_x,rows[,prefetch]' (bulk + NSBC kernel pair) or 'staged3' / 'staged4' "
+                        "instead of autotuning")
     p.add_argument("--batched-only", action="store_true", help="time only the batched workload")
     p.add_argument("--batch-launch", default="", help="batched launch 'threads_x,rows,blocks,prefetch,split'")
     return p.parse_args()
@@ -138,24 +142,34 @@ def measured_peak_gbs():
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for name in ("lbm_kernels.cuh", "lbm_device.cuh"):
+    for name in ("lbm_kernels.cuh", "lbm_device.cuh", "lbm_staged.cuh"):
         with open(os.path.join(ROOT, "paper_2005_08674_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(storage: str, interior_cells: int):
-    """DRAM bytes per bulk launch from the committed ncu summary, scaled by the
+def step_kernel(sim, nx, ny):
+    """(kernel description, traffic summary file stem, cells one launch updates)
+    of the kernel that carries the step: the staged kernel updates every node,
+    the bulk kernel the interior (the NSBC kernel the perimeter, beside it)."""
+    if sim.staged:
+        return ("batch_ws_kernel (staged step: interior tiles by bulk copies + NSBC chunks, "
+                f"{sim.staged} stages)", "staged_step_traffic", nx * ny)
+    return "bulk_kernel (fused pull-stream + BGK collide)", "bulk_kernel_traffic", (nx - 2) * (ny - 2)
+
+
+def profiled_traffic(stem: str, storage: str, cells: int):
+    """DRAM bytes per launch from the committed ncu summary, scaled by the
     cells one launch processes, if the kernel source is unchanged since then."""
-    path = os.path.join(ROOT, "profiles", f"bulk_kernel_traffic_{storage}.md")
+    path = os.path.join(ROOT, "profiles", f"{stem}_{storage}.md")
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m_sha = re.search(r"kernel_source_sha:\s*([0-9a-f]+)", text)
-    m_b = re.search(r"dram_bytes_per_interior_cell:\s*([0-9.]+)", text)
+    m_b = re.search(r"dram_bytes_per_cell:\s*([0-9.]+)", text)
     if not m_sha or not m_b or m_sha.group(1) != kernel_source_sha():
         return None
-    return float(m_b.group(1)) * interior_cells
+    return float(m_b.group(1)) * cells
 
 
 # --- CPU oracle (baseline / reference arm) --------------------------------------
@@ -324,7 +338,10 @@ def run_ours(args, rank, world, local_rank):
 
     sim = lbm.Simulation(w.nx, w.ny, w.tau, w.farfield_rho, w.farfield_u, storage=args.storage)
     sim.init(*fields)
-    if args.launch:
+    if args.launch.startswith("staged"):
+        bx, rows, pf = 0, 0, 0
+        sim.set_staged(int(args.launch[len("staged"):] or 3))
+    elif args.launch:
         parts = [int(v) for v in args.launch.split(",")]
         bx, rows, pf = (parts + [0])[:3]
         sim.set_launch(bx, rows, pf)
@@ -367,9 +384,10 @@ def run_ours(args, rank, world, local_rank):
     bulk_avg = bulk_ms / max(nb, 1)
     nsbc_avg = nsbc_ms / max(nn, 1)
     peak, peak_kind = measured_peak_gbs()
-    alg_bytes = BYTES_PER_CELL[args.storage] * interior
+    kname, kstem, kcells = step_kernel(sim, w.nx, w.ny)
+    alg_bytes = BYTES_PER_CELL[args.storage] * kcells
     achieved = alg_bytes / (bulk_avg * 1e-3) / 1e9
-    traffic = profiled_traffic(args.storage, interior)
+    traffic = profiled_traffic(kstem, args.storage, kcells)
 
     line = None
     if rank == 0:
@@ -378,18 +396,19 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
             "config": {"workload": describe(w, args.storage), "nx": w.nx, "ny": w.ny,
-                       "bulk_launch": {"threads_x": bx, "rows": rows, "prefetch_rows": pf},
+                       "step_kernel": {"staged_stages": sim.staged} if sim.staged else
+                       {"bulk_threads_x": bx, "bulk_rows": rows, "prefetch_rows": pf},
                        "l2": f"inputs larger than L2: {lbm.lbm_buffer_bytes(sim.h) / 1e9:.2f} GB per population buffer",
                        "parallelism": "replicas" if world > 1 else "single-gpu",
                        "stable": bool(stable)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "bulk_kernel (fused pull-stream + BGK collide)",
-                         "bytes_per_cell": BYTES_PER_CELL[args.storage], "cells_per_launch": interior,
+                         "kernel": kname,
+                         "bytes_per_cell": BYTES_PER_CELL[args.storage], "cells_per_launch": kcells,
                          "avg_launch_ms": bulk_avg, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                         "nsbc_avg_launch_ms": nsbc_avg,
+                         "nsbc_avg_launch_ms": nsbc_avg if nn else None,
                          "timing": f"per-launch CUDA events over {kprof} steps after the timed region"},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": (1 if sim.staged else 2) * args.steps,
             "clocks": clk,
         }
 
@@ -446,9 +465,11 @@ def run_ours(args, rank, world, local_rank):
             s2.step(min(vsteps, 200))
             bms, bn, _, _ = lbm.lbm_profile_read(s2.h)
             bavg = bms / max(bn, 1)
-            gbs = BYTES_PER_CELL[st] * interior / (bavg * 1e-3) / 1e9
+            vname, _, vcells = step_kernel(s2, w.nx, w.ny)
+            gbs = BYTES_PER_CELL[st] * vcells / (bavg * 1e-3) / 1e9
             variants[st] = {"mlups": world * cells * vsteps / (vms * 1e-3) / 1e6, "steps": vsteps,
-                            "bulk_gbs": gbs, "bulk_frac": gbs / peak, "bulk_launch": [vb, vr, vp]}
+                            "kernel_gbs": gbs, "kernel_frac": gbs / peak, "kernel": vname,
+                            "bulk_launch": None if s2.staged else [vb, vr, vp]}
             s2.close()
             del s2
             torch.cuda.empty_cache()

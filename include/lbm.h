@@ -188,15 +188,38 @@ int lbm_reduce(lbm_t* h, const double* ref_rho, const double* ref_ux, const doub
  * (64, 128, 256, 512), rows per block (1, 2, 4, 8), and the distance in rows
  * (0 = off, at most 64) at which each warp asks the bulk-copy engine to
  * prefetch its next segments into L2.  threads_x = rows = 0 restores the
- * built-in shape.  Returns LBM_EINVAL for shapes the kernel was not compiled
- * for. */
+ * built-in shape.  Selects the bulk + NSBC kernel pair (turns the staged
+ * kernel below off).  Returns LBM_EINVAL for shapes the kernel was not
+ * compiled for. */
 int lbm_set_launch(lbm_t* h, int32_t threads_x, int32_t rows, int32_t prefetch_rows);
 
-/* Time every compiled bulk launch shape and prefetch distance on this
- * handle's own buffers (a few steps each, CUDA events on the stream) and keep
- * the fastest; the state is restored afterwards (through a temporary device
- * copy from cudaMallocAsync).  Writes the choice and its time per step in
- * milliseconds to the optional outputs. */
+/* Staged step kernel instead of the bulk + NSBC kernel pair: ONE persistent
+ * launch per step in which one producer warp per block claims work items of
+ * this domain from a counter in device memory -- tiles of 128 16-byte
+ * vectors of the flattened interior rows (padding columns included), staged
+ * into shared memory by nine cp.async.bulk copies completing on an mbarrier,
+ * and chunks of 32 perimeter nodes, each placed after the tile that stages
+ * its rows -- and keeps `stages` (3 or 4) of them in flight while 128
+ * consumer threads collide them.  Same arithmetic as the kernel pair, hence
+ * the same bits.  stages = 0 returns to the kernel pair.  Every wait of the
+ * kernel is bounded (about one second of SM clock); a wait that gives up
+ * makes it return early and lbm_status report LBM_ETIMEOUT.  LBM_EINVAL for
+ * other values.  Device memory for the work list is allocated at the next
+ * lbm_step. */
+int lbm_set_staged(lbm_t* h, int32_t stages);
+/* The current stages setting (0 = kernel pair), or LBM_EINVAL for NULL. */
+int32_t lbm_get_staged(const lbm_t* h);
+/* LBM_ETIMEOUT if a bounded wait of the staged kernel gave up (the state is
+ * then not valid), else LBM_OK; synchronises the stream. */
+int lbm_status(lbm_t* h);
+
+/* Time every compiled bulk launch shape and prefetch distance, and the
+ * staged kernel with 3 and 4 stages, on this handle's own buffers (a few
+ * whole steps each, CUDA events on the stream) and keep the fastest; the
+ * state is restored afterwards (through a temporary device copy from
+ * cudaMallocAsync).  Writes the bulk shape, and the time per step in
+ * milliseconds of the winner, to the optional outputs; lbm_get_staged tells
+ * whether the staged kernel won. */
 int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_rows, double* ms_per_step);
 
 /* Allocation-free form of lbm_reduce, for callers that cannot allocate
@@ -315,7 +338,8 @@ int lbm_wait_selftest(int64_t budget_cycles);
 /* Per-launch timing.  While enabled, lbm_step launches every step directly
  * (no graph) on the handle's stream with CUDA events around the bulk
  * stream-collide kernel and around the NSBC kernel, which then run one after
- * the other.  lbm_profile resets the record. */
+ * the other (with the staged kernel: around its one launch per step, counted
+ * as the bulk kernel).  lbm_profile resets the record. */
 int lbm_profile(lbm_t* h, int32_t enable);
 
 /* Read and reset the record (synchronises): out[0] = total bulk-kernel

@@ -14,6 +14,7 @@
 
 #include "lbm.h"
 #include "lbm_kernels.cuh"
+#include "lbm_staged.cuh"
 
 namespace {
 
@@ -85,9 +86,19 @@ struct lbm {
   int device = 0;
   int collision = 0;                          // 0 = BGK, 1 = MRT
   double s_e = 1.0, s_eps = 1.0, s_q = 1.0;   // MRT energy, energy-square and flux rates
-  // per-launch timing (lbm_profile): event pairs around every bulk and NSBC launch
+  // staged step kernel (lbm_set_staged): the producer/consumer kernel of
+  // lbm_staged.cuh over this domain's one-instance work list; 0 = off, else
+  // the number of tile stages
+  int staged = 0;
+  int4* d_items = nullptr;
+  lbmk::InstDev* d_inst = nullptr;
+  int* d_sched = nullptr;  // work counter, blocks done, give-up flag
+  int n_items = 0, items_storage = -1, staged_grid = 0;
+  // per-launch timing (lbm_profile): an event pair around every launch, and
+  // which kernel it was (0 = bulk or staged step kernel, 1 = NSBC)
   bool profiling = false;
   std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_kind;
   size_t ev_used = 0;
 };
 
@@ -112,6 +123,7 @@ void drop_graphs(lbm_t* h) {
       cudaGraphExecDestroy(g);
       g = nullptr;
     }
+  h->staged_grid = 0;  // the staged kernel's residency may have changed too
 }
 
 int ensure_memory(lbm_t* h) {
@@ -188,6 +200,50 @@ void launch_nsbc(const lbm_t* h, const void* a, void* b, cudaStream_t s) {
                                                             h->nsbc, rates<C>(h));
 }
 
+// ---- staged step kernel --------------------------------------------------
+// One launch per step: the producer warp of each block claims the domain's
+// work items (NSBC chunks of 32 nodes and tiles of 128 vectors of the
+// flattened interior, padding columns included) and stages the tiles into
+// shared memory; the 128 consumer threads collide them.  Same device
+// functions as the bulk and NSBC kernels, so the same bits.
+constexpr int kStagedThreads = 128, kStagedTile = 128;
+
+template <typename T, int MODEL, int STAGES>
+const void* staged_kernel() {
+  return (const void*)lbmk::batch_ws_kernel<T, kStagedThreads, MODEL, kStagedTile, STAGES, 1>;
+}
+
+template <typename T>
+const void* staged_kernel_for(const lbm_t* h) {
+  if (h->staged >= 4) return h->collision == 1 ? staged_kernel<T, 1, 4>() : staged_kernel<T, 0, 4>();
+  return h->collision == 1 ? staged_kernel<T, 1, 3>() : staged_kernel<T, 0, 3>();
+}
+
+int staged_smem(const lbm_t* h) { return (h->staged >= 4 ? 4 : 3) * 9 * (kStagedTile + 2) * 16; }
+
+template <typename T>
+void launch_staged(const lbm_t* h, const void* a, void* b, cudaStream_t s) {
+  const T* A = static_cast<const T*>(a);
+  T* B = static_cast<T*>(b);
+  const int smem = staged_smem(h);
+  const dim3 grid(h->staged_grid), block(kStagedThreads + 32);
+  auto go = [&](auto kernel) {
+    kernel<<<grid, block, smem, s>>>(A, B, h->d_inst, h->d_items, h->n_items, h->nsbc, h->s_e, h->s_eps, h->s_q,
+                                     h->d_sched);
+  };
+  if (h->staged >= 4) {
+    if (h->collision == 1)
+      go(lbmk::batch_ws_kernel<T, kStagedThreads, 1, kStagedTile, 4, 1>);
+    else
+      go(lbmk::batch_ws_kernel<T, kStagedThreads, 0, kStagedTile, 4, 1>);
+  } else {
+    if (h->collision == 1)
+      go(lbmk::batch_ws_kernel<T, kStagedThreads, 1, kStagedTile, 3, 1>);
+    else
+      go(lbmk::batch_ws_kernel<T, kStagedThreads, 0, kStagedTile, 3, 1>);
+  }
+}
+
 template <typename F>
 void dispatch(int storage, F&& f) {
   switch (storage) {
@@ -196,6 +252,51 @@ void dispatch(int storage, F&& f) {
     case LBM_BF16: f(__nv_bfloat16{}); break;
     default: f(float{}); break;
   }
+}
+
+// Work list, instance record and counters of the staged kernel (built once
+// the storage is fixed), and its grid: one resident wave of blocks.  Never
+// called inside a stream capture (lbm_step prepares it before capturing).
+int ensure_staged(lbm_t* h) {
+  if (!h->staged) return LBM_OK;
+  if (h->items_storage != h->storage) {
+    const int V = (int)(16 / h->elt);
+    lbmk::InstDev d{};
+    d.off = 0;
+    d.plane = h->plane;
+    d.nx = h->nx;
+    d.ny = h->ny;
+    d.pitch = h->pitch;
+    d.omega = 1.0 / h->tau;
+    for (int c = 0; c < 3; ++c) d.m0[c] = h->nsbc.m0[c];
+    std::vector<int4> items;
+    lbmk::staged_instance_items(0, d, V, kStagedTile, kStagedThreads / 4, items);
+    if (h->d_items) cudaFree(h->d_items);
+    h->d_items = nullptr;
+    LBM_CUDA(cudaMalloc(&h->d_items, items.size() * sizeof(int4)));
+    LBM_CUDA(cudaMemcpy(h->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    if (!h->d_inst) LBM_CUDA(cudaMalloc(&h->d_inst, sizeof(lbmk::InstDev)));
+    LBM_CUDA(cudaMemcpy(h->d_inst, &d, sizeof d, cudaMemcpyHostToDevice));
+    if (!h->d_sched) {
+      LBM_CUDA(cudaMalloc(&h->d_sched, 4 * sizeof(int)));
+      LBM_CUDA(cudaMemset(h->d_sched, 0, 4 * sizeof(int)));
+    }
+    h->n_items = (int)items.size();
+    h->items_storage = h->storage;
+  }
+  if (h->staged_grid <= 0) {
+    int per_sm = 0, sms = 0;
+    LBM_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+    dispatch(h->storage, [&](auto tag) {
+      using T = decltype(tag);
+      const void* k = staged_kernel_for<T>(h);
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, staged_smem(h));
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kStagedThreads + 32, staged_smem(h));
+    });
+    if (per_sm <= 0) return fail(LBM_ECUDA, "staged step kernel: no block fits on an SM");
+    h->staged_grid = std::min(h->n_items, per_sm * sms);
+  }
+  return LBM_OK;
 }
 
 // Equilibrium initialisation of rows [y0, y1) of both buffers (the other
@@ -224,6 +325,10 @@ void enqueue_step(const lbm_t* h, int from, cudaStream_t s, bool fork) {
   void* b = h->buf[1 - from];
   dispatch(h->storage, [&](auto tag) {
     using T = decltype(tag);
+    if (h->staged) {
+      launch_staged<T>(h, a, b, s);
+      return;
+    }
     if (fork) {
       cudaEventRecord(h->ev_fork, s);
       cudaStreamWaitEvent(h->side, h->ev_fork, 0);
@@ -250,33 +355,42 @@ int capture_graph(lbm_t* h, int from) {
   return LBM_OK;
 }
 
-int profiled_event(lbm_t* h, cudaEvent_t* out) {
-  if (h->ev_used == h->ev_pool.size()) {
-    cudaEvent_t e;
-    LBM_CUDA(cudaEventCreate(&e));
-    h->ev_pool.push_back(e);
+// Event pair for one profiled launch of kernel `kind` (0 bulk / staged, 1 NSBC).
+int profiled_pair(lbm_t* h, int kind, cudaEvent_t* e) {
+  for (int k = 0; k < 2; ++k) {
+    if (h->ev_used == h->ev_pool.size()) {
+      cudaEvent_t x;
+      LBM_CUDA(cudaEventCreate(&x));
+      h->ev_pool.push_back(x);
+      h->ev_kind.push_back(0);
+    }
+    h->ev_kind[h->ev_used] = kind;
+    e[k] = h->ev_pool[h->ev_used++];
   }
-  *out = h->ev_pool[h->ev_used++];
   return LBM_OK;
 }
 
-// One step with an event pair around each kernel, both on the handle's stream.
+// One step with an event pair around each kernel, all on the handle's stream.
 int enqueue_step_profiled(lbm_t* h, int from) {
   const void* a = h->buf[from];
   void* b = h->buf[1 - from];
   cudaEvent_t e[4];
-  for (auto& x : e) {
-    int rc = profiled_event(h, &x);
-    if (rc) return rc;
-  }
+  int rc = profiled_pair(h, 0, e);
+  if (!rc && !h->staged) rc = profiled_pair(h, 1, e + 2);
+  if (rc) return rc;
   dispatch(h->storage, [&](auto tag) {
     using T = decltype(tag);
     cudaEventRecord(e[0], h->stream);
-    launch_bulk<T>(h, a, b, h->bx, h->rows, h->stream);
+    if (h->staged)
+      launch_staged<T>(h, a, b, h->stream);
+    else
+      launch_bulk<T>(h, a, b, h->bx, h->rows, h->stream);
     cudaEventRecord(e[1], h->stream);
-    cudaEventRecord(e[2], h->stream);
-    launch_nsbc<T>(h, a, b, h->stream);
-    cudaEventRecord(e[3], h->stream);
+    if (!h->staged) {
+      cudaEventRecord(e[2], h->stream);
+      launch_nsbc<T>(h, a, b, h->stream);
+      cudaEventRecord(e[3], h->stream);
+    }
   });
   return LBM_OK;
 }
@@ -342,6 +456,9 @@ void lbm_destroy(lbm_t* h) {
     cudaFree(h->scratch);
   }
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  if (h->d_items) cudaFree(h->d_items);
+  if (h->d_inst) cudaFree(h->d_inst);
+  if (h->d_sched) cudaFree(h->d_sched);
   if (h->cap) {
     cudaStreamDestroy(h->cap);
     cudaStreamDestroy(h->side);
@@ -503,6 +620,7 @@ int lbm_step(lbm_t* h, int32_t n) {
   if (n < 0) return fail(LBM_EINVAL, "lbm_step: n=%d < 0", n);
   if (!h->initialised) return fail(LBM_ESTATE, "lbm_step: call lbm_init first");
   int rc = ensure_streams(h);
+  if (!rc) rc = ensure_staged(h);
   if (rc) return rc;
   int left = n;
   if (h->profiling) {
@@ -669,19 +787,17 @@ int lbm_profile(lbm_t* h, int32_t enable) {
 int lbm_profile_read(lbm_t* h, double out[4]) {
   if (!h || !out) return fail(LBM_EINVAL, "lbm_profile_read: NULL argument");
   LBM_CUDA(cudaStreamSynchronize(h->stream));
-  double bulk = 0.0, nsbc = 0.0;
-  const size_t steps = h->ev_used / 4;
-  for (size_t k = 0; k < steps; ++k) {
-    float a = 0.f, b = 0.f;
-    LBM_CUDA(cudaEventElapsedTime(&a, h->ev_pool[4 * k], h->ev_pool[4 * k + 1]));
-    LBM_CUDA(cudaEventElapsedTime(&b, h->ev_pool[4 * k + 2], h->ev_pool[4 * k + 3]));
-    bulk += a;
-    nsbc += b;
+  double ms[2] = {0.0, 0.0}, n[2] = {0.0, 0.0};
+  for (size_t k = 0; k + 1 < h->ev_used; k += 2) {
+    float t = 0.f;
+    LBM_CUDA(cudaEventElapsedTime(&t, h->ev_pool[k], h->ev_pool[k + 1]));
+    ms[h->ev_kind[k]] += t;
+    n[h->ev_kind[k]] += 1.0;
   }
-  out[0] = bulk;
-  out[1] = (double)steps;
-  out[2] = nsbc;
-  out[3] = (double)steps;
+  out[0] = ms[0];
+  out[1] = n[0];
+  out[2] = ms[1];
+  out[3] = n[1];
   h->ev_used = 0;
   return LBM_OK;
 }
@@ -699,7 +815,29 @@ int lbm_set_launch(lbm_t* h, int32_t threads_x, int32_t rows, int32_t prefetch_r
   h->bx = threads_x;
   h->rows = rows;
   h->pf = prefetch_rows;
+  h->staged = 0;
   drop_graphs(h);
+  return LBM_OK;
+}
+
+int lbm_set_staged(lbm_t* h, int32_t stages) {
+  if (!h) return fail(LBM_EINVAL, "lbm_set_staged: NULL handle");
+  if (stages != 0 && stages != 3 && stages != 4)
+    return fail(LBM_EINVAL, "lbm_set_staged: stages=%d (0 = off, 3 or 4)", stages);
+  h->staged = stages;
+  drop_graphs(h);
+  return LBM_OK;
+}
+
+int32_t lbm_get_staged(const lbm_t* h) { return h ? h->staged : LBM_EINVAL; }
+
+int lbm_status(lbm_t* h) {
+  if (!h) return fail(LBM_EINVAL, "lbm_status: NULL handle");
+  if (!h->d_sched) return LBM_OK;
+  int flag = 0;
+  LBM_CUDA(cudaMemcpyAsync(&flag, h->d_sched + 2, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  LBM_CUDA(cudaStreamSynchronize(h->stream));
+  if (flag) return fail(LBM_ETIMEOUT, "lbm_status: a bounded wait of the staged step kernel gave up");
   return LBM_OK;
 }
 
@@ -719,7 +857,19 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
   const long long cells = (long long)h->nx * h->ny;
   const int reps = (int)std::max<long long>(4, std::min<long long>(64, (1LL << 28) / std::max(cells, 1LL)));
   float best = 1e30f;
-  int best_bx = h->bx, best_rows = h->rows, best_pf = h->pf;
+  int best_bx = h->bx, best_rows = h->rows, best_pf = h->pf, best_staged = h->staged;
+  // whole steps as the graphs run them (NSBC kernel on the forked branch)
+  auto time_steps = [&]() -> float {
+    for (int k = 0; k < 2; ++k) enqueue_step(h, k & 1, h->stream, true);
+    cudaEventRecord(e0, h->stream);
+    for (int k = 0; k < reps; ++k) enqueue_step(h, k & 1, h->stream, true);
+    cudaEventRecord(e1, h->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return 1e30f;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    return ms / reps;
+  };
+  h->staged = 0;
   for (int bx : kShapesBX)
     for (int r : kShapesRows)
       for (int pf : kPrefetchRows) {
@@ -727,25 +877,31 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
         h->bx = bx;
         h->rows = r;
         h->pf = pf;
-        for (int k = 0; k < 2; ++k) enqueue_step(h, k & 1, h->stream, false);
-        cudaEventRecord(e0, h->stream);
-        for (int k = 0; k < reps; ++k) enqueue_step(h, k & 1, h->stream, false);
-        cudaEventRecord(e1, h->stream);
-        LBM_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        ms /= reps;
+        const float ms = time_steps();
         if (ms < best) {
           best = ms;
           best_bx = bx;
           best_rows = r;
           best_pf = pf;
+          best_staged = 0;
         }
       }
+  // the staged step kernel (producer/consumer, 3 or 4 tile stages)
+  for (int st : {3, 4}) {
+    h->staged = st;
+    drop_graphs(h);
+    if (ensure_staged(h) != LBM_OK) break;
+    const float ms = time_steps();
+    if (ms < best) {
+      best = ms;
+      best_staged = st;
+    }
+  }
   rc = check_launch();
   h->bx = best_bx;
   h->rows = best_rows;
   h->pf = best_pf;
+  h->staged = best_staged;
   drop_graphs(h);
   LBM_CUDA(cudaMemcpyAsync(h->buf[h->cur], backup, bb, cudaMemcpyDeviceToDevice, h->stream));
   LBM_CUDA(cudaFreeAsync(backup, h->stream));

@@ -61,6 +61,9 @@ _SIGS = {
     "lbm_load_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int64]),
     "lbm_set_launch": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
     "lbm_autotune": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _dp]),
+    "lbm_set_staged": (ctypes.c_int, [_vp, _i32]),
+    "lbm_get_staged": (ctypes.c_int32, [_vp]),
+    "lbm_status": (ctypes.c_int, [_vp]),
     "lbm_reduce_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _dp]),
     "lbm_profile": (ctypes.c_int, [_vp, _i32]),
     "lbm_profile_read": (ctypes.c_int, [_vp, _dp]),
@@ -272,6 +275,18 @@ def lbm_autotune(h):
     return bx.value, rows.value, pf.value, ms.value
 
 
+def lbm_set_staged(h, stages: int):
+    return _check(_L.lbm_set_staged(h, int(stages)))
+
+
+def lbm_get_staged(h) -> int:
+    return int(_L.lbm_get_staged(h))
+
+
+def lbm_status(h):
+    return _check(_L.lbm_status(h))
+
+
 def lbm_profile(h, enable: bool):
     return _check(_L.lbm_profile(h, int(bool(enable))))
 
@@ -390,6 +405,20 @@ class Simulation:
 
     def set_launch(self, threads_x, rows, prefetch_rows=0):
         lbm_set_launch(self.h, threads_x, rows, prefetch_rows)
+        return self
+
+    def set_staged(self, stages=3):
+        """The staged producer/consumer step kernel (3 or 4 stages; 0 = bulk + NSBC kernel pair)."""
+        lbm_set_staged(self.h, stages)
+        return self
+
+    @property
+    def staged(self) -> int:
+        return lbm_get_staged(self.h)
+
+    def status(self):
+        """Raises LbmError(LBM_ETIMEOUT) if a bounded device-side wait gave up."""
+        lbm_status(self.h)
         return self
 
 

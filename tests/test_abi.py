@@ -65,6 +65,14 @@ def test_host_side_argument_checks(lib_path):
             lbm.lbm_step(h, 1)  # not initialised
         with pytest.raises(lbm.LbmError):
             lbm.lbm_set_launch(h, 96, 1, 0)
+        assert lbm.lbm_get_staged(h) == 0
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_set_staged(h, 2)
+        lbm.lbm_set_staged(h, 3)
+        assert lbm.lbm_get_staged(h) == 3
+        lbm.lbm_set_launch(h, 128, 1, 0)  # back to the kernel pair
+        assert lbm.lbm_get_staged(h) == 0
+        lbm.lbm_status(h)  # nothing launched yet: OK without touching the device
         assert lbm.lbm_steps_done(h) == 0
     finally:
         lbm.lbm_destroy(h)

@@ -143,16 +143,25 @@ def _window(nx, ny, cx, cy, k):
 
 
 @pytest.mark.parametrize("storage", ["f32"])
-def test_full_size_8192_sampled(lbm, storage):
+@pytest.mark.parametrize("launch", ["autotuned", "staged", "pair"])
+def test_full_size_8192_sampled(lbm, storage, launch):
     """8192^2, four pulses, in the bench's launch configuration (graph replay,
-    autotuned bulk shape): sampled nodes after k steps against oracle windows."""
+    autotuned: the staged kernel or the bulk + NSBC pair, whichever is faster)
+    and in each of the two forced: sampled nodes after k steps against oracle
+    windows."""
     import torch
     w = inputs.pulse_8192()
     k = 20
     sim = lbm.Simulation(w.nx, w.ny, w.tau, storage=storage)
     sim.init(*w.fields())
-    sim.autotune()
+    if launch == "autotuned":
+        sim.autotune()
+    elif launch == "staged":
+        sim.set_staged(3)
+    else:
+        sim.set_launch(256, 1, 0)
     sim.step(k)
+    sim.status()
     mac = sim.macros_device()
     centres = [(int(round(c[0])), int(round(c[1]))) for c in w.params["centres"]]
     samples = centres + [(0, 0), (w.nx - 1, 0), (0, w.ny - 1), (w.nx - 1, w.ny - 1),
