@@ -639,6 +639,7 @@ lbm_batch_t* lbm_batch_create(int32_t count, const lbm_instance_desc* descs, int
     // one contiguous run of vectors, so a tile is one copy per plane
     d.pitch = (int)round_up((size_t)s.nx, 16 / b->elt);
     d.plane = (long long)(round_up((size_t)s.ny * d.pitch * b->elt, 256) / b->elt);
+    lbmk::set_row_divisor(d, (int)(16 / b->elt));
     d.off = off;
     d.omega = 1.0 / s.tau;
     d.m0[0] = s.farfield_rho;

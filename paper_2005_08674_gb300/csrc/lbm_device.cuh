@@ -284,20 +284,28 @@ __device__ __forceinline__ void equilibrium(C drho, C ux, C uy, C (&e)[9], C s =
   }
 }
 
+// a / rho for the velocity u = (rho u) / rho: in float the fast division
+// intrinsic (within 2 ulp for rho in the normal range; rho is near 1 here),
+// an IEEE division in double (the parity mode).
+__device__ __forceinline__ float div_rho(float a, float rho) { return __fdividef(a, rho); }
+__device__ __forceinline__ double div_rho(double a, double rho) { return a / rho; }
+
 // BGK collision, Eq. (lbe_1) with dt = 1, on shifted populations held as
 // s * h (s = storage scale; the relaxation is linear in h, only the moments
-// need 1/s).
+// need 1/s).  Written as h* = (1 - omega) h + omega h^eq with omega folded
+// into the equilibrium weights: one fused multiply-add per population.
 template <typename C>
 __device__ __forceinline__ void collide_bgk(C (&h)[9], C omega, C s = C(1)) {
   C sd, sjx, sjy;
   moments(h, sd, sjx, sjy);
   const C is = C(1) / s;
   const C drho = sd * is;
-  const C inv = is / (C(1) + drho);
+  const C inv = div_rho(is, C(1) + drho);
   C e[9];
-  equilibrium(drho, sjx * inv, sjy * inv, e, s);
+  equilibrium(drho, sjx * inv, sjy * inv, e, s * omega);
+  const C keep = C(1) - omega;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) h[i] = h[i] + omega * (e[i] - h[i]);
+  for (int i = 0; i < 9; ++i) h[i] = keep * h[i] + e[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -326,7 +334,7 @@ __device__ __forceinline__ void collide_mrt(C (&h)[9], const Rates<C>& r, C s = 
   moments(h, sd, sjx, sjy);
   const C is = C(1) / s;
   const C drho = sd * is;
-  const C inv = is / (C(1) + drho);
+  const C inv = div_rho(is, C(1) + drho);
   C e[9];
   equilibrium(drho, sjx * inv, sjy * inv, e, s);
   C n[9];

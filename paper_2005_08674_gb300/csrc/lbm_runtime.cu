@@ -269,6 +269,7 @@ int ensure_staged(lbm_t* h) {
     d.pitch = h->pitch;
     d.omega = 1.0 / h->tau;
     for (int c = 0; c < 3; ++c) d.m0[c] = h->nsbc.m0[c];
+    lbmk::set_row_divisor(d, V);
     std::vector<int4> items;
     lbmk::staged_instance_items(0, d, V, kStagedTile, kStagedThreads / 4, items);
     if (h->d_items) cudaFree(h->d_items);

@@ -19,10 +19,31 @@ namespace lbmk {
 struct InstDev {
   long long off;    // element offset of the instance's planes in each pool
   long long plane;  // elements per plane
-  int nx, ny, pitch, pad;
+  int nx, ny, pitch;
+  int vec_shift;      // divisor pitch / V (16-byte vectors per row) as a
+  unsigned vec_mul;   // multiply-and-shift pair, set by set_row_divisor
+  int pad;
   double omega;     // 1 / tau
   double m0[3];     // far field (rho, ux, uy)
 };
+
+// Division of a flattened vector index by the vectors per row, q = j / nvec,
+// as a multiply-high and a shift (Granlund & Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994): with
+// l = ceil(log2 nvec) and m = floor(2^32 (2^l - nvec) / nvec) + 1,
+// q = (umulhi(m, j) + j) >> l for every 0 <= j < 2^31 (the sum cannot
+// overflow since umulhi(m, j) <= j).
+inline void set_row_divisor(InstDev& d, int V) {
+  const unsigned long long nvec = (unsigned long long)(d.pitch / V);
+  int l = 0;
+  while ((1ull << l) < nvec) ++l;
+  d.vec_shift = l;
+  d.vec_mul = (unsigned)((((1ull << l) - nvec) << 32) / nvec + 1);
+}
+
+__device__ __forceinline__ int row_of_vector(int j, const InstDev& d) {
+  return (int)((__umulhi(d.vec_mul, (unsigned)j) + (unsigned)j) >> d.vec_shift);
+}
 
 // ---------------------------------------------------------------------------
 // Staging: an instance's flattened interior is ONE contiguous range per plane
@@ -122,7 +143,7 @@ __device__ __forceinline__ void collide_tile(const unsigned char* sl, const Inst
   for (int u2 = threadIdx.x; u2 < w.z * SPLIT; u2 += BX) {
     const int u = u2 / SPLIT, part = u2 - u * SPLIT;
     const int j = w.y + u;
-    const int y = 1 + j / nvec;
+    const int y = 1 + row_of_vector(j, d);
     const int x0 = (j - (y - 1) * nvec) * V + part * CPT;
     C v[9][CPT], lf[9], rt[9];
 #pragma unroll
