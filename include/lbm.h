@@ -150,7 +150,10 @@ int lbm_step(lbm_t* h, int32_t n);
 int64_t lbm_steps_done(const lbm_t* h);
 
 /* Macroscopic fields rho, ux, uy (Eqs. cf_0, cf_1 as discrete sums) of the
- * current state into HOST arrays [ny][nx] double; synchronises. */
+ * current state into HOST arrays [ny][nx] double; synchronises.  The sums
+ * are taken in the storage's compute type (float for f32 / f16 / bf16, where
+ * the shifted populations keep rho - 1 exact to float rounding; double for
+ * f64) and widened to double. */
 int lbm_get_macros(lbm_t* h, double* rho, double* ux, double* uy);
 
 /* As lbm_get_macros into DEVICE arrays [ny][nx] double; asynchronous. */
@@ -171,7 +174,9 @@ int lbm_save_state(lbm_t* h, void* host, size_t bytes, int64_t* steps);
 int lbm_load_state(lbm_t* h, const void* host, size_t bytes, int64_t steps);
 
 /* FP64 reductions over all nodes, used for the reflection measure and as an
- * instability check.  If ref_rho is non-NULL, ref_* are DEVICE [.][ref_pitch]
+ * instability check.  Each node's terms are formed in the storage's compute
+ * type (as for lbm_get_macros; rho_r - 1 is formed in double before it is
+ * rounded) and every sum is accumulated in double.  If ref_rho is non-NULL, ref_* are DEVICE [.][ref_pitch]
  * double fields whose element [0] is aligned with node (0, 0) of this
  * handle (pass a pointer into a larger, padded reference domain).  Writes
  * HOST out[4]:

@@ -409,20 +409,23 @@ __device__ __forceinline__ void perimeter_node(int k, int nx, int ny, int& x, in
   }
 }
 
-// Moments (rho, ux, uy) at node (x, y) in double, from the stored state.
+// (rho - 1, ux, uy) at node (x, y) from the stored state, in the compute
+// type of the storage: float for f32 / f16 / bf16 (the shifted populations
+// keep rho - 1 free of cancellation, so float loses nothing the storage kept),
+// double in the f64 parity mode.
 template <typename T>
-__device__ __forceinline__ void node_moments_f64(const T* __restrict__ A, const Geom& g, int x, int y,
-                                                 double (&m)[3]) {
+__device__ __forceinline__ void node_dmoments(const T* __restrict__ A, const Geom& g, int x, int y,
+                                              typename Store<T>::C (&m)[3]) {
   using S = Store<T>;
+  using C = typename S::C;
   const long long o = (long long)y * g.pitch + x;
-  double h[9];
+  C h[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) h[i] = (double)S::ldg1(A + i * g.plane + o);
-  double drho, jx, jy;
+  for (int i = 0; i < 9; ++i) h[i] = S::ldg1(A + i * g.plane + o);
+  C drho, jx, jy;
   moments(h, drho, jx, jy);
-  const double rho = 1.0 + drho;
-  const double inv = 1.0 / rho;  // one FP64 divide (GB300's FP64 pipe is narrow)
-  m[0] = rho;
+  const C inv = div_rho(C(1), C(1) + drho);
+  m[0] = drho;
   m[1] = jx * inv;
   m[2] = jy * inv;
 }

@@ -372,12 +372,12 @@ __global__ void macros_kernel(const T* __restrict__ A, Geom g, double* __restric
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= g.nx) return;
   for (int y = y0 + (int)blockIdx.y; y < y1; y += (int)gridDim.y) {
-    double m[3];
-    node_moments_f64(A, g, x, y, m);
+    typename Store<T>::C m[3];
+    node_dmoments(A, g, x, y, m);
     const long long k = (long long)y * g.nx + x;
-    rho[k] = m[0];
-    ux[k] = m[1];
-    uy[k] = m[2];
+    rho[k] = 1.0 + (double)m[0];
+    ux[k] = (double)m[1];
+    uy[k] = (double)m[2];
   }
 }
 
@@ -434,32 +434,44 @@ __device__ __forceinline__ double block_sum(double v, double* smem) {
   return s;  // valid in thread 0
 }
 
+// Per node: (rho - 1, u) in the storage's compute type, the three energy /
+// mass terms formed there, and every sum accumulated in double.  Sums:
+// [0] mass sum rho (node count + sum of rho - 1), [1] disturbance energy
+// sum cs^2 (rho - rho_r)^2 / (2 rho_ff) + rho_ff |u - u_r|^2 / 2 against the
+// reference field (or the far field), [2] kinetic energy sum rho |u|^2 / 2,
+// [3] nodes with a non-finite or non-positive density.
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) reduce_kernel(const T* __restrict__ A, Geom g, RefField ref, double rho_ff,
                                                     double uxf, double uyf, double* __restrict__ partials) {
+  using C = typename Store<T>::C;
   __shared__ double smem[NT / 32];
-  const double cs2 = 1.0 / 3.0;
   double s[4] = {0.0, 0.0, 0.0, 0.0};
-  const double e_rho = 0.5 * cs2 / rho_ff;  // no FP64 divide per node
+  long long count = 0;
+  const C e_rho = C(0.5 / (3.0 * rho_ff));  // cs^2 / (2 rho_ff), rounded once
+  const C e_u = C(0.5 * rho_ff);
+  const C dr_ff = C(rho_ff - 1.0), ur_ff = C(uxf), vr_ff = C(uyf);
   // rows over blocks, columns over threads (no integer divisions per node)
   for (int y = blockIdx.x; y < g.ny; y += gridDim.x) {
     for (int x = threadIdx.x; x < g.nx; x += NT) {
-      double m[3];
-      node_moments_f64(A, g, x, y, m);
-      double rr = rho_ff, ur = uxf, vr = uyf;
+      C m[3];
+      node_dmoments(A, g, x, y, m);
+      C drr = dr_ff, ur = ur_ff, vr = vr_ff;
       if (ref.rho) {
         const long long r = (long long)y * ref.pitch + x;
-        rr = ref.rho[r];
-        ur = ref.ux[r];
-        vr = ref.uy[r];
+        drr = C(ref.rho[r] - 1.0);  // rho_r - 1 rounded once: no cancellation against rho - 1
+        ur = C(ref.ux[r]);
+        vr = C(ref.uy[r]);
       }
-      const double dr = m[0] - rr, du = m[1] - ur, dv = m[2] - vr;
-      s[0] += m[0];
-      s[1] += e_rho * dr * dr + 0.5 * rho_ff * (du * du + dv * dv);
-      s[2] += 0.5 * m[0] * (m[1] * m[1] + m[2] * m[2]);
-      s[3] += (isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]) && m[0] > 0.0) ? 0.0 : 1.0;
+      const C dr = m[0] - drr, du = m[1] - ur, dv = m[2] - vr;
+      const C rho = C(1) + m[0];
+      ++count;
+      s[0] += (double)m[0];
+      s[1] += (double)(e_rho * dr * dr + e_u * (du * du + dv * dv));
+      s[2] += (double)(C(0.5) * rho * (m[1] * m[1] + m[2] * m[2]));
+      s[3] += (isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]) && rho > C(0)) ? 0.0 : 1.0;
     }
   }
+  s[0] += (double)count;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const double t = block_sum<NT>(s[c], smem);
