@@ -184,10 +184,10 @@ def cpu_threads() -> int:
     return int(v) if v and v.isdigit() else (os.cpu_count() or 1)
 
 
-def time_oracle(seconds: float, warmup: int = 1, fixed_steps: int | None = None):
+def time_oracle(seconds: float, warmup: int = 1, fixed_steps: int | None = None, openmp: bool = True):
     import oracle
     w = oracle_sample_workload()
-    o = oracle.Oracle(w.nx, w.ny, w.tau, openmp=True).init(*w.fields())
+    o = oracle.Oracle(w.nx, w.ny, w.tau, openmp=openmp).init(*w.fields())
     o.step(warmup)
     steps, t0 = 0, time.perf_counter()
     while True:
@@ -197,8 +197,9 @@ def time_oracle(seconds: float, warmup: int = 1, fixed_steps: int | None = None)
         if (fixed_steps is not None and steps >= fixed_steps) or (fixed_steps is None and el >= seconds):
             break
     mlups = w.cells * steps / el / 1e6
-    sample = (f"FP64 C oracle (OpenMP over rows) on the same pulse recipe at {w.nx}x{w.ny} "
-              f"(4 pulses, tau 0.55), {steps} steps after {warmup} warm-up, host cores")
+    how = "OpenMP over rows, all host cores" if openmp else "one thread"
+    sample = (f"FP64 C oracle ({how}) on the same pulse recipe at {w.nx}x{w.ny} "
+              f"(4 pulses, tau 0.55), {steps} steps after {warmup} warm-up")
     return mlups, steps, el, sample
 
 
@@ -515,6 +516,9 @@ def run_ours(args, rank, world, local_rank):
         mlups, steps, el, sample = time_oracle(args.cpu_seconds)
         line["cpu_baseline"] = {"value": mlups, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
                                 "sample": sample, "seconds": el}
+        m1, _, el1, sample1 = time_oracle(args.cpu_seconds / 3, openmp=False)
+        line["cpu_baseline"]["single_thread"] = {"value": m1, "unit": UNIT, "cores": 1, "sample": sample1,
+                                                 "seconds": el1}
     return line
 
 

@@ -31,6 +31,7 @@
 #include "lbm.h"
 #include "lbm_kernels.cuh"
 #include "lbm_staged.cuh"
+#include "lbm_trace.h"
 
 int lbm_internal_fail(int code, const char* msg);
 int lbm_internal_set_edges(lbmk::Nsbc* p, const int32_t types[4], const double uw[8]);
@@ -770,6 +771,7 @@ int lbm_batch_init(lbm_batch_t* b, int32_t k, const double* rho, const double* u
 }
 
 int lbm_batch_step(lbm_batch_t* b, int32_t n) {
+  LBM_TRACE("lbm_batch_step");
   if (!b) return bfail(LBM_EINVAL, "lbm_batch_step: NULL handle");
   if (n < 0) return bfail(LBM_EINVAL, "lbm_batch_step: n=%d < 0", n);
   for (int k = 0; k < b->count; ++k)
@@ -882,6 +884,7 @@ int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_
 
 int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_t* blocks, int32_t* prefetch_rows,
                        int32_t* split, int32_t* tma_tile, double* ms_per_step) {
+  LBM_TRACE("lbm_batch_autotune");
   if (!b) return bfail(LBM_EINVAL, "lbm_batch_autotune: NULL handle");
   for (int k = 0; k < b->count; ++k)
     if (!b->initialised[k]) return bfail(LBM_ESTATE, "lbm_batch_autotune: instance %d not initialised", k);

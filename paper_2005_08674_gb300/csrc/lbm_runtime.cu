@@ -15,6 +15,7 @@
 #include "lbm.h"
 #include "lbm_kernels.cuh"
 #include "lbm_staged.cuh"
+#include "lbm_trace.h"
 
 namespace {
 
@@ -586,6 +587,7 @@ int lbm_init_device(lbm_t* h, const double* d_rho, const double* d_ux, const dou
 }
 
 int lbm_init(lbm_t* h, const double* rho, const double* ux, const double* uy) {
+  LBM_TRACE("lbm_init");
   if (!h || !rho || !ux || !uy) return fail(LBM_EINVAL, "lbm_init: NULL argument");
   int rc = ensure_memory(h);
   if (rc) return rc;
@@ -617,6 +619,7 @@ int lbm_init(lbm_t* h, const double* rho, const double* ux, const double* uy) {
 }
 
 int lbm_step(lbm_t* h, int32_t n) {
+  LBM_TRACE("lbm_step");
   if (!h) return fail(LBM_EINVAL, "lbm_step: NULL handle");
   if (n < 0) return fail(LBM_EINVAL, "lbm_step: n=%d < 0", n);
   if (!h->initialised) return fail(LBM_ESTATE, "lbm_step: call lbm_init first");
@@ -661,6 +664,7 @@ int lbm_get_macros_device(lbm_t* h, double* d_rho, double* d_ux, double* d_uy) {
 }
 
 int lbm_get_macros(lbm_t* h, double* rho, double* ux, double* uy) {
+  LBM_TRACE("lbm_get_macros");
   if (!h || !rho || !ux || !uy) return fail(LBM_EINVAL, "lbm_get_macros: NULL argument");
   if (!h->initialised) return fail(LBM_ESTATE, "lbm_get_macros: call lbm_init first");
   int rc = ensure_streams(h);
@@ -756,6 +760,7 @@ int lbm_load_state(lbm_t* h, const void* host, size_t bytes, int64_t steps) {
 
 int lbm_reduce(lbm_t* h, const double* ref_rho, const double* ref_ux, const double* ref_uy, int32_t ref_pitch,
                double out[4]) {
+  LBM_TRACE("lbm_reduce");
   if (!h || !out) return fail(LBM_EINVAL, "lbm_reduce: NULL argument");
   if (!h->initialised) return fail(LBM_ESTATE, "lbm_reduce: call lbm_init first");
   if (ref_rho && (!ref_ux || !ref_uy || ref_pitch < h->nx))
@@ -843,6 +848,7 @@ int lbm_status(lbm_t* h) {
 }
 
 int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_rows, double* ms_per_step) {
+  LBM_TRACE("lbm_autotune");
   if (!h) return fail(LBM_EINVAL, "lbm_autotune: NULL handle");
   if (!h->initialised) return fail(LBM_ESTATE, "lbm_autotune: call lbm_init first");
   int rc = ensure_streams(h);

@@ -187,31 +187,64 @@ def test_full_size_8192_sampled(lbm, storage, launch):
         sim.set_launch(256, 1, 0)
     sim.step(k)
     sim.status()
-    mac = sim.macros_device()
     centres = [(int(round(c[0])), int(round(c[1]))) for c in w.params["centres"]]
     samples = centres + [(0, 0), (w.nx - 1, 0), (0, w.ny - 1), (w.nx - 1, w.ny - 1),
                          (4097, 0), (0, 333), (w.nx - 1, 5000), (2222, w.ny - 1), (4096, 4096)]
-    rho_all, ux_all, uy_all = w.fields()
+    worst = _sampled_error(sim, w.fields(), w.nx, w.ny, w.tau, k, samples)
+    sim.close()
+    torch.cuda.empty_cache()
+    assert worst <= TOL[storage], worst
+
+
+def _sampled_error(sim, fields, nx, ny, tau, k, samples):
+    """Largest |difference| of (rho, ux, uy) between the device state after k
+    steps and oracle runs on windows around the sample nodes: a window of
+    radius k + 4 evolves like the whole domain, k steps on, wherever its own
+    cut edges cannot reach (information moves one node per step)."""
+    mac = sim.macros_device()
     worst = 0.0
     for (cx, cy) in samples:
-        x0, x1, y0, y1 = _window(w.nx, w.ny, cx, cy, k)
-        sub = [a[y0:y1, x0:x1] for a in (rho_all, ux_all, uy_all)]
-        o = oracle.Oracle(x1 - x0, y1 - y0, w.tau).init(*sub).step(k)
-        ref = o.macros()
+        x0, x1, y0, y1 = _window(nx, ny, cx, cy, k)
+        sub = [np.ascontiguousarray(a[y0:y1, x0:x1]) for a in fields]
+        ref = oracle.Oracle(x1 - x0, y1 - y0, tau).init(*sub).step(k).macros()
         got = mac[:, y0:y1, x0:x1].cpu().numpy()
         # exact region: away from window edges that are not domain edges
         m = k + 2
         ex0 = 0 if x0 == 0 else m
-        ex1 = (x1 - x0) if x1 == w.nx else (x1 - x0) - m
+        ex1 = (x1 - x0) if x1 == nx else (x1 - x0) - m
         ey0 = 0 if y0 == 0 else m
-        ey1 = (y1 - y0) if y1 == w.ny else (y1 - y0) - m
+        ey1 = (y1 - y0) if y1 == ny else (y1 - y0) - m
         assert ex1 > ex0 and ey1 > ey0
         for c in range(3):
             worst = max(worst, float(np.abs(got[c][ey0:ey1, ex0:ex1] - ref[c][ey0:ey1, ex0:ex1]).max()))
-    sim.close()
     del mac
+    return worst
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("nx,ny", [(65536, 4096), (4096, 65536)])
+def test_maximum_extent_sampled(lbm, storage, nx, ny):
+    """The largest extent lbm_create accepts along each axis, 65,536 nodes: a
+    population plane then holds 2^28 nodes, so element offsets into a buffer
+    pass 2^31, and a row holds 16,384 (f32) or 8,192 (f16) vectors.  Autotuned
+    launch, two pulses next to opposite corners; sampled windows against the
+    oracle after k steps."""
+    import torch
+    k, tau = 20, 0.6
+    centres = [(6.0, 5.0), (nx - 7.0, ny - 6.0)]
+    fields = inputs.acoustic_pulse(nx, ny, 1e-3, 4.0, centres)
+    sim = lbm.Simulation(nx, ny, tau, storage=storage)
+    sim.init(*fields)
+    sim.autotune()
+    sim.step(k)
+    sim.status()
+    samples = [(6, 5), (nx - 7, ny - 6), (0, 0), (nx - 1, 0), (0, ny - 1), (nx - 1, ny - 1),
+               (nx // 2, 0), (0, ny // 2), (nx - 1, ny // 2 + 3), (nx // 2 + 5, ny - 1), (nx // 2, ny // 2)]
+    worst = _sampled_error(sim, fields, nx, ny, tau, k, samples)
+    sim.close()
+    del fields
     torch.cuda.empty_cache()
-    assert worst <= TOL[storage], worst
+    assert worst <= {"f32": 1e-6, "f16": 1e-4}[storage], worst
 
 
 PAPER_VORTEX_RATES = (1.4, 1.4, 1.2)  # omega_e, omega_eps, omega_q of the vortex test (Sec. 7)
