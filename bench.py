@@ -498,6 +498,32 @@ def run_ours(args, rank, world, local_rank):
                                "note": f"{lbm.lbm_buffer_bytes(s3.h) / 1e6:.1f} MB per buffer: L2-resident"}
             s3.close()
             del s3
+        # the same pulse recipe at smaller sizes (f32, autotuned): where the
+        # populations start to fit in L2 and launch gaps start to count
+        sizes = {}
+        for n in (1024, 2048, 4096):
+            wn = workload(f"pulse-{n}")
+            s4 = lbm.Simulation(wn.nx, wn.ny, wn.tau, wn.farfield_rho, wn.farfield_u, storage="f32")
+            s4.init(*wn.fields())
+            s4.autotune()
+            s4.step(args.warmup)
+            nsteps = min(args.steps, 400)
+            torch.cuda.synchronize()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(s4.stream)
+            s4.step(nsteps)
+            a1.record(s4.stream)
+            torch.cuda.synchronize()
+            vms = a0.elapsed_time(a1)
+            mlups = world * wn.cells * nsteps / (vms * 1e-3) / 1e6
+            sizes[f"pulse-{n}"] = {"mlups": mlups, "steps": nsteps, "frac_of_72B_roofline": mlups * 1e6 * 72 / 1e9 / peak,
+                                   "step_kernel": f"staged {s4.staged}" if s4.staged else "bulk + NSBC pair",
+                                   "mb_per_buffer": lbm.lbm_buffer_bytes(s4.h) / 1e6}
+            s4.close()
+            del s4
+            torch.cuda.empty_cache()
+        variants["sizes_f32"] = sizes
         # batched: 256 independent instances, one persistent launch per step
         from paper_2005_08674_gb300 import inputs
         ws = inputs.batch_instances()

@@ -189,6 +189,21 @@ int lbm_load_state(lbm_t* h, const void* host, size_t bytes, int64_t steps);
 int lbm_reduce(lbm_t* h, const double* ref_rho, const double* ref_ux, const double* ref_uy,
                int32_t ref_pitch, double out[4]);
 
+/* Bounds-checked build.  liblbm_check.so is this library compiled with
+ * LBM_CHECK (paper_2005_08674_gb300/build.py, build(check=True)): there every
+ * global access of the step kernels (vector and scalar population loads and
+ * stores, the bulk tile copies, the L2 prefetches) and every shared-memory
+ * tile access is first checked against the population buffers and pools the
+ * host allocated or bound (on the current device) and against its slot; an
+ * access that fails is not made (a load yields 0) and is counted instead.
+ * The paper has no counterpart: it is a test instrument standing in for a
+ * device memory checker.  Writes the number of rejected accesses since the
+ * last reset and the first rejected address (top bit set: a shared-memory
+ * offset) to *rejected / *first_address, and clears both if reset != 0;
+ * synchronises the device.  Returns 1 in the checked build, 0 in the ordinary
+ * one (where both outputs are 0), LBM_EINVAL for NULL outputs. */
+int lbm_check_read(int64_t* rejected, uint64_t* first_address, int32_t reset);
+
 /* Launch shape of the bulk stream-collide kernel: threads per block along x
  * (64, 128, 256, 512), rows per block (1, 2, 4, 8), and the distance in rows
  * (0 = off, at most 64) at which each warp asks the bulk-copy engine to

@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "lbm.h"
+#include "lbm_aux.cuh"
 #include "lbm_kernels.cuh"
 #include "lbm_staged.cuh"
 #include "lbm_trace.h"
@@ -560,6 +561,8 @@ int ensure_batch_memory(lbm_batch_t* b) {
     BATCH_CUDA(cudaMalloc(&b->scratch, lbm_batch_scratch_bytes(b)));
     BATCH_CUDA(cudaMemset(b->pool[0], 0, pb));
     BATCH_CUDA(cudaMemset(b->pool[1], 0, pb));
+    lbmk::check_add(b->pool[0], pb);  // bounds-checked build only
+    lbmk::check_add(b->pool[1], pb);
     b->owns_pools = true;
     b->bound = true;
   }
@@ -661,6 +664,10 @@ void lbm_batch_destroy(lbm_batch_t* b) {
   if (!b) return;
   cudaStreamSynchronize(b->stream);
   drop_batch_graphs(b);
+  if (b->bound) {
+    lbmk::check_remove(b->pool[0]);
+    lbmk::check_remove(b->pool[1]);
+  }
   if (b->owns_pools) {
     cudaFree(b->pool[0]);
     cudaFree(b->pool[1]);
@@ -693,9 +700,18 @@ int lbm_batch_bind(lbm_batch_t* b, void* dev_a, void* dev_b, void* dev_scratch) 
   b->pool[0] = dev_a;
   b->pool[1] = dev_b;
   b->scratch = dev_scratch;
+  lbmk::check_add(dev_a, lbm_batch_buffer_bytes(b));  // bounds-checked build only
+  lbmk::check_add(dev_b, lbm_batch_buffer_bytes(b));
   b->bound = true;
   return LBM_OK;
 }
+
+namespace lbmk {
+// This unit's share of lbm_check_read (its kernels have their own table).
+void batch_check_read(unsigned long long* count, unsigned long long* first, bool reset) {
+  check_read(count, first, reset);
+}
+}  // namespace lbmk
 
 int lbm_batch_set_nsbc(lbm_batch_t* b, double gamma, double beta, double kappa, int32_t grad_order) {
   if (!b) return bfail(LBM_EINVAL, "lbm_batch_set_nsbc: NULL handle");

@@ -13,6 +13,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include "lbm_check.cuh"
+
 namespace lbmk {
 
 // ---------------------------------------------------------------------------
@@ -44,11 +46,16 @@ struct Store<double> {
   using C = double;
   static constexpr int V = 2;
   __device__ static void ld(const double* p, C (&o)[V]) {
+    if (!in_bounds(p, 16)) {
+      o[0] = o[1] = 0.0;
+      return;
+    }
     const double2 t = __ldcs(reinterpret_cast<const double2*>(p));
     o[0] = t.x;
     o[1] = t.y;
   }
   __device__ static void st(double* p, const C (&o)[V]) {
+    if (!in_bounds(p, 16)) return;
     __stcs(reinterpret_cast<double2*>(p), make_double2(o[0], o[1]));
   }
   static constexpr double kScale = 1.0;
@@ -59,10 +66,14 @@ struct Store<double> {
     o[1] = t.y;
   }
   __device__ static C ld1s(const double* p) { return *p; }
-  __device__ static C ld1(const double* p) { return __ldcs(p); }
-  __device__ static C ldg1(const double* p) { return __ldg(p); }
-  __device__ static void st1(double* p, C v) { *p = v; }
-  __device__ static void st1r(double* p, C v) { *p = v; }
+  __device__ static C ld1(const double* p) { return in_bounds(p, 8) ? __ldcs(p) : 0.0; }
+  __device__ static C ldg1(const double* p) { return in_bounds(p, 8) ? __ldg(p) : 0.0; }
+  __device__ static void st1(double* p, C v) {
+    if (in_bounds(p, 8)) *p = v;
+  }
+  __device__ static void st1r(double* p, C v) {
+    if (in_bounds(p, 8)) *p = v;
+  }
   __device__ static double cvt(C v) { return v; }
 };
 
@@ -71,6 +82,10 @@ struct Store<float> {
   using C = float;
   static constexpr int V = 4;
   __device__ static void ld(const float* p, C (&o)[V]) {
+    if (!in_bounds(p, 16)) {
+      o[0] = o[1] = o[2] = o[3] = 0.f;
+      return;
+    }
     const float4 t = __ldcs(reinterpret_cast<const float4*>(p));
     o[0] = t.x;
     o[1] = t.y;
@@ -78,6 +93,7 @@ struct Store<float> {
     o[3] = t.w;
   }
   __device__ static void st(float* p, const C (&o)[V]) {
+    if (!in_bounds(p, 16)) return;
     __stcs(reinterpret_cast<float4*>(p), make_float4(o[0], o[1], o[2], o[3]));
   }
   static constexpr float kScale = 1.0f;
@@ -89,10 +105,14 @@ struct Store<float> {
     o[3] = t.w;
   }
   __device__ static C ld1s(const float* p) { return *p; }
-  __device__ static C ld1(const float* p) { return __ldcs(p); }
-  __device__ static C ldg1(const float* p) { return __ldg(p); }
-  __device__ static void st1(float* p, C v) { *p = v; }
-  __device__ static void st1r(float* p, C v) { *p = v; }
+  __device__ static C ld1(const float* p) { return in_bounds(p, 4) ? __ldcs(p) : 0.f; }
+  __device__ static C ldg1(const float* p) { return in_bounds(p, 4) ? __ldg(p) : 0.f; }
+  __device__ static void st1(float* p, C v) {
+    if (in_bounds(p, 4)) *p = v;
+  }
+  __device__ static void st1r(float* p, C v) {
+    if (in_bounds(p, 4)) *p = v;
+  }
   __device__ static float cvt(C v) { return v; }
 };
 
@@ -112,6 +132,11 @@ struct Store<__half> {
   static constexpr int V = 8;
   static constexpr float kScale = kHalfScale;
   __device__ static void ld(const __half* p, C (&o)[V]) {
+    if (!in_bounds(p, 16)) {
+#pragma unroll
+      for (int k = 0; k < V; ++k) o[k] = 0.f;
+      return;
+    }
     const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
     const uint32_t w[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
@@ -124,6 +149,7 @@ struct Store<__half> {
     }
   }
   __device__ static void st(__half* p, const C (&o)[V]) {
+    if (!in_bounds(p, 16)) return;
     uint32_t w[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -158,16 +184,23 @@ struct Store<__half> {
     o[3] = fb.y;
   }
   __device__ static void stp(__half* p, const C (&o)[4]) {
+    if (!in_bounds(p, 8)) return;
     const __half2 a = __floats2half2_rn(o[0], o[1]), b = __floats2half2_rn(o[2], o[3]);
     uint2 t;
     memcpy(&t.x, &a, 4);
     memcpy(&t.y, &b, 4);
     __stcs(reinterpret_cast<uint2*>(p), t);
   }
-  __device__ static C ld1(const __half* p) { return __half2float(*p); }
-  __device__ static void st1r(__half* p, C v) { *p = __float2half_rn(v); }
-  __device__ static C ldg1(const __half* p) { return __half2float(__ldg(p)) * kHalfUnscale; }
-  __device__ static void st1(__half* p, C v) { *p = __float2half_rn(v * kHalfScale); }
+  __device__ static C ld1(const __half* p) { return in_bounds(p, 2) ? __half2float(*p) : 0.f; }
+  __device__ static void st1r(__half* p, C v) {
+    if (in_bounds(p, 2)) *p = __float2half_rn(v);
+  }
+  __device__ static C ldg1(const __half* p) {
+    return in_bounds(p, 2) ? __half2float(__ldg(p)) * kHalfUnscale : 0.f;
+  }
+  __device__ static void st1(__half* p, C v) {
+    if (in_bounds(p, 2)) *p = __float2half_rn(v * kHalfScale);
+  }
   __device__ static __half cvt(C v) { return __float2half_rn(v * kHalfScale); }
 };
 
@@ -176,6 +209,11 @@ struct Store<__nv_bfloat16> {
   using C = float;
   static constexpr int V = 8;
   __device__ static void ld(const __nv_bfloat16* p, C (&o)[V]) {
+    if (!in_bounds(p, 16)) {
+#pragma unroll
+      for (int k = 0; k < V; ++k) o[k] = 0.f;
+      return;
+    }
     const uint4 t = __ldcs(reinterpret_cast<const uint4*>(p));
     const uint32_t w[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
@@ -188,6 +226,7 @@ struct Store<__nv_bfloat16> {
     }
   }
   __device__ static void st(__nv_bfloat16* p, const C (&o)[V]) {
+    if (!in_bounds(p, 16)) return;
     uint32_t w[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -222,22 +261,28 @@ struct Store<__nv_bfloat16> {
     o[3] = fb.y;
   }
   __device__ static void stp(__nv_bfloat16* p, const C (&o)[4]) {
+    if (!in_bounds(p, 8)) return;
     const __nv_bfloat162 a = __floats2bfloat162_rn(o[0], o[1]), b = __floats2bfloat162_rn(o[2], o[3]);
     uint2 t;
     memcpy(&t.x, &a, 4);
     memcpy(&t.y, &b, 4);
     __stcs(reinterpret_cast<uint2*>(p), t);
   }
-  __device__ static C ld1(const __nv_bfloat16* p) { return __bfloat162float(*p); }
-  __device__ static C ldg1(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
-  __device__ static void st1(__nv_bfloat16* p, C v) { *p = __float2bfloat16_rn(v); }
-  __device__ static void st1r(__nv_bfloat16* p, C v) { *p = __float2bfloat16_rn(v); }
+  __device__ static C ld1(const __nv_bfloat16* p) { return in_bounds(p, 2) ? __bfloat162float(*p) : 0.f; }
+  __device__ static C ldg1(const __nv_bfloat16* p) { return in_bounds(p, 2) ? __bfloat162float(__ldg(p)) : 0.f; }
+  __device__ static void st1(__nv_bfloat16* p, C v) {
+    if (in_bounds(p, 2)) *p = __float2bfloat16_rn(v);
+  }
+  __device__ static void st1r(__nv_bfloat16* p, C v) {
+    if (in_bounds(p, 2)) *p = __float2bfloat16_rn(v);
+  }
   __device__ static __nv_bfloat16 cvt(C v) { return __float2bfloat16_rn(v); }
 };
 
 // Bulk-copy-engine prefetch of [p, p + bytes) into L2 (16-byte aligned,
 // bytes a multiple of 16); no registers or shared memory are tied up.
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  if (!in_bounds(p, bytes)) return;
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "lbm.h"
+#include "lbm_aux.cuh"
 #include "lbm_kernels.cuh"
 #include "lbm_staged.cuh"
 #include "lbm_trace.h"
@@ -136,6 +137,8 @@ int ensure_memory(lbm_t* h) {
   LBM_CUDA(cudaMalloc(&h->scratch, sb));
   LBM_CUDA(cudaMemset(h->buf[0], 0, bb));
   LBM_CUDA(cudaMemset(h->buf[1], 0, bb));
+  lbmk::check_add(h->buf[0], bb);  // bounds-checked build only
+  lbmk::check_add(h->buf[1], bb);
   h->owns_memory = true;
   h->bound = true;
   return LBM_OK;
@@ -452,6 +455,10 @@ void lbm_destroy(lbm_t* h) {
   if (!h) return;
   if (h->stream || h->cap) cudaStreamSynchronize(h->stream);
   drop_graphs(h);
+  if (h->bound) {
+    lbmk::check_remove(h->buf[0]);
+    lbmk::check_remove(h->buf[1]);
+  }
   if (h->owns_memory) {
     cudaFree(h->buf[0]);
     cudaFree(h->buf[1]);
@@ -568,6 +575,8 @@ int lbm_bind(lbm_t* h, void* dev_a, void* dev_b, void* dev_scratch) {
   h->buf[0] = dev_a;
   h->buf[1] = dev_b;
   h->scratch = dev_scratch;
+  lbmk::check_add(dev_a, lbm_buffer_bytes(h));  // bounds-checked build only
+  lbmk::check_add(dev_b, lbm_buffer_bytes(h));
   h->bound = true;
   h->owns_memory = false;
   return LBM_OK;
@@ -655,6 +664,20 @@ int lbm_step(lbm_t* h, int32_t n) {
 }
 
 int64_t lbm_steps_done(const lbm_t* h) { return h ? h->steps : -1; }
+
+namespace lbmk {
+void batch_check_read(unsigned long long* count, unsigned long long* first, bool reset);  // lbm_batch.cu
+}
+
+int lbm_check_read(int64_t* rejected, uint64_t* first_address, int32_t reset) {
+  if (!rejected || !first_address) return fail(LBM_EINVAL, "lbm_check_read: NULL argument");
+  unsigned long long c1 = 0, f1 = 0, c2 = 0, f2 = 0;
+  lbmk::check_read(&c1, &f1, reset != 0);
+  lbmk::batch_check_read(&c2, &f2, reset != 0);
+  *rejected = (int64_t)(c1 + c2);
+  *first_address = c1 ? f1 : f2;
+  return lbmk::kChecked ? 1 : 0;
+}
 
 int lbm_get_macros_device(lbm_t* h, double* d_rho, double* d_ux, double* d_uy) {
   if (!h || !d_rho || !d_ux || !d_uy) return fail(LBM_EINVAL, "lbm_get_macros_device: NULL argument");

@@ -107,6 +107,7 @@ __device__ __forceinline__ void issue_tile(const T* __restrict__ A, const InstDe
   constexpr int SLOT = (TILE + 2) * 16;
   const long long plane_elems = (long long)d.ny * d.pitch;
   long long lo[9], hi[9];
+  bool ok[9];
   uint32_t total = 0;
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
@@ -114,14 +115,20 @@ __device__ __forceinline__ void issue_tile(const T* __restrict__ A, const InstDe
     lo[i] = start < 0 ? 0 : start;
     const long long end = start + (long long)(w.z + 2) * V;
     hi[i] = end > plane_elems ? plane_elems : end;
-    total += (uint32_t)((hi[i] - lo[i]) * (long long)sizeof(T));
+    const long long bytes = (hi[i] - lo[i]) * (long long)sizeof(T);
+    // (checked build: a copy whose source or slot range fails is not issued
+    // and not counted in the barrier's byte total)
+    ok[i] = in_bounds(A + d.off + i * d.plane + lo[i], (unsigned long long)bytes) &&
+            in_slot((lo[i] - start) * (long long)sizeof(T), bytes, SLOT);
+    if (ok[i]) total += (uint32_t)bytes;
   }
   mbar_expect_tx(bar, total);
 #pragma unroll
   for (int i = 0; i < 9; ++i) {
     const long long start = (long long)(1 + pull_row_shift(i)) * d.pitch + (long long)(w.y - 1) * V;
-    bulk_copy_g2s(slot + i * SLOT + (lo[i] - start) * (long long)sizeof(T), A + d.off + i * d.plane + lo[i],
-                  (uint32_t)((hi[i] - lo[i]) * (long long)sizeof(T)), bar);
+    if (ok[i])
+      bulk_copy_g2s(slot + i * SLOT + (lo[i] - start) * (long long)sizeof(T), A + d.off + i * d.plane + lo[i],
+                    (uint32_t)((hi[i] - lo[i]) * (long long)sizeof(T)), bar);
   }
 }
 
@@ -145,6 +152,10 @@ __device__ __forceinline__ void collide_tile(const unsigned char* sl, const Inst
     const int j = w.y + u;
     const int y = 1 + row_of_vector(j, d);
     const int x0 = (j - (y - 1) * nvec) * V + part * CPT;
+    // elements (u + 1) V + part CPT - 1 .. + CPT of every plane's slot
+    if (!in_slot(((long long)(u + 1) * V + part * CPT - 1) * (long long)sizeof(T), (CPT + 2) * (long long)sizeof(T),
+                 SLOT))
+      continue;
     C v[9][CPT], lf[9], rt[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {

@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "liblbm.so")
+# LBM_CHECKED=1 loads the bounds-checked build (build(check=True)) instead
+CHECKED = os.environ.get("LBM_CHECKED") == "1"
+LIB_PATH = os.path.join(_HERE, "liblbm_check.so" if CHECKED else "liblbm.so")
 
 LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EUNSTABLE, LBM_ESTATE, LBM_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 LBM_F64, LBM_F32, LBM_F16, LBM_BF16 = 0, 1, 2, 3
@@ -86,6 +88,7 @@ _SIGS = {
     "lbm_batch_status": (ctypes.c_int, [_vp]),
     "lbm_wait_selftest": (ctypes.c_int, [ctypes.c_int64]),
     "lbm_last_error": (ctypes.c_char_p, []),
+    "lbm_check_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_uint64), _i32]),
 }
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_L, _name)
@@ -103,6 +106,15 @@ def _check(rc: int) -> int:
     if rc != LBM_OK:
         raise LbmError(rc, lbm_last_error())
     return rc
+
+
+def lbm_check_read(reset: bool = False):
+    """(checked build?, rejected accesses, first rejected address) -- see lbm.h."""
+    n, a = ctypes.c_int64(0), ctypes.c_uint64(0)
+    rc = _L.lbm_check_read(ctypes.byref(n), ctypes.byref(a), int(reset))
+    if rc < 0:
+        raise LbmError(rc, lbm_last_error())
+    return bool(rc), int(n.value), int(a.value)
 
 
 def _host(a) -> np.ndarray:

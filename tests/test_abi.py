@@ -77,3 +77,11 @@ def test_host_side_argument_checks(lib_path):
     finally:
         lbm.lbm_destroy(h)
     lbm.lbm_destroy(None)
+
+
+def test_ordinary_build_reports_no_checker(lib_path):
+    """lbm_check_read exists in every build; the ordinary one has no checker."""
+    from paper_2005_08674_gb300 import lbm
+    if lbm.CHECKED:
+        pytest.skip("the bounds-checked library is loaded")
+    assert lbm.lbm_check_read() == (False, 0, 0)
