@@ -48,8 +48,8 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--launch", default="",
-                   help="'threads_x,rows[,prefetch]' (bulk + NSBC kernel pair) or 'staged3' / 'staged4' "
-                        "instead of autotuning")
+                   help="'threads_x,rows[,prefetch]' (bulk + NSBC kernel pair), 'fused[:threads_x,rows,prefetch]' "
+                        "(both in one launch) or 'staged3' / 'staged4' instead of autotuning")
     p.add_argument("--batched-only", action="store_true", help="time only the batched workload")
     p.add_argument("--batch-launch", default="", help="batched launch 'threads_x,rows,blocks,prefetch,split'")
     return p.parse_args()
@@ -155,6 +155,8 @@ def step_kernel(sim, nx, ny):
     if sim.staged:
         return ("batch_ws_kernel (staged step: interior tiles by bulk copies + NSBC chunks, "
                 f"{sim.staged} stages)", "staged_step_traffic", nx * ny)
+    if sim.fused:
+        return "fused_step_kernel (bulk rows + NSBC quads in one launch)", "fused_step_traffic", nx * ny
     return "bulk_kernel (fused pull-stream + BGK collide)", "bulk_kernel_traffic", (nx - 2) * (ny - 2)
 
 
@@ -342,6 +344,11 @@ def run_ours(args, rank, world, local_rank):
     if args.launch.startswith("staged"):
         bx, rows, pf = 0, 0, 0
         sim.set_staged(int(args.launch[len("staged"):] or 3))
+    elif args.launch.startswith("fused"):
+        parts = [int(v) for v in args.launch[len("fused"):].lstrip(":").split(",") if v] or [128, 1, 0]
+        bx, rows, pf = (parts + [0, 0])[:3]
+        sim.set_launch(bx, rows, pf)
+        sim.set_fused(True)
     elif args.launch:
         parts = [int(v) for v in args.launch.split(",")]
         bx, rows, pf = (parts + [0])[:3]
@@ -398,7 +405,7 @@ def run_ours(args, rank, world, local_rank):
             "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
             "config": {"workload": describe(w, args.storage), "nx": w.nx, "ny": w.ny,
                        "step_kernel": {"staged_stages": sim.staged} if sim.staged else
-                       {"bulk_threads_x": bx, "bulk_rows": rows, "prefetch_rows": pf},
+                       {"bulk_threads_x": bx, "bulk_rows": rows, "prefetch_rows": pf, "fused": sim.fused},
                        "l2": f"inputs larger than L2: {lbm.lbm_buffer_bytes(sim.h) / 1e9:.2f} GB per population buffer",
                        "parallelism": "replicas" if world > 1 else "single-gpu",
                        "stable": bool(stable)},
@@ -409,7 +416,7 @@ def run_ours(args, rank, world, local_rank):
                          "avg_launch_ms": bulk_avg, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "nsbc_avg_launch_ms": nsbc_avg if nn else None,
                          "timing": f"per-launch CUDA events over {kprof} steps after the timed region"},
-            "gpu_launches": (1 if sim.staged else 2) * args.steps,
+            "gpu_launches": (1 if sim.staged or sim.fused else 2) * args.steps,
             "clocks": clk,
         }
 
@@ -518,7 +525,8 @@ def run_ours(args, rank, world, local_rank):
             vms = a0.elapsed_time(a1)
             mlups = world * wn.cells * nsteps / (vms * 1e-3) / 1e6
             sizes[f"pulse-{n}"] = {"mlups": mlups, "steps": nsteps, "frac_of_72B_roofline": mlups * 1e6 * 72 / 1e9 / peak,
-                                   "step_kernel": f"staged {s4.staged}" if s4.staged else "bulk + NSBC pair",
+                                   "step_kernel": (f"staged {s4.staged}" if s4.staged else
+                                                   "fused" if s4.fused else "bulk + NSBC pair"),
                                    "mb_per_buffer": lbm.lbm_buffer_bytes(s4.h) / 1e6}
             s4.close()
             del s4

@@ -229,17 +229,28 @@ int lbm_set_launch(lbm_t* h, int32_t threads_x, int32_t rows, int32_t prefetch_r
 int lbm_set_staged(lbm_t* h, int32_t stages);
 /* The current stages setting (0 = kernel pair), or LBM_EINVAL for NULL. */
 int32_t lbm_get_staged(const lbm_t* h);
+/* One launch per step with the bulk + NSBC kernel pair's work: the bulk grid
+ * of the current lbm_set_launch shape and the NSBC quads (Sec. 5) in a
+ * single kernel, perimeter blocks first.  For domains small enough that the
+ * step is bound by launch gaps rather than by HBM.  Bit-identical to the
+ * pair.  enable != 0 turns it on (and the staged kernel off); lbm_set_launch
+ * and lbm_set_staged turn it off.  lbm_autotune also times it against the
+ * pair for every shape.  lbm_get_fused: 1 if on, 0 if off, LBM_EINVAL for a
+ * NULL handle. */
+int lbm_set_fused(lbm_t* h, int32_t enable);
+int32_t lbm_get_fused(const lbm_t* h);
 /* LBM_ETIMEOUT if a bounded wait of the staged kernel gave up (the state is
  * then not valid), else LBM_OK; synchronises the stream. */
 int lbm_status(lbm_t* h);
 
-/* Time every compiled bulk launch shape and prefetch distance, and the
- * staged kernel with 3 and 4 stages, on this handle's own buffers (a few
- * whole steps each, CUDA events on the stream) and keep the fastest; the
- * state is restored afterwards (through a temporary device copy from
- * cudaMallocAsync).  Writes the bulk shape, and the time per step in
- * milliseconds of the winner, to the optional outputs; lbm_get_staged tells
- * whether the staged kernel won. */
+/* Time every compiled bulk launch shape and prefetch distance (as the
+ * kernel pair and as the fused one-launch step), and the staged kernel with
+ * 3 and 4 stages, on this handle's own buffers (a few whole steps each,
+ * CUDA events on the stream) and keep the fastest; the state is restored
+ * afterwards (through a temporary device copy from cudaMallocAsync).  Writes
+ * the bulk shape, and the time per step in milliseconds of the winner, to
+ * the optional outputs; lbm_get_staged / lbm_get_fused tell whether the
+ * staged or the fused form won. */
 int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_rows, double* ms_per_step);
 
 /* Allocation-free form of lbm_reduce, for callers that cannot allocate

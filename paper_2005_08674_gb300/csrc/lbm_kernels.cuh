@@ -6,6 +6,7 @@
 //                  or MRT, Eq. mrt_lbe)
 //                  over interior nodes, 16-byte vector loads/stores along x,
 //                  x-1 / x+1 neighbours exchanged with warp shuffles.
+//   fused_step_kernel : both in one launch (perimeter blocks first).
 //   nsbc_kernel  : the boundary of Sec. 5 on every edge and corner node:
 //                  gradient prediction (Eq. nes_2) with one-sided differences
 //                  whose points are loaded by neighbouring lanes and gathered
@@ -322,6 +323,33 @@ __device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict
   const int n[1] = {node};
   const bool ok[1] = {true};
   nsbc_nodes<T, MODEL, 1>(A, B, g, p, rates, n, ok, q);
+}
+
+// One launch for the whole step (the "fused" form, for domains small enough
+// that launch gaps dominate): the first n_edge blocks take the perimeter,
+// one node per quad of lanes as in nsbc_kernel; the others are the blocks of
+// bulk_kernel's (threads_x, rows) grid, numbered row-major with nbx blocks
+// along x.  Same device functions, so the same bits as the kernel pair.
+template <typename T, int BX, int MODEL>
+__global__ void __launch_bounds__(BX) fused_step_kernel(const T* __restrict__ A, T* __restrict__ B, Geom g, Nsbc p,
+                                                        Rates<typename Store<T>::C> rates, int rows, int pf, int n_edge,
+                                                        int nbx) {
+  constexpr int V = Store<T>::V;
+  if ((int)blockIdx.x < n_edge) {
+    const int t = blockIdx.x * BX + threadIdx.x;
+    const int node = t >> 2, q = t & 3;
+    if (node >= 2 * g.nx + 2 * (g.ny - 2)) return;  // a quad leaves together
+    nsbc_node<T, MODEL>(A, B, g, p, rates, node, q);
+    return;
+  }
+  const int k = (int)blockIdx.x - n_edge;
+  const int bx = k % nbx, by = k / nbx;
+  const int lane = threadIdx.x & 31;
+  const int x0 = (bx * BX + threadIdx.x) * V;
+  const int y_begin = 1 + by * rows;
+  const int y_end = min(y_begin + rows, g.ny - 1);
+  const unsigned pf_bytes = warp_segment_bytes<T>(g, x0 - lane * V);
+  for (int y = y_begin; y < y_end; ++y) bulk_row<T, MODEL>(A, B, g, rates, y, x0, lane, pf, pf_bytes);
 }
 
 template <typename T, int MODEL>

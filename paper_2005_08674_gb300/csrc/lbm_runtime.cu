@@ -92,6 +92,9 @@ struct lbm {
   // lbm_staged.cuh over this domain's one-instance work list; 0 = off, else
   // the number of tile stages
   int staged = 0;
+  // fused step kernel (lbm_set_fused): the bulk grid of the current shape and
+  // the NSBC quads in one launch per step
+  bool fused = false;
   int4* d_items = nullptr;
   lbmk::InstDev* d_inst = nullptr;
   int* d_sched = nullptr;  // work counter, blocks done, give-up flag
@@ -202,6 +205,33 @@ void launch_nsbc(const lbm_t* h, const void* a, void* b, cudaStream_t s) {
   else
     lbmk::nsbc_kernel<T, 0><<<blocks, kNsbcThreads, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
                                                             h->nsbc, rates<C>(h));
+}
+
+template <typename T, int BX>
+void launch_fused_bx(const lbm_t* h, const void* a, void* b, int rows, cudaStream_t s) {
+  using C = typename lbmk::Store<T>::C;
+  constexpr int V = lbmk::Store<T>::V;
+  const int nvec = (h->nx + V - 1) / V;
+  const int nbx = (nvec + BX - 1) / BX, nby = (h->ny - 2 + rows - 1) / rows;
+  const long long perim = 2LL * h->nx + 2LL * (h->ny - 2);
+  const int n_edge = (int)((perim * 4 + BX - 1) / BX);
+  const int grid = n_edge + nbx * nby;
+  if (h->collision == 1)
+    lbmk::fused_step_kernel<T, BX, 1><<<grid, BX, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
+                                                         h->nsbc, rates<C>(h), rows, h->pf, n_edge, nbx);
+  else
+    lbmk::fused_step_kernel<T, BX, 0><<<grid, BX, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
+                                                         h->nsbc, rates<C>(h), rows, h->pf, n_edge, nbx);
+}
+
+template <typename T>
+void launch_fused(const lbm_t* h, const void* a, void* b, cudaStream_t s) {
+  switch (h->bx) {
+    case 64: launch_fused_bx<T, 64>(h, a, b, h->rows, s); break;
+    case 256: launch_fused_bx<T, 256>(h, a, b, h->rows, s); break;
+    case 512: launch_fused_bx<T, 512>(h, a, b, h->rows, s); break;
+    default: launch_fused_bx<T, 128>(h, a, b, h->rows, s); break;
+  }
 }
 
 // ---- staged step kernel --------------------------------------------------
@@ -334,6 +364,10 @@ void enqueue_step(const lbm_t* h, int from, cudaStream_t s, bool fork) {
       launch_staged<T>(h, a, b, s);
       return;
     }
+    if (h->fused) {
+      launch_fused<T>(h, a, b, s);
+      return;
+    }
     if (fork) {
       cudaEventRecord(h->ev_fork, s);
       cudaStreamWaitEvent(h->side, h->ev_fork, 0);
@@ -380,18 +414,21 @@ int enqueue_step_profiled(lbm_t* h, int from) {
   const void* a = h->buf[from];
   void* b = h->buf[1 - from];
   cudaEvent_t e[4];
+  const bool one = h->staged || h->fused;  // one launch per step
   int rc = profiled_pair(h, 0, e);
-  if (!rc && !h->staged) rc = profiled_pair(h, 1, e + 2);
+  if (!rc && !one) rc = profiled_pair(h, 1, e + 2);
   if (rc) return rc;
   dispatch(h->storage, [&](auto tag) {
     using T = decltype(tag);
     cudaEventRecord(e[0], h->stream);
     if (h->staged)
       launch_staged<T>(h, a, b, h->stream);
+    else if (h->fused)
+      launch_fused<T>(h, a, b, h->stream);
     else
       launch_bulk<T>(h, a, b, h->bx, h->rows, h->stream);
     cudaEventRecord(e[1], h->stream);
-    if (!h->staged) {
+    if (!one) {
       cudaEventRecord(e[2], h->stream);
       launch_nsbc<T>(h, a, b, h->stream);
       cudaEventRecord(e[3], h->stream);
@@ -845,15 +882,27 @@ int lbm_set_launch(lbm_t* h, int32_t threads_x, int32_t rows, int32_t prefetch_r
   h->rows = rows;
   h->pf = prefetch_rows;
   h->staged = 0;
+  h->fused = false;
   drop_graphs(h);
   return LBM_OK;
 }
+
+int lbm_set_fused(lbm_t* h, int32_t enable) {
+  if (!h) return fail(LBM_EINVAL, "lbm_set_fused: NULL handle");
+  h->fused = enable != 0;
+  if (h->fused) h->staged = 0;
+  drop_graphs(h);
+  return LBM_OK;
+}
+
+int32_t lbm_get_fused(const lbm_t* h) { return h ? (h->fused ? 1 : 0) : LBM_EINVAL; }
 
 int lbm_set_staged(lbm_t* h, int32_t stages) {
   if (!h) return fail(LBM_EINVAL, "lbm_set_staged: NULL handle");
   if (stages != 0 && stages != 3 && stages != 4)
     return fail(LBM_EINVAL, "lbm_set_staged: stages=%d (0 = off, 3 or 4)", stages);
   h->staged = stages;
+  if (stages) h->fused = false;
   drop_graphs(h);
   return LBM_OK;
 }
@@ -888,6 +937,7 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
   const int reps = (int)std::max<long long>(4, std::min<long long>(64, (1LL << 28) / std::max(cells, 1LL)));
   float best = 1e30f;
   int best_bx = h->bx, best_rows = h->rows, best_pf = h->pf, best_staged = h->staged;
+  bool best_fused = h->fused;
   // whole steps as the graphs run them (NSBC kernel on the forked branch)
   auto time_steps = [&]() -> float {
     for (int k = 0; k < 2; ++k) enqueue_step(h, k & 1, h->stream, true);
@@ -902,20 +952,24 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
   h->staged = 0;
   for (int bx : kShapesBX)
     for (int r : kShapesRows)
-      for (int pf : kPrefetchRows) {
-        if (r > 1 && (h->ny - 2) / r < 152) continue;  // too few blocks to fill the GPU
-        h->bx = bx;
-        h->rows = r;
-        h->pf = pf;
-        const float ms = time_steps();
-        if (ms < best) {
-          best = ms;
-          best_bx = bx;
-          best_rows = r;
-          best_pf = pf;
-          best_staged = 0;
+      for (int pf : kPrefetchRows)
+        for (bool fz : {false, true}) {  // the kernel pair, or both in one launch
+          if (r > 1 && (h->ny - 2) / r < 152) continue;  // too few blocks to fill the GPU
+          h->bx = bx;
+          h->rows = r;
+          h->pf = pf;
+          h->fused = fz;
+          const float ms = time_steps();
+          if (ms < best) {
+            best = ms;
+            best_bx = bx;
+            best_rows = r;
+            best_pf = pf;
+            best_staged = 0;
+            best_fused = fz;
+          }
         }
-      }
+  h->fused = false;
   // the staged step kernel (producer/consumer, 3 or 4 tile stages)
   for (int st : {3, 4}) {
     h->staged = st;
@@ -925,6 +979,7 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
     if (ms < best) {
       best = ms;
       best_staged = st;
+      best_fused = false;
     }
   }
   rc = check_launch();
@@ -932,6 +987,7 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
   h->rows = best_rows;
   h->pf = best_pf;
   h->staged = best_staged;
+  h->fused = best_fused && !best_staged;
   drop_graphs(h);
   LBM_CUDA(cudaMemcpyAsync(h->buf[h->cur], backup, bb, cudaMemcpyDeviceToDevice, h->stream));
   LBM_CUDA(cudaFreeAsync(backup, h->stream));

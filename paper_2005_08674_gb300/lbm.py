@@ -65,6 +65,8 @@ _SIGS = {
     "lbm_autotune": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _dp]),
     "lbm_set_staged": (ctypes.c_int, [_vp, _i32]),
     "lbm_get_staged": (ctypes.c_int32, [_vp]),
+    "lbm_set_fused": (ctypes.c_int, [_vp, _i32]),
+    "lbm_get_fused": (ctypes.c_int32, [_vp]),
     "lbm_status": (ctypes.c_int, [_vp]),
     "lbm_reduce_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _dp]),
     "lbm_profile": (ctypes.c_int, [_vp, _i32]),
@@ -295,6 +297,14 @@ def lbm_get_staged(h) -> int:
     return int(_L.lbm_get_staged(h))
 
 
+def lbm_set_fused(h, enable: bool):
+    return _check(_L.lbm_set_fused(h, int(bool(enable))))
+
+
+def lbm_get_fused(h) -> int:
+    return int(_L.lbm_get_fused(h))
+
+
 def lbm_status(h):
     return _check(_L.lbm_status(h))
 
@@ -427,6 +437,15 @@ class Simulation:
     @property
     def staged(self) -> int:
         return lbm_get_staged(self.h)
+
+    def set_fused(self, enable=True):
+        """Bulk grid of the current shape and NSBC quads in one launch per step."""
+        lbm_set_fused(self.h, enable)
+        return self
+
+    @property
+    def fused(self) -> bool:
+        return lbm_get_fused(self.h) == 1
 
     def status(self):
         """Raises LbmError(LBM_ETIMEOUT) if a bounded device-side wait gave up."""

@@ -1,12 +1,13 @@
 """Driver for the bounds-checked library (run in a child process with
 LBM_CHECKED=1 by test_checked_build_gpu.py; not collected by pytest).
 
-Steps every launch form of the single-domain and batched paths on small,
-odd-sized domains (all storages, BGK and MRT, first- and second-order NSBC
-differences, periodic and velocity edges) and prints one JSON line: whether
-the loaded library is the checked build, how many accesses its checker
-rejected, the first rejected address, and the largest f64 difference from
-the oracle (the checked build must still compute the same results)."""
+Steps every launch form of the single-domain (kernel pair, fused, staged)
+and batched paths on small, odd-sized domains (all storages, BGK and MRT,
+first- and second-order NSBC differences, periodic and velocity edges) and
+prints one JSON line: whether the loaded library is the checked build, how
+many accesses its checker rejected, the first rejected address, and the
+largest f64 difference from the oracle (the checked build must still compute
+the same results)."""
 import json
 import os
 import sys
@@ -23,7 +24,7 @@ from paper_2005_08674_gb300 import inputs, lbm  # noqa: E402
 STEPS = 21
 SIZES = [(3, 3), (5, 7), (33, 17), (65, 4), (517, 4), (4, 129), (130, 66)]
 LAUNCHES = [("pair", (64, 1, 0)), ("pair", (128, 2, 1)), ("pair", (256, 1, 3)), ("pair", (512, 8, 64)),
-            ("staged", 3), ("staged", 4)]
+            ("fused", (128, 1, 0)), ("fused", (64, 4, 3)), ("staged", 3), ("staged", 4)]
 BATCH_LAUNCHES = [(128, 1, -1, 0, 0, 0), (64, 1, 0, 0, 0, 0), (128, 2, 0, 1, 1, 0), (256, 4, 152, 0, 0, 0),
                   (64, 4, 7, 64, 1, 0), (128, 1, 0, 0, 1, 128), (128, 1, 0, 0, 1, 256), (256, 1, 0, 0, 1, 256),
                   (128, 4, -1, 1, 0, 0), (256, 1, -1, 0, 1, 0), (128, 3, 0, 0, 0, 128), (128, 4, 0, 2, 0, 128),
@@ -51,6 +52,7 @@ def main():
                             s.set_staged(arg)
                         else:
                             s.set_launch(*arg)
+                            s.set_fused(kind == "fused")
                         got = s.step(STEPS).macros()
                         s.reduce(allow_unstable=True)
                     if storage == "f64" and i == 0:
