@@ -13,11 +13,14 @@ namespace lbmk {
 // A2 if not null) from double fields [ny][nx]; padding columns are zeroed.
 // The equilibrium is formed in double and rounded once to the storage type
 // (forming it in float measurably changed the 16-bit runs' reflection
-// figures).  Grid: x over the pitch, blockIdx.y striding over the rows.
+// figures).  The stored value is the deviation from the far-field
+// equilibrium (Shift).  Grid: x over the pitch, blockIdx.y striding over the
+// rows.
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void init_kernel(T* __restrict__ A, T* __restrict__ A2, Geom g, const double* __restrict__ rho,
-                            const double* __restrict__ ux, const double* __restrict__ uy, int y0, int y1) {
+__global__ void init_kernel(T* __restrict__ A, T* __restrict__ A2, Geom g, Shift<double> zd,
+                            const double* __restrict__ rho, const double* __restrict__ ux,
+                            const double* __restrict__ uy, int y0, int y1) {
   using S = Store<T>;
   using C = typename S::C;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -29,6 +32,8 @@ __global__ void init_kernel(T* __restrict__ A, T* __restrict__ A2, Geom g, const
     if (x < g.nx) {
       const long long k = (long long)y * g.nx + x;
       equilibrium(rho[k] - 1.0, ux[k], uy[k], e);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) e[i] = sub_rn(e[i], zd.sh[i]);
     }
     const long long idx = (long long)y * g.pitch + x;
 #pragma unroll
@@ -42,13 +47,13 @@ __global__ void init_kernel(T* __restrict__ A, T* __restrict__ A2, Geom g, const
 
 // Macroscopic fields (double) of rows [y0, y1) of the stored state; same grid.
 template <typename T>
-__global__ void macros_kernel(const T* __restrict__ A, Geom g, double* __restrict__ rho, double* __restrict__ ux,
-                              double* __restrict__ uy, int y0, int y1) {
+__global__ void macros_kernel(const T* __restrict__ A, Geom g, Shift<typename Store<T>::C> z, double* __restrict__ rho,
+                              double* __restrict__ ux, double* __restrict__ uy, int y0, int y1) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= g.nx) return;
   for (int y = y0 + (int)blockIdx.y; y < y1; y += (int)gridDim.y) {
     typename Store<T>::C m[3];
-    node_dmoments(A, g, x, y, m);
+    node_dmoments(A, g, x, y, z, m);
     const long long k = (long long)y * g.nx + x;
     rho[k] = 1.0 + (double)m[0];
     ux[k] = (double)m[1];
@@ -63,10 +68,10 @@ inline dim3 rows_grid(int width, int rows) {
 
 // One population plane <-> absolute double field [ny][nx].
 template <typename T>
-__global__ void plane_to_f64(const T* __restrict__ A, Geom g, int i, double* __restrict__ out) {
+__global__ void plane_to_f64(const T* __restrict__ A, Geom g, Shift<double> zd, int i, double* __restrict__ out) {
   using S = Store<T>;
   const long long n = (long long)g.ny * g.nx;
-  const double w = wt<double>(i);
+  const double w = wt<double>(i) + zd.sh[i];
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(k / g.nx), x = (int)(k % g.nx);
     out[k] = (double)S::ldg1(A + i * g.plane + (long long)y * g.pitch + x) + w;
@@ -74,10 +79,10 @@ __global__ void plane_to_f64(const T* __restrict__ A, Geom g, int i, double* __r
 }
 
 template <typename T>
-__global__ void f64_to_plane(T* __restrict__ A, Geom g, int i, const double* __restrict__ in) {
+__global__ void f64_to_plane(T* __restrict__ A, Geom g, Shift<double> zd, int i, const double* __restrict__ in) {
   using S = Store<T>;
   const long long n = (long long)g.ny * g.pitch;
-  const double w = wt<double>(i);
+  const double w = wt<double>(i) + zd.sh[i];
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
        idx += (long long)gridDim.x * blockDim.x) {
     const int y = (int)(idx / g.pitch), x = (int)(idx % g.pitch);
@@ -131,8 +136,9 @@ struct KahanSum {
 // against the reference field (or the far field), [2] kinetic energy sum
 // rho |u|^2 / 2, [3] nodes with a non-finite or non-positive density.
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) reduce_kernel(const T* __restrict__ A, Geom g, RefField ref, double rho_ff,
-                                                    double uxf, double uyf, double* __restrict__ partials) {
+__global__ void __launch_bounds__(NT) reduce_kernel(const T* __restrict__ A, Geom g, Shift<typename Store<T>::C> z,
+                                                    RefField ref, double rho_ff, double uxf, double uyf,
+                                                    double* __restrict__ partials) {
   using C = typename Store<T>::C;
   __shared__ double smem[NT / 32];
   double s[3] = {0.0, 0.0, 0.0};
@@ -145,7 +151,7 @@ __global__ void __launch_bounds__(NT) reduce_kernel(const T* __restrict__ A, Geo
     KahanSum<C> k0, k1, k2;
     for (int x = threadIdx.x; x < g.nx; x += NT) {
       C m[3];
-      node_dmoments(A, g, x, y, m);
+      node_dmoments(A, g, x, y, z, m);
       C drr = dr_ff, ur = ur_ff, vr = vr_ff;
       if (ref.rho) {
         const long long r = (long long)y * ref.pitch + x;

@@ -92,6 +92,7 @@ struct lbm_batch {
   void* scratch = nullptr;  // 3 fields of the largest instance (double)
   bool owns_pools = false, bound = false;
   InstDev* d_inst = nullptr;
+  void* d_shift = nullptr;  // per-instance storage shifts in the compute type (Shift<C>[count])
   int4* d_items = nullptr;
   int n_items = 0, n_bulk_items = 0;
   // launch shape; the default is the producer/consumer form (128 consumer
@@ -99,6 +100,7 @@ struct lbm_batch {
   int bx = 128, rows = 3, blocks = 0;  // blocks: -1 one per item, 0 one resident wave, > 0 as given
   int pf = 1;                          // register path: L2 prefetch distance; producer/consumer: nodes per quad
   bool split = false;                   // NSBC chunks in their own concurrent launch
+  bool shift = false;                   // some instance has a far field not at rest (Shift)
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int wave = 1;                        // resident blocks on the device for the current shape
@@ -150,9 +152,10 @@ __device__ __forceinline__ void prefetch_tile(const T* __restrict__ A, const Ins
 // PART 1: bulk tiles only; PART 2: NSBC chunks only (the split schedule runs
 // 1 and 2 as two concurrent launches, so the bulk launch keeps the register
 // budget -- and occupancy -- of the single-domain bulk kernel).
-template <typename T, int BX, int MODEL, int PART>
+template <typename T, int BX, int MODEL, int PART, bool SHIFT = false>
 __global__ void __launch_bounds__(BX) batch_step_kernel(const T* __restrict__ A, T* __restrict__ B,
                                                         const InstDev* __restrict__ inst,
+                                                        const lbmk::Shift<typename lbmk::Store<T>::C>* __restrict__ shifts,
                                                         const int4* __restrict__ items, int i0, int i1,
                                                         lbmk::Nsbc p, double s_e, double s_eps, double s_q, int pf) {
   using C = typename lbmk::Store<T>::C;
@@ -163,7 +166,8 @@ __global__ void __launch_bounds__(BX) batch_step_kernel(const T* __restrict__ A,
     const bool edge = PART == 2 || (PART == 0 && w.x < 0);
     const InstDev d = inst[edge ? ~w.x : w.x];
     const lbmk::Geom g{d.nx, d.ny, d.pitch, d.plane};
-    const lbmk::Rates<C> r{C(d.omega), C(s_e), C(s_eps), C(s_q)};
+    lbmk::Rates<C> r{C(d.omega), C(s_e), C(s_eps), C(s_q), {}};
+    if constexpr (SHIFT) r.z = shifts[edge ? ~w.x : w.x];
     const T* a = A + d.off;
     T* b = B + d.off;
     if constexpr (PART != 2) {
@@ -184,7 +188,7 @@ __global__ void __launch_bounds__(BX) batch_step_kernel(const T* __restrict__ A,
           const int j = w.y + (valid ? jr : 0);
           const int yy = 1 + j / nvec;
           const int x0 = (j - (yy - 1) * nvec) * V;
-          lbmk::bulk_row<T, MODEL>(a, b, g, r, yy, x0, lane, 0, 0u, valid);
+          lbmk::bulk_row<T, MODEL, SHIFT>(a, b, g, r, yy, x0, lane, 0, 0u, valid);
         }
         continue;
       }
@@ -195,7 +199,7 @@ __global__ void __launch_bounds__(BX) batch_step_kernel(const T* __restrict__ A,
       q.m0[1] = d.m0[1];
       q.m0[2] = d.m0[2];
       const int node = w.y + ((int)threadIdx.x >> 2);
-      if (node < w.y + w.z) lbmk::nsbc_node<T, MODEL>(a, b, g, q, r, node, (int)threadIdx.x & 3);
+      if (node < w.y + w.z) lbmk::nsbc_node<T, MODEL, SHIFT>(a, b, g, q, r, node, (int)threadIdx.x & 3);
     }
   }
 }
@@ -229,9 +233,10 @@ __global__ void wait_selftest_kernel(long long budget, int* flag) {
 // bulk tile it took is already in flight (two slots).  The last block out
 // resets the counters for the next step.  sched[2] is set if a bounded wait
 // on a copy gave up.
-template <typename T, int BX, int MODEL, int TILE>
+template <typename T, int BX, int MODEL, int TILE, bool SHIFT = false>
 __global__ void __launch_bounds__(BX) batch_tma_kernel(const T* __restrict__ A, T* __restrict__ B,
                                                        const InstDev* __restrict__ inst,
+                                                       const lbmk::Shift<typename lbmk::Store<T>::C>* __restrict__ shifts,
                                                        const int4* __restrict__ items, int n_items, lbmk::Nsbc p,
                                                        double s_e, double s_eps, double s_q, int* __restrict__ sched) {
   using C = typename lbmk::Store<T>::C;
@@ -283,7 +288,8 @@ __global__ void __launch_bounds__(BX) batch_tma_kernel(const T* __restrict__ A, 
     const int4 w = items[cur];
     const bool edge = w.x < 0;
     const InstDev d = inst[edge ? ~w.x : w.x];
-    const lbmk::Rates<C> r{C(d.omega), C(s_e), C(s_eps), C(s_q)};
+    lbmk::Rates<C> r{C(d.omega), C(s_e), C(s_eps), C(s_q), {}};
+    if constexpr (SHIFT) r.z = shifts[edge ? ~w.x : w.x];
     if (edge) {
       lbmk::Nsbc q = p;
       q.m0[0] = d.m0[0];
@@ -291,7 +297,7 @@ __global__ void __launch_bounds__(BX) batch_tma_kernel(const T* __restrict__ A, 
       q.m0[2] = d.m0[2];
       const lbmk::Geom g{d.nx, d.ny, d.pitch, d.plane};
       const int node = w.y + (tid >> 2);
-      if (node < w.y + w.z) lbmk::nsbc_node<T, MODEL>(A + d.off, B + d.off, g, q, r, node, tid & 3);
+      if (node < w.y + w.z) lbmk::nsbc_node<T, MODEL, SHIFT>(A + d.off, B + d.off, g, q, r, node, tid & 3);
     } else {
       // thread 0 waits (bounded) and tells the block, so that the whole block
       // takes the same way out if the copy never lands
@@ -307,7 +313,7 @@ __global__ void __launch_bounds__(BX) batch_tma_kernel(const T* __restrict__ A, 
       }
       mbar_wait(&bar[cslot], parity[cslot]);  // completes at once; orders this thread after the copy
       parity[cslot] ^= 1u;
-      collide_tile<T, BX, MODEL, TILE>(smem + cslot * 9 * SLOT, d, w, B, r);
+      collide_tile<T, BX, MODEL, TILE, SHIFT>(smem + cslot * 9 * SLOT, d, w, B, r);
     }
     __syncthreads();  // done with the current slot; s_next visible
     if (tid == 0) {
@@ -325,27 +331,45 @@ __global__ void __launch_bounds__(BX) batch_tma_kernel(const T* __restrict__ A, 
   }
 }
 
+// SHIFT: whether any instance has a far field not at rest (its stored
+// populations are then deviations from that equilibrium; see Shift).
+template <typename F>
+void with_shift(bool on, F&& f) {
+  if (on)
+    f(std::integral_constant<bool, true>{});
+  else
+    f(std::integral_constant<bool, false>{});
+}
+
 template <typename T, int BX, int MODEL, int TILE>
 void launch_tma(const lbm_batch_t* b, int from, cudaStream_t s, int grid) {
   // the dynamic shared-memory limit was raised by wave_blocks() when the work
   // list was built (never inside a stream capture)
   constexpr int smem = 2 * 9 * (TILE + 2) * 16;
-  batch_tma_kernel<T, BX, MODEL, TILE><<<grid, BX, smem, s>>>(static_cast<const T*>(b->pool[from]),
-                                                              static_cast<T*>(b->pool[1 - from]), b->d_inst,
-                                                              b->d_items, b->n_items, b->nsbc, b->s_e, b->s_eps,
-                                                              b->s_q, b->d_err);
+  with_shift(b->shift, [&](auto zc) {
+    batch_tma_kernel<T, BX, MODEL, TILE, decltype(zc)::value><<<grid, BX, smem, s>>>(
+        static_cast<const T*>(b->pool[from]), static_cast<T*>(b->pool[1 - from]), b->d_inst,
+        static_cast<const lbmk::Shift<typename lbmk::Store<T>::C>*>(b->d_shift), b->d_items, b->n_items,
+        b->nsbc, b->s_e, b->s_eps, b->s_q, b->d_err);
+  });
 }
 
 template <typename T, int NC, int MODEL, int TILE, int STAGES, int K>
 void launch_ws(const lbm_batch_t* b, int from, cudaStream_t s, int grid) {
   constexpr int smem = STAGES * 9 * (TILE + 2) * 16;  // limit raised by wave_blocks()
-  batch_ws_kernel<T, NC, MODEL, TILE, STAGES, K><<<grid, NC + 32, smem, s>>>(
-      static_cast<const T*>(b->pool[from]), static_cast<T*>(b->pool[1 - from]), b->d_inst, b->d_items, b->n_items,
-      b->nsbc, b->s_e, b->s_eps, b->s_q, b->d_err);
+  with_shift(b->shift, [&](auto zc) {
+    batch_ws_kernel<T, NC, MODEL, TILE, STAGES, K, decltype(zc)::value><<<grid, NC + 32, smem, s>>>(
+        static_cast<const T*>(b->pool[from]), static_cast<T*>(b->pool[1 - from]), b->d_inst,
+        static_cast<const lbmk::Shift<typename lbmk::Store<T>::C>*>(b->d_shift), b->d_items, b->n_items,
+        b->nsbc, b->s_e, b->s_eps, b->s_q, b->d_err);
+  });
 }
 
 template <typename T, int BX, int PART>
-const void* kernel_ptr(int model) {
+const void* kernel_ptr(int model, bool shift) {
+  if (shift)
+    return model == 1 ? (const void*)batch_step_kernel<T, BX, 1, PART, true>
+                      : (const void*)batch_step_kernel<T, BX, 0, PART, true>;
   return model == 1 ? (const void*)batch_step_kernel<T, BX, 1, PART> : (const void*)batch_step_kernel<T, BX, 0, PART>;
 }
 
@@ -353,12 +377,16 @@ template <typename T, int BX, int PART>
 void launch_part(const lbm_batch_t* b, int from, cudaStream_t s, int grid, int i0, int i1) {
   const T* A = static_cast<const T*>(b->pool[from]);
   T* B = static_cast<T*>(b->pool[1 - from]);
-  if (b->collision == 1)
-    batch_step_kernel<T, BX, 1, PART><<<grid, BX, 0, s>>>(A, B, b->d_inst, b->d_items, i0, i1, b->nsbc, b->s_e,
-                                                          b->s_eps, b->s_q, b->pf);
-  else
-    batch_step_kernel<T, BX, 0, PART><<<grid, BX, 0, s>>>(A, B, b->d_inst, b->d_items, i0, i1, b->nsbc, b->s_e,
-                                                          b->s_eps, b->s_q, b->pf);
+  const auto* zs = static_cast<const lbmk::Shift<typename lbmk::Store<T>::C>*>(b->d_shift);
+  with_shift(b->shift, [&](auto zc) {
+    constexpr bool Z = decltype(zc)::value;
+    if (b->collision == 1)
+      batch_step_kernel<T, BX, 1, PART, Z><<<grid, BX, 0, s>>>(A, B, b->d_inst, zs, b->d_items, i0, i1, b->nsbc, b->s_e,
+                                                              b->s_eps, b->s_q, b->pf);
+    else
+      batch_step_kernel<T, BX, 0, PART, Z><<<grid, BX, 0, s>>>(A, B, b->d_inst, zs, b->d_items, i0, i1, b->nsbc, b->s_e,
+                                                              b->s_eps, b->s_q, b->pf);
+  });
 }
 
 template <typename F>
@@ -415,8 +443,10 @@ int wave_blocks(const lbm_batch_t* b) {
       with_ws(b->rows, b->pf, [&](auto sc, auto kc) {
         constexpr int STAGES = decltype(sc)::value, K = decltype(kc)::value;
         constexpr int smem = STAGES * 9 * (128 + 2) * 16;
-        const void* k = b->collision == 1 ? (const void*)batch_ws_kernel<T, 128, 1, 128, STAGES, K>
-                                          : (const void*)batch_ws_kernel<T, 128, 0, 128, STAGES, K>;
+        const void* k = b->shift ? (b->collision == 1 ? (const void*)batch_ws_kernel<T, 128, 1, 128, STAGES, K, true>
+                                                      : (const void*)batch_ws_kernel<T, 128, 0, 128, STAGES, K, true>)
+                                 : (b->collision == 1 ? (const void*)batch_ws_kernel<T, 128, 1, 128, STAGES, K>
+                                                      : (const void*)batch_ws_kernel<T, 128, 0, 128, STAGES, K>);
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 128 + 32, smem);
       });
@@ -426,8 +456,10 @@ int wave_blocks(const lbm_batch_t* b) {
       with_tma(b->bx, b->tile, [&](auto bxc, auto tc) {
         constexpr int BX = decltype(bxc)::value, TILE = decltype(tc)::value;
         constexpr int smem = 2 * 9 * (TILE + 2) * 16;
-        const void* k = b->collision == 1 ? (const void*)batch_tma_kernel<T, BX, 1, TILE>
-                                          : (const void*)batch_tma_kernel<T, BX, 0, TILE>;
+        const void* k = b->shift ? (b->collision == 1 ? (const void*)batch_tma_kernel<T, BX, 1, TILE, true>
+                                                      : (const void*)batch_tma_kernel<T, BX, 0, TILE, true>)
+                                 : (b->collision == 1 ? (const void*)batch_tma_kernel<T, BX, 1, TILE>
+                                                      : (const void*)batch_tma_kernel<T, BX, 0, TILE>);
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BX, smem);
       });
@@ -435,7 +467,8 @@ int wave_blocks(const lbm_batch_t* b) {
     }
     with_bx(b->bx, [&](auto bxc) {
       constexpr int BX = decltype(bxc)::value;
-      const void* k = b->split ? kernel_ptr<T, BX, 1>(b->collision) : kernel_ptr<T, BX, 0>(b->collision);
+      const void* k =
+          b->split ? kernel_ptr<T, BX, 1>(b->collision, b->shift) : kernel_ptr<T, BX, 0>(b->collision, b->shift);
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BX, 0);
     });
   });
@@ -574,6 +607,19 @@ int ensure_batch_memory(lbm_batch_t* b) {
     BATCH_CUDA(cudaMalloc(&b->d_inst, b->inst.size() * sizeof(InstDev)));
     BATCH_CUDA(cudaMemcpy(b->d_inst, b->inst.data(), b->inst.size() * sizeof(InstDev), cudaMemcpyHostToDevice));
   }
+  if (!b->d_shift) {
+    // each instance's storage shift, rounded once on the host to the compute type
+    int rc = LBM_OK;
+    bdispatch(b->storage, [&](auto tag) {
+      using C = typename lbmk::Store<decltype(tag)>::C;
+      std::vector<lbmk::Shift<C>> z(b->inst.size());
+      for (size_t k = 0; k < z.size(); ++k) z[k] = lbmk::shift_as<C>(lbmk::far_field_shift(b->inst[k].m0));
+      if (cudaMalloc(&b->d_shift, z.size() * sizeof(lbmk::Shift<C>)) != cudaSuccess ||
+          cudaMemcpy(b->d_shift, z.data(), z.size() * sizeof(lbmk::Shift<C>), cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = LBM_ECUDA;
+    });
+    if (rc) return bfail(rc, "lbm_batch: shift table: %s", cudaGetErrorString(cudaGetLastError()));
+  }
   return LBM_OK;
 }
 
@@ -649,6 +695,7 @@ lbm_batch_t* lbm_batch_create(int32_t count, const lbm_instance_desc* descs, int
     d.m0[0] = s.farfield_rho;
     d.m0[1] = s.farfield_ux;
     d.m0[2] = s.farfield_uy;
+    b->shift = b->shift || lbmk::far_field_shift(d.m0).on;
     off += 9 * d.plane;
     b->inst.push_back(d);
     b->tau.push_back(s.tau);
@@ -674,6 +721,7 @@ void lbm_batch_destroy(lbm_batch_t* b) {
     cudaFree(b->scratch);
   }
   cudaFree(b->d_inst);
+  cudaFree(b->d_shift);
   cudaFree(b->d_items);
   cudaFree(b->d_err);
   if (b->cap) cudaStreamDestroy(b->cap);
@@ -772,8 +820,9 @@ int lbm_batch_init(lbm_batch_t* b, int32_t k, const double* rho, const double* u
   bdispatch(b->storage, [&](auto tag) {
     using T = decltype(tag);
     lbmk::init_kernel<T><<<lbmk::rows_grid(d.pitch, d.ny), 256, 0, b->stream>>>(
-        static_cast<T*>(b->pool[0]) + d.off, static_cast<T*>(b->pool[1]) + d.off, inst_geom(d), bscratch(b, 0),
-        bscratch(b, 1), bscratch(b, 2), 0, d.ny);
+        static_cast<T*>(b->pool[0]) + d.off, static_cast<T*>(b->pool[1]) + d.off, inst_geom(d),
+        lbmk::far_field_shift(d.m0),
+        bscratch(b, 0), bscratch(b, 1), bscratch(b, 2), 0, d.ny);
   });
   rc = batch_check_launch();
   if (rc) return rc;
@@ -832,8 +881,9 @@ int lbm_batch_get_macros(lbm_batch_t* b, int32_t k, double* rho, double* ux, dou
   bdispatch(b->storage, [&](auto tag) {
     using T = decltype(tag);
     lbmk::macros_kernel<T><<<lbmk::rows_grid(d.nx, d.ny), 256, 0, b->stream>>>(
-        static_cast<const T*>(b->pool[b->cur]) + d.off, inst_geom(d), bscratch(b, 0), bscratch(b, 1), bscratch(b, 2),
-        0, d.ny);
+        static_cast<const T*>(b->pool[b->cur]) + d.off, inst_geom(d),
+        lbmk::shift_as<typename lbmk::Store<T>::C>(lbmk::far_field_shift(d.m0)), bscratch(b, 0), bscratch(b, 1),
+        bscratch(b, 2), 0, d.ny);
   });
   int rc = batch_check_launch();
   if (rc) return rc;
@@ -856,8 +906,10 @@ int lbm_batch_unstable_nodes(lbm_batch_t* b, int32_t k, int64_t* count) {
   lbmk::RefField ref{nullptr, nullptr, nullptr, 0};
   bdispatch(b->storage, [&](auto tag) {
     using T = decltype(tag);
-    lbmk::reduce_kernel<T, 256><<<blocks, 256, 0, b->stream>>>(static_cast<const T*>(b->pool[b->cur]) + d.off,
-                                                               inst_geom(d), ref, d.m0[0], d.m0[1], d.m0[2], partials);
+    lbmk::reduce_kernel<T, 256><<<blocks, 256, 0, b->stream>>>(
+        static_cast<const T*>(b->pool[b->cur]) + d.off, inst_geom(d),
+        lbmk::shift_as<typename lbmk::Store<T>::C>(lbmk::far_field_shift(d.m0)),
+        ref, d.m0[0], d.m0[1], d.m0[2], partials);
   });
   lbmk::reduce_finish<256><<<1, 256, 0, b->stream>>>(partials, blocks, out);
   int rc = batch_check_launch();

@@ -329,6 +329,53 @@ __device__ __forceinline__ void equilibrium(C drho, C ux, C uy, C (&e)[9], C s =
   }
 }
 
+// Storage shift.  A stored population is h_i = f_i - f_i^eq(m0) (times the
+// storage scale), m0 = (rho0, u0) the far field: sh_i = f_i^eq(m0) - w_i is
+// added back to a deviation from w_i, and shm = (sum sh, sum c sh) = (rho0 - 1,
+// rho0 u0) to its moments.  For a far field at rest everything is zero and
+// h_i = f_i - w_i; with a mean flow the stored numbers stay as small as the
+// disturbance instead of carrying the stream's equilibrium (a 16-bit storage
+// keeps its relative precision for what changes).
+template <typename C>
+struct Shift {
+  C sh[9];
+  C shm[3];
+  bool on;  // false: all zero (far field at rest)
+};
+
+// The shift of far field m0 = (rho0, u0x, u0y), formed in double on the host
+// (the same expression as equilibrium() below, with rho0 - 1 kept apart).
+// Defined once, in lbm_runtime.cu: a host compiler that fuses multiply-adds
+// could otherwise round an inline copy differently in each file, and the
+// single-domain and batched paths must start from the same bits.
+Shift<double> far_field_shift(const double m0[3]);
+
+template <typename C>
+__host__ __device__ inline Shift<C> shift_as(const Shift<double>& z) {
+  Shift<C> o;
+  for (int i = 0; i < 9; ++i) o.sh[i] = C(z.sh[i]);
+  for (int c = 0; c < 3; ++c) o.shm[c] = C(z.shm[c]);
+  o.on = z.on;
+  return o;
+}
+
+// Relaxation rates, and the storage shift the collision needs.
+template <typename C>
+struct Rates {
+  C omega;         // BGK rate 1/tau, also the MRT stress rate omega_nu
+  C s_e, s_eps, s_q;
+  Shift<C> z;
+};
+
+// a * b + c rounded once, in every kernel alike (the shift terms multiply
+// loop-invariant values, and a compiler left free to hoist the product in one
+// kernel and fuse it in another would round them differently).
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+// a - b rounded on its own (never fused with a product that formed a)
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+
 // a / rho for the velocity u = (rho u) / rho: in float the fast division
 // intrinsic (within 2 ulp for rho in the normal range; rho is near 1 here),
 // an IEEE division in double (the parity mode).
@@ -339,18 +386,34 @@ __device__ __forceinline__ double div_rho(double a, double rho) { return a / rho
 // s * h (s = storage scale; the relaxation is linear in h, only the moments
 // need 1/s).  Written as h* = (1 - omega) h + omega h^eq with omega folded
 // into the equilibrium weights: one fused multiply-add per population.
-template <typename C>
-__device__ __forceinline__ void collide_bgk(C (&h)[9], C omega, C s = C(1)) {
+// With a storage shift (SHIFT: a far field not at rest) the moments gain shm
+// and the equilibrium loses sh_i.  The relaxation is one explicitly rounded
+// fused multiply-add per population in both forms, so that the shifted form
+// with a zero shift gives the same bits as the plain one.
+template <bool SHIFT, typename C>
+__device__ __forceinline__ void collide_bgk(C (&h)[9], const Rates<C>& r, C s = C(1)) {
+  const C omega = r.omega;
   C sd, sjx, sjy;
   moments(h, sd, sjx, sjy);
   const C is = C(1) / s;
+  if constexpr (SHIFT) {
+    sd = fma_rn(s, r.z.shm[0], sd);
+    sjx = fma_rn(s, r.z.shm[1], sjx);
+    sjy = fma_rn(s, r.z.shm[2], sjy);
+  }
   const C drho = sd * is;
   const C inv = div_rho(is, C(1) + drho);
   C e[9];
   equilibrium(drho, sjx * inv, sjy * inv, e, s * omega);
   const C keep = C(1) - omega;
+  if constexpr (SHIFT) {
+    const C so = s * omega;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) h[i] = keep * h[i] + e[i];
+    for (int i = 0; i < 9; ++i) h[i] = fma_rn(keep, h[i], fma_rn(-so, r.z.sh[i], e[i]));
+  } else {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) h[i] = fma_rn(keep, h[i], e[i]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -367,24 +430,28 @@ __device__ __forceinline__ void collide_bgk(C (&h)[9], C omega, C s = C(1)) {
 // not change M^-1 S M.  The conserved moments of f - f^eq vanish, so their
 // rates (C_rho, C_jx, C_jy) never enter.  The stress rate is 1/tau.
 // ---------------------------------------------------------------------------
-template <typename C>
-struct Rates {
-  C omega;         // BGK rate 1/tau, also the MRT stress rate omega_nu
-  C s_e, s_eps, s_q;
-};
 
-template <typename C>
+template <bool SHIFT, typename C>
 __device__ __forceinline__ void collide_mrt(C (&h)[9], const Rates<C>& r, C s = C(1)) {
   C sd, sjx, sjy;
   moments(h, sd, sjx, sjy);
   const C is = C(1) / s;
+  if constexpr (SHIFT) {
+    sd = fma_rn(s, r.z.shm[0], sd);
+    sjx = fma_rn(s, r.z.shm[1], sjx);
+    sjy = fma_rn(s, r.z.shm[2], sjy);
+  }
   const C drho = sd * is;
   const C inv = div_rho(is, C(1) + drho);
   C e[9];
   equilibrium(drho, sjx * inv, sjy * inv, e, s);
+  if constexpr (SHIFT) {
+#pragma unroll
+    for (int i = 0; i < 9; ++i) e[i] = fma_rn(-s, r.z.sh[i], e[i]);
+  }
   C n[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) n[i] = h[i] - e[i];
+  for (int i = 0; i < 9; ++i) n[i] = sub_rn(h[i], e[i]);
   const C ax = n[1] + n[2], ay = n[3] + n[4], d = (n[5] + n[6]) + (n[7] + n[8]);
   const C me = C(-4) * n[0] - (ax + ay) + C(2) * d;
   const C mep = C(4) * n[0] - C(2) * (ax + ay) + d;
@@ -409,12 +476,12 @@ __device__ __forceinline__ void collide_mrt(C (&h)[9], const Rates<C>& r, C s = 
 }
 
 // Collision model: 0 = BGK (Eq. lbe_1), 1 = MRT (Eq. mrt_lbe).
-template <int MODEL, typename C>
+template <int MODEL, bool SHIFT, typename C>
 __device__ __forceinline__ void collide(C (&h)[9], const Rates<C>& r, C s = C(1)) {
   if constexpr (MODEL == 1)
-    collide_mrt(h, r, s);
+    collide_mrt<SHIFT>(h, r, s);
   else
-    collide_bgk(h, r.omega, s);
+    collide_bgk<SHIFT>(h, r, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -460,7 +527,7 @@ __device__ __forceinline__ void perimeter_node(int k, int nx, int ny, int& x, in
 // double in the f64 parity mode.
 template <typename T>
 __device__ __forceinline__ void node_dmoments(const T* __restrict__ A, const Geom& g, int x, int y,
-                                              typename Store<T>::C (&m)[3]) {
+                                              const Shift<typename Store<T>::C>& z, typename Store<T>::C (&m)[3]) {
   using S = Store<T>;
   using C = typename S::C;
   const long long o = (long long)y * g.pitch + x;
@@ -469,6 +536,9 @@ __device__ __forceinline__ void node_dmoments(const T* __restrict__ A, const Geo
   for (int i = 0; i < 9; ++i) h[i] = S::ldg1(A + i * g.plane + o);
   C drho, jx, jy;
   moments(h, drho, jx, jy);
+  drho += z.shm[0];
+  jx += z.shm[1];
+  jy += z.shm[2];
   const C inv = div_rho(C(1), C(1) + drho);
   m[0] = drho;
   m[1] = jx * inv;
@@ -478,10 +548,15 @@ __device__ __forceinline__ void node_dmoments(const T* __restrict__ A, const Geo
 // (rho - 1, ux, uy) of a node's shifted populations (physical units) in the
 // compute type of the storage: the shifted populations keep d_rho free of
 // cancellation, so float is exact to float rounding of the perturbation.
-template <typename C>
-__device__ __forceinline__ void dmoments_of(const C (&h)[9], C (&m)[3]) {
+template <bool SHIFT, typename C>
+__device__ __forceinline__ void dmoments_of(const C (&h)[9], const Shift<C>& z, C (&m)[3]) {
   C drho, jx, jy;
   moments(h, drho, jx, jy);
+  if constexpr (SHIFT) {
+    drho += z.shm[0];
+    jx += z.shm[1];
+    jy += z.shm[2];
+  }
   const C inv = C(1) / (C(1) + drho);
   m[0] = drho;
   m[1] = jx * inv;

@@ -43,7 +43,7 @@ __device__ __forceinline__ unsigned warp_segment_bytes(const Geom& g, int warp_x
 // (0 = off, only with a row shared by the warp): lane 0 asks the bulk-copy
 // engine to pull the warp's segments of row y + pf into L2, so more bytes
 // are in flight than the registers of the resident warps hold.
-template <typename T, int MODEL>
+template <typename T, int MODEL, bool SHIFT = false>
 __device__ __forceinline__ void bulk_row(const T* __restrict__ A, T* __restrict__ B, const Geom& g,
                                          const Rates<typename Store<T>::C>& rates, int y, int x0, int lane,
                                          int pf, unsigned pf_bytes, bool valid = true) {
@@ -118,7 +118,7 @@ __device__ __forceinline__ void bulk_row(const T* __restrict__ A, T* __restrict_
       h[6] = k == V - 1 ? r6 : v[6][k + 1];
       h[7] = k == V - 1 ? r7 : v[7][k + 1];
       h[8] = k == 0 ? l8 : v[8][k - 1];
-      collide<MODEL>(h, rates, C(S::kScale));  // in stored units
+      collide<MODEL, SHIFT>(h, rates, C(S::kScale));  // in stored units
 #pragma unroll
       for (int i = 0; i < 9; ++i) o[i][k] = h[i];
     }
@@ -140,7 +140,7 @@ __device__ __forceinline__ void bulk_row(const T* __restrict__ A, T* __restrict_
   }
 }
 
-template <typename T, int BX, int MODEL>
+template <typename T, int BX, int MODEL, bool SHIFT = false>
 __global__ void __launch_bounds__(BX) bulk_kernel(const T* __restrict__ A, T* __restrict__ B, Geom g,
                                                   Rates<typename Store<T>::C> rates, int rows, int pf) {
   constexpr int V = Store<T>::V;
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(BX) bulk_kernel(const T* __restrict__ A, T* __
   const int y_begin = 1 + blockIdx.y * rows;
   const int y_end = min(y_begin + rows, g.ny - 1);
   const unsigned pf_bytes = warp_segment_bytes<T>(g, x0 - lane * V);
-  for (int y = y_begin; y < y_end; ++y) bulk_row<T, MODEL>(A, B, g, rates, y, x0, lane, pf, pf_bytes);
+  for (int y = y_begin; y < y_end; ++y) bulk_row<T, MODEL, SHIFT>(A, B, g, rates, y, x0, lane, pf, pf_bytes);
 }
 
 // ---------------------------------------------------------------------------
@@ -212,7 +212,7 @@ __device__ __forceinline__ C edge_predict(C vb, C v1, C v2, int c, bool diagonal
 // The rest of the node, given its pulled populations and the blended
 // (rho_c - 1, u_c): velocity override, reconstruction of the unknown
 // populations, correction, collision and the store.
-template <typename T, int MODEL>
+template <typename T, int MODEL, bool SHIFT = false>
 __device__ __forceinline__ void edge_finish(T* __restrict__ B, const Geom& g, const Nsbc& p,
                                             const Rates<typename Store<T>::C>& rates, const EdgeNode& en,
                                             typename Store<T>::C (&h)[9], const bool (&known)[9],
@@ -234,9 +234,14 @@ __device__ __forceinline__ void edge_finish(T* __restrict__ B, const Geom& g, co
     }
 
     // Eqs. (nes_0), (nes_1): f_in = f_in^eq(m_c) + f_out - f_out^eq(m_c)
+    // (in stored deviations: h^eq = f^eq - f^eq(m0), the same relation)
     const C drho_c = mc[0];
     C e[9];
     equilibrium(drho_c, mc[1], mc[2], e);
+    if constexpr (SHIFT) {
+#pragma unroll
+      for (int i = 0; i < 9; ++i) e[i] = sub_rn(e[i], rates.z.sh[i]);
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
       const int o = opp(i);
@@ -246,6 +251,11 @@ __device__ __forceinline__ void edge_finish(T* __restrict__ B, const Geom& g, co
     // Eq. (nes_4): f_i -= w_i (d_rho + kappa c_i . d(rho u))
     C drho, jx, jy;
     moments(h, drho, jx, jy);
+    if constexpr (SHIFT) {
+      drho += rates.z.shm[0];
+      jx += rates.z.shm[1];
+      jy += rates.z.shm[2];
+    }
     const C d_rho = drho - drho_c;
     const C d_jx = jx - (C(1) + mc[0]) * mc[1];
     const C d_jy = jy - (C(1) + mc[0]) * mc[2];
@@ -254,7 +264,7 @@ __device__ __forceinline__ void edge_finish(T* __restrict__ B, const Geom& g, co
     for (int i = 0; i < 9; ++i) h[i] -= wt<C>(i) * (d_rho + kap * (C(cx(i)) * d_jx + C(cy(i)) * d_jy));
   }
 
-  collide<MODEL>(h, rates);
+  collide<MODEL, SHIFT>(h, rates);
   const long long o = (long long)y * g.pitch + x;
 #pragma unroll
   for (int i = 0; i < 9; ++i) S::st1(B + i * g.plane + o, h[i]);
@@ -269,7 +279,7 @@ __device__ __forceinline__ void edge_finish(T* __restrict__ B, const Geom& g, co
 // blended components and finishes the node.  Every load of the K nodes is
 // issued before the first is used (one round trip for all of them); nodes
 // with valid[k] false are computed (from in-range addresses) but not stored.
-template <typename T, int MODEL, int K>
+template <typename T, int MODEL, int K, bool SHIFT = false>
 __device__ __forceinline__ void nsbc_nodes(const T* __restrict__ A, T* __restrict__ B, const Geom& g, const Nsbc& p,
                                            const Rates<typename Store<T>::C>& rates, const int (&node)[K],
                                            const bool (&valid)[K], int q) {
@@ -296,7 +306,7 @@ __device__ __forceinline__ void nsbc_nodes(const T* __restrict__ A, T* __restric
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     C mq[3];
-    dmoments_of(v[k], mq);  // all zeros from zero populations
+    dmoments_of<SHIFT>(v[k], rates.z, mq);  // lanes that loaded nothing get unused values
     C t0[3], t1[3], t2[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -314,15 +324,15 @@ __device__ __forceinline__ void nsbc_nodes(const T* __restrict__ A, T* __restric
   if (q != 0) return;
 #pragma unroll
   for (int k = 0; k < K; ++k)
-    if (valid[k]) edge_finish<T, MODEL>(B, g, p, rates, en[k], h[k], known[k], mc[k]);
+    if (valid[k]) edge_finish<T, MODEL, SHIFT>(B, g, p, rates, en[k], h[k], known[k], mc[k]);
 }
 
-template <typename T, int MODEL>
+template <typename T, int MODEL, bool SHIFT = false>
 __device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict__ B, const Geom& g, const Nsbc& p,
                                           const Rates<typename Store<T>::C>& rates, int node, int q) {
   const int n[1] = {node};
   const bool ok[1] = {true};
-  nsbc_nodes<T, MODEL, 1>(A, B, g, p, rates, n, ok, q);
+  nsbc_nodes<T, MODEL, 1, SHIFT>(A, B, g, p, rates, n, ok, q);
 }
 
 // One launch for the whole step (the "fused" form, for domains small enough
@@ -330,7 +340,7 @@ __device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict
 // one node per quad of lanes as in nsbc_kernel; the others are the blocks of
 // bulk_kernel's (threads_x, rows) grid, numbered row-major with nbx blocks
 // along x.  Same device functions, so the same bits as the kernel pair.
-template <typename T, int BX, int MODEL>
+template <typename T, int BX, int MODEL, bool SHIFT = false>
 __global__ void __launch_bounds__(BX) fused_step_kernel(const T* __restrict__ A, T* __restrict__ B, Geom g, Nsbc p,
                                                         Rates<typename Store<T>::C> rates, int rows, int pf, int n_edge,
                                                         int nbx) {
@@ -339,7 +349,7 @@ __global__ void __launch_bounds__(BX) fused_step_kernel(const T* __restrict__ A,
     const int t = blockIdx.x * BX + threadIdx.x;
     const int node = t >> 2, q = t & 3;
     if (node >= 2 * g.nx + 2 * (g.ny - 2)) return;  // a quad leaves together
-    nsbc_node<T, MODEL>(A, B, g, p, rates, node, q);
+    nsbc_node<T, MODEL, SHIFT>(A, B, g, p, rates, node, q);
     return;
   }
   const int k = (int)blockIdx.x - n_edge;
@@ -349,17 +359,17 @@ __global__ void __launch_bounds__(BX) fused_step_kernel(const T* __restrict__ A,
   const int y_begin = 1 + by * rows;
   const int y_end = min(y_begin + rows, g.ny - 1);
   const unsigned pf_bytes = warp_segment_bytes<T>(g, x0 - lane * V);
-  for (int y = y_begin; y < y_end; ++y) bulk_row<T, MODEL>(A, B, g, rates, y, x0, lane, pf, pf_bytes);
+  for (int y = y_begin; y < y_end; ++y) bulk_row<T, MODEL, SHIFT>(A, B, g, rates, y, x0, lane, pf, pf_bytes);
 }
 
-template <typename T, int MODEL>
+template <typename T, int MODEL, bool SHIFT = false>
 __global__ void __launch_bounds__(128) nsbc_kernel(const T* __restrict__ A, T* __restrict__ B, Geom g, Nsbc p,
                                                    Rates<typename Store<T>::C> rates) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int node = t >> 2, q = t & 3;
   const int perim = 2 * g.nx + 2 * (g.ny - 2);
   if (node >= perim) return;  // a quad leaves together
-  nsbc_node<T, MODEL>(A, B, g, p, rates, node, q);
+  nsbc_node<T, MODEL, SHIFT>(A, B, g, p, rates, node, q);
 }
 
 }  // namespace lbmk

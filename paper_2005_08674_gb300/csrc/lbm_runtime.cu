@@ -18,6 +18,23 @@
 #include "lbm_staged.cuh"
 #include "lbm_trace.h"
 
+namespace lbmk {
+Shift<double> far_field_shift(const double m0[3]) {
+  Shift<double> z{};
+  const double drho = m0[0] - 1.0, rho = m0[0], ux = m0[1], uy = m0[2];
+  const double usq = 1.5 * (ux * ux + uy * uy);
+  for (int i = 0; i < 9; ++i) {
+    const double cu = cx(i) * ux + cy(i) * uy;
+    z.sh[i] = wt<double>(i) * (drho + rho * (3.0 * cu + 4.5 * cu * cu - usq));
+  }
+  z.shm[0] = drho;
+  z.shm[1] = rho * ux;
+  z.shm[2] = rho * uy;
+  z.on = !(drho == 0.0 && ux == 0.0 && uy == 0.0);
+  return z;
+}
+}  // namespace lbmk
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -97,6 +114,7 @@ struct lbm {
   bool fused = false;
   int4* d_items = nullptr;
   lbmk::InstDev* d_inst = nullptr;
+  void* d_shift = nullptr;  // the far field's storage shift in the compute type (staged kernel)
   int* d_sched = nullptr;  // work counter, blocks done, give-up flag
   int n_items = 0, items_storage = -1, staged_grid = 0;
   // per-launch timing (lbm_profile): an event pair around every launch, and
@@ -165,9 +183,24 @@ int grid_for(long long n, int threads) {
 
 // ---- typed launchers ------------------------------------------------------
 
+
+// storage shift of the handle's far field (stored populations are
+// deviations from its equilibrium)
+lbmk::Shift<double> zshift(const lbm_t* h) { return lbmk::far_field_shift(h->nsbc.m0); }
+
 template <typename C>
 lbmk::Rates<C> rates(const lbm_t* h) {
-  return lbmk::Rates<C>{C(1.0 / h->tau), C(h->s_e), C(h->s_eps), C(h->s_q)};
+  return lbmk::Rates<C>{C(1.0 / h->tau), C(h->s_e), C(h->s_eps), C(h->s_q), lbmk::shift_as<C>(zshift(h))};
+}
+
+// SHIFT: the far field is not at rest, so the stored populations are
+// deviations from its equilibrium (Shift); the plain kernels otherwise.
+template <typename F>
+void with_shift(const lbm_t* h, F&& f) {
+  if (zshift(h).on)
+    f(std::integral_constant<bool, true>{});
+  else
+    f(std::integral_constant<bool, false>{});
 }
 
 template <typename T, int BX>
@@ -176,12 +209,15 @@ void launch_bulk_bx(const lbm_t* h, const void* a, void* b, int rows, cudaStream
   constexpr int V = lbmk::Store<T>::V;
   const int nvec = (h->nx + V - 1) / V;
   dim3 grid((nvec + BX - 1) / BX, (h->ny - 2 + rows - 1) / rows);
-  if (h->collision == 1)
-    lbmk::bulk_kernel<T, BX, 1><<<grid, BX, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
-                                                   rates<C>(h), rows, h->pf);
-  else
-    lbmk::bulk_kernel<T, BX, 0><<<grid, BX, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
-                                                   rates<C>(h), rows, h->pf);
+  with_shift(h, [&](auto zc) {
+    constexpr bool Z = decltype(zc)::value;
+    if (h->collision == 1)
+      lbmk::bulk_kernel<T, BX, 1, Z><<<grid, BX, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
+                                                        rates<C>(h), rows, h->pf);
+    else
+      lbmk::bulk_kernel<T, BX, 0, Z><<<grid, BX, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
+                                                        rates<C>(h), rows, h->pf);
+  });
 }
 
 template <typename T>
@@ -199,12 +235,15 @@ void launch_nsbc(const lbm_t* h, const void* a, void* b, cudaStream_t s) {
   using C = typename lbmk::Store<T>::C;
   const long long perim = 2LL * h->nx + 2LL * (h->ny - 2);
   const int blocks = (int)((perim * 4 + kNsbcThreads - 1) / kNsbcThreads);
-  if (h->collision == 1)
-    lbmk::nsbc_kernel<T, 1><<<blocks, kNsbcThreads, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
-                                                            h->nsbc, rates<C>(h));
-  else
-    lbmk::nsbc_kernel<T, 0><<<blocks, kNsbcThreads, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
-                                                            h->nsbc, rates<C>(h));
+  with_shift(h, [&](auto zc) {
+    constexpr bool Z = decltype(zc)::value;
+    if (h->collision == 1)
+      lbmk::nsbc_kernel<T, 1, Z><<<blocks, kNsbcThreads, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b),
+                                                                 geom(h), h->nsbc, rates<C>(h));
+    else
+      lbmk::nsbc_kernel<T, 0, Z><<<blocks, kNsbcThreads, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b),
+                                                                 geom(h), h->nsbc, rates<C>(h));
+  });
 }
 
 template <typename T, int BX>
@@ -216,12 +255,15 @@ void launch_fused_bx(const lbm_t* h, const void* a, void* b, int rows, cudaStrea
   const long long perim = 2LL * h->nx + 2LL * (h->ny - 2);
   const int n_edge = (int)((perim * 4 + BX - 1) / BX);
   const int grid = n_edge + nbx * nby;
-  if (h->collision == 1)
-    lbmk::fused_step_kernel<T, BX, 1><<<grid, BX, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
-                                                         h->nsbc, rates<C>(h), rows, h->pf, n_edge, nbx);
-  else
-    lbmk::fused_step_kernel<T, BX, 0><<<grid, BX, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
-                                                         h->nsbc, rates<C>(h), rows, h->pf, n_edge, nbx);
+  with_shift(h, [&](auto zc) {
+    constexpr bool Z = decltype(zc)::value;
+    if (h->collision == 1)
+      lbmk::fused_step_kernel<T, BX, 1, Z><<<grid, BX, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
+                                                              h->nsbc, rates<C>(h), rows, h->pf, n_edge, nbx);
+    else
+      lbmk::fused_step_kernel<T, BX, 0, Z><<<grid, BX, 0, s>>>(static_cast<const T*>(a), static_cast<T*>(b), geom(h),
+                                                              h->nsbc, rates<C>(h), rows, h->pf, n_edge, nbx);
+  });
 }
 
 template <typename T>
@@ -243,14 +285,16 @@ void launch_fused(const lbm_t* h, const void* a, void* b, cudaStream_t s) {
 constexpr int kStagedThreads = 128, kStagedTile = 128;
 
 template <typename T, int MODEL, int STAGES>
-const void* staged_kernel() {
-  return (const void*)lbmk::batch_ws_kernel<T, kStagedThreads, MODEL, kStagedTile, STAGES, 1>;
+const void* staged_kernel(bool shift) {
+  return shift ? (const void*)lbmk::batch_ws_kernel<T, kStagedThreads, MODEL, kStagedTile, STAGES, 1, true>
+               : (const void*)lbmk::batch_ws_kernel<T, kStagedThreads, MODEL, kStagedTile, STAGES, 1, false>;
 }
 
 template <typename T>
 const void* staged_kernel_for(const lbm_t* h) {
-  if (h->staged >= 4) return h->collision == 1 ? staged_kernel<T, 1, 4>() : staged_kernel<T, 0, 4>();
-  return h->collision == 1 ? staged_kernel<T, 1, 3>() : staged_kernel<T, 0, 3>();
+  const bool z = zshift(h).on;
+  if (h->staged >= 4) return h->collision == 1 ? staged_kernel<T, 1, 4>(z) : staged_kernel<T, 0, 4>(z);
+  return h->collision == 1 ? staged_kernel<T, 1, 3>(z) : staged_kernel<T, 0, 3>(z);
 }
 
 int staged_smem(const lbm_t* h) { return (h->staged >= 4 ? 4 : 3) * 9 * (kStagedTile + 2) * 16; }
@@ -262,20 +306,24 @@ void launch_staged(const lbm_t* h, const void* a, void* b, cudaStream_t s) {
   const int smem = staged_smem(h);
   const dim3 grid(h->staged_grid), block(kStagedThreads + 32);
   auto go = [&](auto kernel) {
-    kernel<<<grid, block, smem, s>>>(A, B, h->d_inst, h->d_items, h->n_items, h->nsbc, h->s_e, h->s_eps, h->s_q,
-                                     h->d_sched);
+    kernel<<<grid, block, smem, s>>>(A, B, h->d_inst,
+                                     static_cast<const lbmk::Shift<typename lbmk::Store<T>::C>*>(h->d_shift),
+                                     h->d_items, h->n_items, h->nsbc, h->s_e, h->s_eps, h->s_q, h->d_sched);
   };
-  if (h->staged >= 4) {
-    if (h->collision == 1)
-      go(lbmk::batch_ws_kernel<T, kStagedThreads, 1, kStagedTile, 4, 1>);
-    else
-      go(lbmk::batch_ws_kernel<T, kStagedThreads, 0, kStagedTile, 4, 1>);
-  } else {
-    if (h->collision == 1)
-      go(lbmk::batch_ws_kernel<T, kStagedThreads, 1, kStagedTile, 3, 1>);
-    else
-      go(lbmk::batch_ws_kernel<T, kStagedThreads, 0, kStagedTile, 3, 1>);
-  }
+  with_shift(h, [&](auto zc) {
+    constexpr bool Z = decltype(zc)::value;
+    if (h->staged >= 4) {
+      if (h->collision == 1)
+        go(lbmk::batch_ws_kernel<T, kStagedThreads, 1, kStagedTile, 4, 1, Z>);
+      else
+        go(lbmk::batch_ws_kernel<T, kStagedThreads, 0, kStagedTile, 4, 1, Z>);
+    } else {
+      if (h->collision == 1)
+        go(lbmk::batch_ws_kernel<T, kStagedThreads, 1, kStagedTile, 3, 1, Z>);
+      else
+        go(lbmk::batch_ws_kernel<T, kStagedThreads, 0, kStagedTile, 3, 1, Z>);
+    }
+  });
 }
 
 template <typename F>
@@ -312,6 +360,14 @@ int ensure_staged(lbm_t* h) {
     LBM_CUDA(cudaMemcpy(h->d_items, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice));
     if (!h->d_inst) LBM_CUDA(cudaMalloc(&h->d_inst, sizeof(lbmk::InstDev)));
     LBM_CUDA(cudaMemcpy(h->d_inst, &d, sizeof d, cudaMemcpyHostToDevice));
+    if (!h->d_shift) LBM_CUDA(cudaMalloc(&h->d_shift, sizeof(lbmk::Shift<double>)));
+    int rcz = LBM_OK;
+    dispatch(h->storage, [&](auto tag) {
+      using C = typename lbmk::Store<decltype(tag)>::C;
+      const lbmk::Shift<C> z = lbmk::shift_as<C>(zshift(h));
+      if (cudaMemcpy(h->d_shift, &z, sizeof z, cudaMemcpyHostToDevice) != cudaSuccess) rcz = LBM_ECUDA;
+    });
+    if (rcz) return fail(rcz, "staged step kernel: shift copy failed");
     if (!h->d_sched) {
       LBM_CUDA(cudaMalloc(&h->d_sched, 4 * sizeof(int)));
       LBM_CUDA(cudaMemset(h->d_sched, 0, 4 * sizeof(int)));
@@ -340,7 +396,7 @@ void enqueue_init_rows(const lbm_t* h, const double* d_rho, const double* d_ux, 
   dispatch(h->storage, [&](auto tag) {
     using T = decltype(tag);
     lbmk::init_kernel<T><<<lbmk::rows_grid(h->pitch, y1 - y0), 256, 0, h->stream>>>(
-        static_cast<T*>(h->buf[0]), static_cast<T*>(h->buf[1]), geom(h), d_rho, d_ux, d_uy, y0, y1);
+        static_cast<T*>(h->buf[0]), static_cast<T*>(h->buf[1]), geom(h), zshift(h), d_rho, d_ux, d_uy, y0, y1);
   });
 }
 
@@ -348,7 +404,8 @@ void enqueue_macros_rows(const lbm_t* h, double* d_rho, double* d_ux, double* d_
   dispatch(h->storage, [&](auto tag) {
     using T = decltype(tag);
     lbmk::macros_kernel<T><<<lbmk::rows_grid(h->nx, y1 - y0), 256, 0, h->stream>>>(
-        static_cast<const T*>(h->buf[h->cur]), geom(h), d_rho, d_ux, d_uy, y0, y1);
+        static_cast<const T*>(h->buf[h->cur]), geom(h), lbmk::shift_as<typename lbmk::Store<T>::C>(zshift(h)), d_rho,
+        d_ux, d_uy, y0, y1);
   });
 }
 
@@ -504,6 +561,7 @@ void lbm_destroy(lbm_t* h) {
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   if (h->d_items) cudaFree(h->d_items);
   if (h->d_inst) cudaFree(h->d_inst);
+  if (h->d_shift) cudaFree(h->d_shift);
   if (h->d_sched) cudaFree(h->d_sched);
   if (h->cap) {
     cudaStreamDestroy(h->cap);
@@ -758,8 +816,8 @@ int lbm_get_populations(lbm_t* h, double* f) {
   for (int i = 0; i < 9; ++i) {
     dispatch(h->storage, [&](auto tag) {
       using T = decltype(tag);
-      lbmk::plane_to_f64<T><<<grid_for(n, 256), 256, 0, h->stream>>>(static_cast<const T*>(h->buf[h->cur]), geom(h), i,
-                                                                      scratch_field(h, 0));
+      lbmk::plane_to_f64<T><<<grid_for(n, 256), 256, 0, h->stream>>>(static_cast<const T*>(h->buf[h->cur]), geom(h),
+                                                                      zshift(h), i, scratch_field(h, 0));
     });
     int rc = check_launch();
     if (rc) return rc;
@@ -781,7 +839,7 @@ int lbm_set_populations(lbm_t* h, const double* f) {
       using T = decltype(tag);
       for (int b = 0; b < 2; ++b)
         lbmk::f64_to_plane<T><<<grid_for((long long)h->ny * h->pitch, 256), 256, 0, h->stream>>>(
-            static_cast<T*>(h->buf[b]), geom(h), i, scratch_field(h, 0));
+            static_cast<T*>(h->buf[b]), geom(h), zshift(h), i, scratch_field(h, 0));
     });
     rc = check_launch();
     if (rc) return rc;
@@ -831,8 +889,8 @@ int lbm_reduce(lbm_t* h, const double* ref_rho, const double* ref_ux, const doub
   dispatch(h->storage, [&](auto tag) {
     using T = decltype(tag);
     lbmk::reduce_kernel<T, kReduceThreads><<<blocks, kReduceThreads, 0, h->stream>>>(
-        static_cast<const T*>(h->buf[h->cur]), geom(h), ref, h->nsbc.m0[0], h->nsbc.m0[1], h->nsbc.m0[2],
-        scratch_partials(h));
+        static_cast<const T*>(h->buf[h->cur]), geom(h), lbmk::shift_as<typename lbmk::Store<T>::C>(zshift(h)), ref,
+        h->nsbc.m0[0], h->nsbc.m0[1], h->nsbc.m0[2], scratch_partials(h));
   });
   lbmk::reduce_finish<kReduceThreads><<<1, kReduceThreads, 0, h->stream>>>(scratch_partials(h), blocks, scratch_out(h));
   int rc = check_launch();
@@ -1087,7 +1145,8 @@ extern "C" int lbm_reduce_noalloc(lbm_t* h, const double* ref_rho, const double*
   dispatch(h->storage, [&](auto tag) {
     using T = decltype(tag);
     lbmk::reduce_kernel<T, kNoAllocThreads><<<(int)blocks, kNoAllocThreads, 0, h->stream>>>(
-        static_cast<const T*>(h->buf[h->cur]), geom(h), ref, h->nsbc.m0[0], h->nsbc.m0[1], h->nsbc.m0[2], partials);
+        static_cast<const T*>(h->buf[h->cur]), geom(h), lbmk::shift_as<typename lbmk::Store<T>::C>(zshift(h)), ref,
+        h->nsbc.m0[0], h->nsbc.m0[1], h->nsbc.m0[2], partials);
   });
   lbmk::reduce_finish<kNoAllocThreads><<<1, kNoAllocThreads, 0, h->stream>>>(partials, (int)blocks, d_out);
   rc = check_launch();

@@ -135,7 +135,7 @@ __device__ __forceinline__ void issue_tile(const T* __restrict__ A, const InstDe
 // Collide the nodes of a staged bulk tile (slot `sl`) and store them to B.
 // 16-bit storages are collided in half vectors (4 nodes per thread) so the
 // per-thread register footprint matches the f32 path.
-template <typename T, int BX, int MODEL, int TILE>
+template <typename T, int BX, int MODEL, int TILE, bool SHIFT = false>
 __device__ __forceinline__ void collide_tile(const unsigned char* sl, const InstDev& d, const int4& w,
                                              T* __restrict__ B, const lbmk::Rates<typename lbmk::Store<T>::C>& r) {
   using S = lbmk::Store<T>;
@@ -180,7 +180,7 @@ __device__ __forceinline__ void collide_tile(const unsigned char* sl, const Inst
       h[6] = kk == CPT - 1 ? rt[6] : v[6][kk + 1];
       h[7] = kk == CPT - 1 ? rt[7] : v[7][kk + 1];
       h[8] = kk == 0 ? lf[8] : v[8][kk - 1];
-      lbmk::collide<MODEL>(h, r, C(S::kScale));
+      lbmk::collide<MODEL, SHIFT>(h, r, C(S::kScale));
 #pragma unroll
       for (int i = 0; i < 9; ++i) o[i][kk] = h[i];
     }
@@ -216,9 +216,10 @@ __device__ __forceinline__ void collide_tile(const unsigned char* sl, const Inst
 // (one arrival per consumer warp).  No block-wide barrier inside the loop;
 // every wait is bounded, and on give-up a thread records the flag and leaves.
 // ---------------------------------------------------------------------------
-template <typename T, int NC, int MODEL, int TILE, int STAGES, int K>
+template <typename T, int NC, int MODEL, int TILE, int STAGES, int K, bool SHIFT = false>
 __global__ void __launch_bounds__(NC + 32, 4) batch_ws_kernel(const T* __restrict__ A, T* __restrict__ B,
                                                            const InstDev* __restrict__ inst,
+                                                           const Shift<typename Store<T>::C>* __restrict__ shifts,
                                                            const int4* __restrict__ items, int n_items, lbmk::Nsbc p,
                                                            double s_e, double s_eps, double s_q,
                                                            int* __restrict__ sched) {
@@ -292,7 +293,8 @@ __global__ void __launch_bounds__(NC + 32, 4) batch_ws_kernel(const T* __restric
     if (w.w < 0) break;
     const bool edge = w.x < 0;
     const InstDev d = rinst[s];
-    const lbmk::Rates<C> r{C(d.omega), C(s_e), C(s_eps), C(s_q)};
+    lbmk::Rates<C> r{C(d.omega), C(s_e), C(s_eps), C(s_q), {}};
+    if constexpr (SHIFT) r.z = shifts[w.x < 0 ? ~w.x : w.x];  // the instance's storage shift
     if (edge) {
       lbmk::Nsbc q = p;
       q.m0[0] = d.m0[0];
@@ -308,9 +310,9 @@ __global__ void __launch_bounds__(NC + 32, 4) batch_ws_kernel(const T* __restric
         valid[k] = n < w.z;
         node[k] = w.y + (valid[k] ? n : 0);
       }
-      lbmk::nsbc_nodes<T, MODEL, K>(A + d.off, B + d.off, g, q, r, node, valid, tid & 3);
+      lbmk::nsbc_nodes<T, MODEL, K, SHIFT>(A + d.off, B + d.off, g, q, r, node, valid, tid & 3);
     } else {
-      collide_tile<T, NC, MODEL, TILE>(smem + s * 9 * SLOT, d, w, B, r);
+      collide_tile<T, NC, MODEL, TILE, SHIFT>(smem + s * 9 * SLOT, d, w, B, r);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
