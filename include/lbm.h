@@ -41,8 +41,10 @@ extern "C" {
 #define LBM_ETIMEOUT (-6)  /* a bounded device-side wait gave up (see lbm_batch_status) */
 
 /* Storage of the populations in device memory.  Every type stores the
- * deviation f_i - w_i from the rest-state weights (a shift that keeps the
- * stored magnitudes small, so rounding is relative to the perturbation).
+ * deviation f_i - f_i^eq(m_0) from the equilibrium of the far field m_0 given
+ * to lbm_create (for a far field at rest that is f_i - w_i): a shift that
+ * keeps the stored magnitudes as small as the disturbance, so rounding is
+ * relative to it even in a mean flow.  binary16 holds it scaled by 2^12.
  * Arithmetic: LBM_F64 computes in double everywhere; the other three
  * collide and apply the NSBC in float, with the NSBC gradient extrapolation
  * and far-field blend (Eqs. nes_2, nes_3) in double. */
