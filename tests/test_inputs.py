@@ -1,0 +1,59 @@
+"""The seeded input generators shared by the oracle's and the CUDA path's
+tests: SplitMix64 against its published test vector (seed 0), the uniform
+draw's definition, and the initial fields against their defining properties
+(a pulse's half width at half maximum, a vortex's stream at its centre and
+its swirl's sense, a plane wave's peak condensation)."""
+import math
+
+import numpy as np
+
+from paper_2005_08674_gb300 import inputs
+
+
+def test_splitmix64_reference_vector():
+    g = inputs.SplitMix64(0)
+    assert [g.next_u64() for _ in range(3)] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_uniform_is_the_top_53_bits():
+    a, b = inputs.SplitMix64(7), inputs.SplitMix64(7)
+    for _ in range(5):
+        z = a.next_u64()
+        assert b.uniform() == (z >> 11) * 2.0 ** -53
+    u = [inputs.SplitMix64(k).uniform() for k in range(200)]
+    assert all(0.0 <= x < 1.0 for x in u)
+
+
+def test_pulse_half_width_at_half_maximum():
+    A, b = 1e-3, 4.0
+    rho, ux, uy = inputs.acoustic_pulse(41, 31, A, b, [(20.0, 15.0)])
+    assert math.isclose(rho[15, 20] - 1.0, A, rel_tol=1e-12)
+    assert math.isclose(rho[15, 24] - 1.0, A / 2, rel_tol=1e-12)   # distance b along x
+    assert math.isclose(rho[11, 20] - 1.0, A / 2, rel_tol=1e-12)   # distance b along y
+    assert np.all(ux == 0) and np.all(uy == 0)
+
+
+def test_vortex_stream_and_swirl():
+    u0, bu, rc = 0.05, 0.02, 6.0
+    rho, ux, uy = inputs.convected_vortex(61, 41, u0, bu, rc, 30.0, 20.0)
+    assert math.isclose(ux[20, 30], u0, rel_tol=1e-14) and uy[20, 30] == 0.0
+    # counter-clockwise swirl: +y velocity to the right of the centre, -x above it
+    assert uy[20, 36] > 0 and ux[26, 30] < u0
+    # density dips at the centre and returns to 1 far away
+    assert rho[20, 30] < 1.0 and math.isclose(rho[0, 0], 1.0, abs_tol=1e-12)
+
+
+def test_plane_wave_peak_and_direction():
+    """Along the propagation direction the condensation peaks at zeta / rho0 one
+    width lam ahead of the origin (xi exp(-xi^2 / 2 lam^2) peaks at xi = lam),
+    and the velocity is cs times the condensation along that direction."""
+    zeta, lam = 0.01, 4.0
+    rho, ux, uy = inputs.plane_wave(64, 64, zeta, lam, 0.0, origin=(20.0, 10.0))
+    assert math.isclose(rho[5, 24] - 1.0, zeta, rel_tol=1e-12)       # xi = x - 20 = lam
+    assert math.isclose(rho[5, 16] - 1.0, -zeta, rel_tol=1e-12)      # xi = -lam
+    assert float(np.max(rho - 1.0)) <= zeta * (1 + 1e-12)
+    assert np.allclose(ux, inputs.CS * (rho - 1.0), rtol=0, atol=1e-15) and np.all(uy == 0)
+    rho60, ux60, uy60 = inputs.plane_wave(64, 64, zeta, lam, 60.0)
+    s = rho60 - 1.0
+    assert np.allclose(ux60, inputs.CS * s * 0.5, atol=1e-15)
+    assert np.allclose(uy60, inputs.CS * s * math.sqrt(3) / 2, atol=1e-15)
