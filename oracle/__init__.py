@@ -70,6 +70,7 @@ def lib(openmp: bool = False):
             L.or_steps.argtypes = [ctypes.c_void_p]
             L.or_equilibrium.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp]
             L.or_lattice.argtypes = [_ip, _ip, _dp, _ip]
+            L.or_set_storage.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
             _libs[openmp] = L
     return _libs[openmp]
 
@@ -153,6 +154,17 @@ class Oracle:
 
     def step(self, n: int = 1):
         self._L.or_step(self._h, int(n))
+        return self
+
+    STORAGE_FORMATS = {"f64": 0, "f32": 1, "f16": 2, "bf16": 3}
+
+    def storage(self, fmt: str, far_field_shift: bool = True):
+        """Storage emulation (a test instrument): from now on, and at once, every
+        population is kept as its deviation from f^eq(m_0) (or from w_i)
+        rounded through `fmt` (f32, f16 scaled by 2^12, bf16); "f64" is off.
+        All arithmetic stays double, so the difference to a plain run is what
+        the narrower storage alone loses."""
+        self._L.or_set_storage(self._h, self.STORAGE_FORMATS[fmt], int(bool(far_field_shift)))
         return self
 
     @property

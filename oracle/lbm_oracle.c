@@ -84,6 +84,8 @@ typedef struct or_sim {
   double Minv[9][9];
   double *f, *fn;     /* [9][ny][nx] post-collision populations, and the next buffer */
   long steps;
+  int store_fmt;      /* storage emulation (test instrument): 0 off, 1 binary32, 2 binary16 x 2^12, 3 bfloat16 */
+  int store_ff;       /* deviations stored from f^eq(m_0) (1) or from w_i (0) */
 } or_sim;
 
 #define F(s, buf, i, x, y) ((buf)[((size_t)(i) * (size_t)(s)->ny + (size_t)(y)) * (size_t)(s)->nx + (size_t)(x)])
@@ -325,6 +327,50 @@ void or_mrt_matrix(const or_sim* s, double* M) {
     for (int i = 0; i < 9; ++i) M[a * 9 + i] = s->M[a][i];
 }
 
+/* Storage emulation -- a test instrument, off unless or_set_storage is called.
+ * It models only what keeping the populations in a narrower format loses:
+ * after the initialisation and after every step each population f_i is
+ * replaced by r_i + q(f_i - r_i), with r_i = f_i^eq(m_0) (store_ff = 1) or
+ * w_i (store_ff = 0) and q rounding to nearest, ties to even, through
+ * binary32 (format 1), binary16 holding the value times 2^12 (format 2) or
+ * bfloat16 (format 3; the binary32 value's upper half, rounded).  The 16-bit
+ * formats are reached through binary32, as a device computing in float would
+ * reach them.  Everything in between stays double. */
+static double q_store(double v, int fmt) {
+  if (fmt == 1) return (double)(float)v;
+  if (fmt == 2) return (double)(_Float16)(float)(v * 4096.0) / 4096.0;
+  if (fmt == 3) {
+    float f = (float)v;
+    uint32_t b;
+    memcpy(&b, &f, sizeof b);
+    if ((b & 0x7f800000u) != 0x7f800000u) { /* finite: round the lower half away, ties to even */
+      b += 0x7fffu + ((b >> 16) & 1u);
+      b &= 0xffff0000u;
+    }
+    memcpy(&f, &b, sizeof f);
+    return (double)f;
+  }
+  return v;
+}
+
+static void apply_storage(const or_sim* s, double* buf) {
+  if (!s->store_fmt) return;
+  double r[9];
+  if (s->store_ff)
+    or_equilibrium(s->m0[0], s->m0[1], s->m0[2], r);
+  else
+    for (int i = 0; i < 9; ++i) r[i] = WT[i];
+  for (int i = 0; i < 9; ++i)
+    for (int y = 0; y < s->ny; ++y)
+      for (int x = 0; x < s->nx; ++x) F(s, buf, i, x, y) = r[i] + q_store(F(s, buf, i, x, y) - r[i], s->store_fmt);
+}
+
+void or_set_storage(or_sim* s, int format, int far_field_shift) {
+  s->store_fmt = format;
+  s->store_ff = far_field_shift;
+  apply_storage(s, s->f);
+}
+
 /* f := f^eq(rho, u) at every node; fields are [ny][nx], x fastest */
 void or_init(or_sim* s, const double* rho, const double* ux, const double* uy) {
   double feq[9];
@@ -334,6 +380,7 @@ void or_init(or_sim* s, const double* rho, const double* ux, const double* uy) {
       or_equilibrium(rho[k], ux[k], uy[k], feq);
       for (int i = 0; i < 9; ++i) F(s, s->f, i, x, y) = feq[i];
     }
+  apply_storage(s, s->f);
   s->steps = 0;
 }
 
@@ -387,6 +434,7 @@ void or_step(or_sim* s, int n) {
           collide_bgk(s, g);
         for (int i = 0; i < 9; ++i) F(s, s->fn, i, x, y) = g[i];
       }
+    apply_storage(s, s->fn);
     double* t = s->f;
     s->f = s->fn;
     s->fn = t;
