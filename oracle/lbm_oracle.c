@@ -21,6 +21,9 @@
  *   NSBC ..................... Sec. 5: Eq. (nes_0)/(nes_1) mirror, Eq. (nes_2) gradient
  *                              prediction, Eq. (nes_3) far-field blend, Eq. (nes_4) correction,
  *                              then the ordinary collision at the boundary node.
+ *   storage emulation ........ no counterpart in the paper: an optional rounding of the
+ *                              stored populations through a narrower format (or_set_storage),
+ *                              used by the tests to separate storage loss from arithmetic.
  *
  * Readings taken where the paper is silent or ambiguous (all selectable where
  * an alternative is plausible):
