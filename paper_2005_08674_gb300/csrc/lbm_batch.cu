@@ -18,7 +18,10 @@
 //   batch_tma_kernel  the same staging with the whole block taking turns;
 //   batch_step_kernel tiles straight from global memory (register path).
 // The staged forms take items from a counter in device memory, in memory
-// order with each NSBC chunk after the tile that stages its rows.
+// order with each NSBC chunk after the tile that stages its rows.  Every form
+// is compiled plain and with the far-field storage shift (Shift); a batch
+// with any instance in a mean flow runs the shifted one, reading each
+// instance's shift from a small device table.
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -1,6 +1,9 @@
 // lbm_runtime.cu -- host runtime behind the C ABI of include/lbm.h: handle
 // state, device memory (library-owned or caller-bound), stream, CUDA-graph
-// replay of the step loop, launch-shape autotuning, and the entry points.
+// replay of the step loop, the three step forms (bulk + NSBC kernel pair,
+// fused one-launch kernel, staged producer/consumer kernel) in their plain
+// or far-field-shifted variant, launch-shape autotuning, and the entry
+// points.
 #include <cuda_runtime.h>
 
 #include <algorithm>
