@@ -119,7 +119,14 @@ def vortex_reference():
         ref = R.window(big.macros(), P, V_N, V_N)
         refs.append(ref)
         rs.append(R.energy(*test.macros(), *ref) / e0)
-    return dict(u0=u0, f0=f0, refs=refs, e0=e0, r_max=max(rs), final=test.macros())
+    final = test.macros()
+    # what the storage format alone loses: the oracle with its populations
+    # rounded through that format (deviations from the far-field equilibrium)
+    emulated = {}
+    for fmt in ("f16", "bf16"):
+        o = oracle.Oracle(V_N, V_N, V_TAU, 1.0, (u0, 0.0), **kw).storage(fmt, True).init(*f0)
+        emulated[fmt] = float(np.abs(o.step(V_STEPS).macros()[0] - final[0]).max())
+    return dict(u0=u0, f0=f0, refs=refs, e0=e0, r_max=max(rs), final=final, emulated=emulated)
 
 
 # f32 and f16 meet the bars (density error 1e-4 for 16-bit storage, R_max
@@ -142,7 +149,8 @@ def test_vortex_storage_error_and_reflection(lbm, vortex_reference, storage, rho
     r_max = max(rs)
     change = abs(r_max - ref["r_max"]) / ref["r_max"]
     res = dict(storage=storage, workload=f"vortex leaving a {V_N}^2 domain, MRT, {V_STEPS} steps",
-               max_abs_drho=d_rho, max_abs_du=d_u, r_max=r_max, r_max_oracle=ref["r_max"], r_change=change)
+               max_abs_drho=d_rho, max_abs_du=d_u, r_max=r_max, r_max_oracle=ref["r_max"], r_change=change,
+               oracle_storage_emulation_drho=ref["emulated"].get(storage))
     out = os.environ.get("LBM_RESULTS_DIR")
     if out:
         os.makedirs(out, exist_ok=True)
@@ -151,3 +159,7 @@ def test_vortex_storage_error_and_reflection(lbm, vortex_reference, storage, rho
     print(res)
     assert d_rho <= rho_tol, res
     assert change <= r_tol, res
+    if storage in ref["emulated"]:
+        # the 16-bit error is the storage format's: within a factor of 3 of the
+        # oracle run that loses only what that storage loses
+        assert d_rho <= 3.0 * ref["emulated"][storage], res
