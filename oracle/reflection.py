@@ -14,6 +14,11 @@ extended domain D' = D padded by P nodes on every side (padding at the far
 field) that is large enough that nothing reflected at the edge of D' can
 re-enter D by the final time.  Then R(t) = E[test(t), ref(t)] / E[ref(0), m0],
 and R_max = max over sampled t.
+
+The measure itself is pinned by its closed forms (zero for equal fields,
+symmetry, the one-node disturbance, padding and windowing as inverses).  The
+values of R_max it gives for the paper's experiments are parity unpinned
+against the paper, which prints no reflection numbers.
 """
 from __future__ import annotations
 
