@@ -298,10 +298,17 @@ typedef struct lbm_instance_desc {
 lbm_batch_t* lbm_batch_create(int32_t count, const lbm_instance_desc* descs, int32_t storage);
 /* Frees library-owned device memory; synchronises the stream.  NULL-safe. */
 void lbm_batch_destroy(lbm_batch_t* b);
+/* NSBC parameters (Eqs. nes_2-nes_4) for every instance of the batch: same
+ * arguments, ranges and LBM_EINVAL cases as lbm_set_nsbc.  Host-only. */
 int lbm_batch_set_nsbc(lbm_batch_t* b, double gamma, double beta, double kappa, int32_t grad_order);
+/* Collision model (LBM_BGK, or LBM_MRT with the rates of Sec. 4) for every
+ * instance: same arguments and errors as lbm_set_collision.  Host-only. */
 int lbm_batch_set_collision(lbm_batch_t* b, int32_t model, double omega_e, double omega_eps, double omega_q);
 /* Edge types for every instance of the batch, as lbm_set_edges. */
 int lbm_batch_set_edges(lbm_batch_t* b, const int32_t types[4], const double uw[8]);
+/* CUDA stream (a cudaStream_t, NULL = the legacy default stream) on which
+ * every later call on the batch works, as lbm_set_stream.  The step graph is
+ * captured on a private stream and launched on this one, so it is kept. */
 int lbm_batch_set_stream(lbm_batch_t* b, void* cuda_stream);
 /* Total nodes over all instances. */
 int64_t lbm_batch_cells(const lbm_batch_t* b);
@@ -316,6 +323,8 @@ int lbm_batch_bind(lbm_batch_t* b, void* dev_a, void* dev_b, void* dev_scratch);
 int lbm_batch_init(lbm_batch_t* b, int32_t k, const double* rho, const double* ux, const double* uy);
 /* n steps of every instance (all must be initialised); asynchronous. */
 int lbm_batch_step(lbm_batch_t* b, int32_t n);
+/* Steps issued (host counter, no sync); an lbm_batch_init after steps
+ * were taken restarts it at 0 for the whole batch.  -1 for NULL. */
 int64_t lbm_batch_steps_done(const lbm_batch_t* b);
 /* Macros of instance k into HOST arrays [ny_k][nx_k] double; synchronises. */
 int lbm_batch_get_macros(lbm_batch_t* b, int32_t k, double* rho, double* ux, double* uy);
