@@ -3,7 +3,8 @@ LBM_CHECKED=1 by test_checked_build_gpu.py; not collected by pytest).
 
 Steps every launch form of the single-domain (kernel pair, fused, staged)
 and batched paths on small, odd-sized domains (all storages, BGK and MRT,
-first- and second-order NSBC differences, periodic and velocity edges) and
+first- and second-order NSBC differences, periodic and velocity edges, far
+fields at rest and in a stream, i.e. the plain and shifted kernels) and
 prints one JSON line: whether the loaded library is the checked build, how
 many accesses its checker rejected, the first rejected address, and the
 largest f64 difference from the oracle (the checked build must still compute
@@ -39,7 +40,9 @@ def main():
     torch.cuda.set_device(0)
     worst = 0.0
     kws = [dict(beta=0.1), dict(collision="mrt", mrt_rates=(1.4, 1.4, 1.2), grad_order=2),
-           dict(edges=[("velocity", 0.03, 0.0), "nsbc", "periodic", "periodic"])]
+           dict(edges=[("velocity", 0.03, 0.0), "nsbc", "periodic", "periodic"]),
+           # a far field with a mean flow: the shifted form of every step kernel
+           dict(farfield_rho=1.001, farfield_u=(0.04, -0.01), beta=0.1, collision="mrt", mrt_rates=(1.4, 1.4, 1.2))]
     for nx, ny in SIZES:
         fields = inputs.acoustic_pulse(nx, ny, 1e-3, 2.0, [((nx - 1) / 2, (ny - 1) / 2)])
         ref = oracle.Oracle(nx, ny, 0.6, beta=0.1).init(*fields).step(STEPS).macros()
