@@ -43,6 +43,23 @@ def test_vortex_stream_and_swirl():
     assert rho[20, 30] < 1.0 and math.isclose(rho[0, 0], 1.0, abs_tol=1e-12)
 
 
+def test_vortex_swirl_profile_and_radial_balance():
+    """The swirl v_theta = beta u0 (r / R_c) exp(-r^2 / 2 R_c^2) reaches
+    beta u0 e^(-1/2) at r = R_c; the density satisfies the radial momentum
+    balance of a steady vortex to first order, cs^2 d(rho)/dr = v_theta^2 / r
+    (central differences along the x axis, within 1 %), and its integral from
+    the centre to the far field, cs^2 (1 - rho(0)) = (beta u0)^2 / 2."""
+    u0, bu, rc = 0.05, 0.02, 12.0
+    rho, ux, uy = inputs.convected_vortex(121, 101, u0, bu, rc, 60.0, 50.0)
+    assert math.isclose(uy[50, 72], bu * math.exp(-0.5), rel_tol=1e-13) and ux[50, 72] == u0
+    assert math.isclose(ux[62, 60], u0 - bu * math.exp(-0.5), rel_tol=1e-13) and uy[62, 60] == 0.0
+    for r in (6, 12, 18):
+        v = uy[50, 60 + r]
+        drho = (rho[50, 61 + r] - rho[50, 59 + r]) / 2.0
+        assert math.isclose(inputs.CS ** 2 * drho, v * v / r, rel_tol=0.01), r
+    assert math.isclose(inputs.CS ** 2 * (1.0 - rho[50, 60]), bu * bu / 2.0, rel_tol=1e-12)
+
+
 def test_plane_wave_peak_and_direction():
     """Along the propagation direction the condensation peaks at zeta / rho0 one
     width lam ahead of the origin (xi exp(-xi^2 / 2 lam^2) peaks at xi = lam),
