@@ -117,6 +117,11 @@ int lbm_set_precision(lbm_t* h, int32_t storage);
  * default stream) for all later device work of this handle. */
 int lbm_set_stream(lbm_t* h, void* cuda_stream);
 
+/* Node counts of the domain as given to lbm_create, so that a caller or a
+ * binding can size the [ny][nx] arrays the other calls read and write.
+ * Host-only.  LBM_EINVAL for a NULL argument. */
+int lbm_get_dims(const lbm_t* h, int32_t* nx, int32_t* ny);
+
 /* Bytes of ONE population buffer: 9 planes of ny rows of `pitch` elements
  * of the storage type, pitch = nx rounded up to 64, each plane starting
  * 256-byte aligned. */
@@ -312,6 +317,9 @@ int lbm_batch_set_edges(lbm_batch_t* b, const int32_t types[4], const double uw[
 int lbm_batch_set_stream(lbm_batch_t* b, void* cuda_stream);
 /* Total nodes over all instances. */
 int64_t lbm_batch_cells(const lbm_batch_t* b);
+/* Node counts of instance k (its descriptor's nx, ny).  Host-only.
+ * LBM_EINVAL for a NULL argument or k out of range. */
+int lbm_batch_get_dims(const lbm_batch_t* b, int32_t k, int32_t* nx, int32_t* ny);
 /* Bytes of ONE population pool (all instances), and of the scratch area
  * (three [ny][nx] double fields of the largest instance + reduction slots). */
 size_t lbm_batch_buffer_bytes(const lbm_batch_t* b);

@@ -736,6 +736,14 @@ void lbm_batch_destroy(lbm_batch_t* b) {
 
 int64_t lbm_batch_cells(const lbm_batch_t* b) { return b ? b->cells : -1; }
 
+int lbm_batch_get_dims(const lbm_batch_t* b, int32_t k, int32_t* nx, int32_t* ny) {
+  if (!b || !nx || !ny) return bfail(LBM_EINVAL, "lbm_batch_get_dims: NULL argument");
+  if (k < 0 || k >= b->count) return bfail(LBM_EINVAL, "lbm_batch_get_dims: instance %d out of range", k);
+  *nx = b->inst[k].nx;
+  *ny = b->inst[k].ny;
+  return LBM_OK;
+}
+
 size_t lbm_batch_buffer_bytes(const lbm_batch_t* b) { return b ? (size_t)b->pool_elems * b->elt : 0; }
 
 size_t lbm_batch_scratch_bytes(const lbm_batch_t* b) {

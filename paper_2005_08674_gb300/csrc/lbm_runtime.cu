@@ -763,6 +763,13 @@ int lbm_step(lbm_t* h, int32_t n) {
 
 int64_t lbm_steps_done(const lbm_t* h) { return h ? h->steps : -1; }
 
+int lbm_get_dims(const lbm_t* h, int32_t* nx, int32_t* ny) {
+  if (!h || !nx || !ny) return fail(LBM_EINVAL, "lbm_get_dims: NULL argument");
+  *nx = h->nx;
+  *ny = h->ny;
+  return LBM_OK;
+}
+
 namespace lbmk {
 void batch_check_read(unsigned long long* count, unsigned long long* first, bool reset);  // lbm_batch.cu
 }

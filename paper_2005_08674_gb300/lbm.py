@@ -47,6 +47,7 @@ _SIGS = {
     "lbm_set_edges": (ctypes.c_int, [_vp, _vp, _vp]),
     "lbm_batch_set_edges": (ctypes.c_int, [_vp, _vp, _vp]),
     "lbm_set_stream": (ctypes.c_int, [_vp, _vp]),
+    "lbm_get_dims": (ctypes.c_int, [_vp, _i32p, _i32p]),
     "lbm_buffer_bytes": (ctypes.c_size_t, [_vp]),
     "lbm_scratch_bytes": (ctypes.c_size_t, [_vp]),
     "lbm_bind": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -77,6 +78,7 @@ _SIGS = {
     "lbm_batch_set_collision": (ctypes.c_int, [_vp, _i32, _dbl, _dbl, _dbl]),
     "lbm_batch_set_stream": (ctypes.c_int, [_vp, _vp]),
     "lbm_batch_cells": (ctypes.c_int64, [_vp]),
+    "lbm_batch_get_dims": (ctypes.c_int, [_vp, _i32, _i32p, _i32p]),
     "lbm_batch_buffer_bytes": (ctypes.c_size_t, [_vp]),
     "lbm_batch_scratch_bytes": (ctypes.c_size_t, [_vp]),
     "lbm_batch_bind": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
@@ -119,8 +121,22 @@ def lbm_check_read(reset: bool = False):
     return bool(rc), int(n.value), int(a.value)
 
 
-def _host(a) -> np.ndarray:
+def _host_in(a, shape, what: str) -> np.ndarray:
+    """A C-contiguous float64 view (or copy) of an input field of `shape`."""
     a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != tuple(shape):
+        raise LbmError(LBM_EINVAL, f"{what}: array of shape {a.shape}, expected {tuple(shape)}")
+    return a
+
+
+def _host_out(a, shape, what: str) -> np.ndarray:
+    """An output array the library writes into: float64, C-contiguous,
+    writeable and of `shape` (no copy is made, so nothing else will do)."""
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous and a.flags.writeable
+            and a.shape == tuple(shape)):
+        got = (a.shape, a.dtype) if isinstance(a, np.ndarray) else type(a).__name__
+        raise LbmError(LBM_EINVAL, f"{what}: needs a writeable C-contiguous float64 array of shape "
+                                   f"{tuple(shape)}, got {got}")
     return a
 
 
@@ -199,9 +215,22 @@ def lbm_bind(h, dev_a: int, dev_b: int, dev_scratch: int):
     return _check(_L.lbm_bind(h, ctypes.c_void_p(dev_a), ctypes.c_void_p(dev_b), ctypes.c_void_p(dev_scratch)))
 
 
+def lbm_get_dims(h):
+    """(nx, ny) of the domain."""
+    nx, ny = ctypes.c_int32(), ctypes.c_int32()
+    _check(_L.lbm_get_dims(h, ctypes.byref(nx), ctypes.byref(ny)))
+    return nx.value, ny.value
+
+
+def _shape(h):
+    nx, ny = lbm_get_dims(h)
+    return ny, nx
+
+
 def lbm_init(h, rho, ux, uy):
     """Host fields [ny][nx] (numpy float64)."""
-    rho, ux, uy = _host(rho), _host(ux), _host(uy)
+    shape = _shape(h)
+    rho, ux, uy = (_host_in(a, shape, "lbm_init") for a in (rho, ux, uy))
     return _check(_L.lbm_init(h, _hp(rho), _hp(ux), _hp(uy)))
 
 
@@ -218,8 +247,8 @@ def lbm_steps_done(h) -> int:
 
 
 def lbm_get_macros(h, rho: np.ndarray, ux: np.ndarray, uy: np.ndarray):
-    for a in (rho, ux, uy):
-        assert a.dtype == np.float64 and a.flags.c_contiguous
+    shape = _shape(h)
+    rho, ux, uy = (_host_out(a, shape, "lbm_get_macros") for a in (rho, ux, uy))
     return _check(_L.lbm_get_macros(h, _hp(rho), _hp(ux), _hp(uy)))
 
 
@@ -229,12 +258,12 @@ def lbm_get_macros_device(h, d_rho: int, d_ux: int, d_uy: int):
 
 
 def lbm_get_populations(h, f: np.ndarray):
-    assert f.dtype == np.float64 and f.flags.c_contiguous
+    f = _host_out(f, (9,) + _shape(h), "lbm_get_populations")
     return _check(_L.lbm_get_populations(h, _hp(f)))
 
 
 def lbm_set_populations(h, f):
-    f = _host(f)
+    f = _host_in(f, (9,) + _shape(h), "lbm_set_populations")
     return _check(_L.lbm_set_populations(h, _hp(f)))
 
 
@@ -376,10 +405,20 @@ class Simulation:
         lbm_init(self.h, rho, ux, uy)
         return self
 
+    def _device_dense(self, t, shape, what):
+        """t must be a contiguous float64 tensor of `shape` on this domain's device."""
+        import torch
+        if not (isinstance(t, torch.Tensor) and t.device == self._a.device and t.dtype == torch.float64
+                and t.is_contiguous() and tuple(t.shape) == tuple(shape)):
+            got = (tuple(t.shape), t.dtype, str(t.device)) if isinstance(t, torch.Tensor) else type(t).__name__
+            raise LbmError(LBM_EINVAL, f"{what}: needs a contiguous float64 tensor of shape {tuple(shape)} "
+                                       f"on {self._a.device}, got {got}")
+        return t
+
     def init_device(self, rho, ux, uy):
         """torch float64 CUDA tensors [ny][nx]."""
         for t in (rho, ux, uy):
-            assert t.is_cuda and t.is_contiguous() and t.dtype.itemsize == 8
+            self._device_dense(t, (self.ny, self.nx), "init_device")
         lbm_init_device(self.h, rho.data_ptr(), ux.data_ptr(), uy.data_ptr())
         return self
 
@@ -402,6 +441,7 @@ class Simulation:
         import torch
         if out is None:
             out = torch.empty((3, self.ny, self.nx), dtype=torch.float64, device=self._a.device)
+        self._device_dense(out, (3, self.ny, self.nx), "macros_device")
         lbm_get_macros_device(self.h, out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr())
         return out
 
@@ -418,7 +458,18 @@ class Simulation:
         """ref: None or a float64 CUDA tensor [3, H, W] whose [:, 0, 0] lines up with node (0, 0)."""
         if ref is None:
             return lbm_reduce(self.h, allow_unstable=allow_unstable)
+        import torch
+        if not (isinstance(ref, torch.Tensor) and ref.device == self._a.device and ref.dtype == torch.float64
+                and ref.dim() == 3 and ref.shape[0] >= 3 and ref.stride(-1) == 1):
+            raise LbmError(LBM_EINVAL, "reduce: ref must be a float64 tensor [3, H, W] with unit stride along W "
+                                       f"on {self._a.device}")
         pitch = ref_pitch or ref.stride(-2)
+        span = (self.ny - 1) * pitch + self.nx  # elements read from the start of each ref plane
+        for c in range(3):
+            avail = ref[c].untyped_storage().nbytes() // 8 - ref[c].storage_offset()
+            if pitch < self.nx or avail < span:
+                raise LbmError(LBM_EINVAL, f"reduce: ref plane {c} holds {avail} elements from its start, "
+                                           f"{self.ny} rows of pitch {pitch} need {span} (pitch >= {self.nx})")
         return lbm_reduce(self.h, ref[0].data_ptr(), ref[1].data_ptr(), ref[2].data_ptr(), pitch,
                           allow_unstable=allow_unstable)
 
@@ -503,8 +554,16 @@ def lbm_batch_bind(b, dev_a: int, dev_b: int, dev_scratch: int):
     return _check(_L.lbm_batch_bind(b, ctypes.c_void_p(dev_a), ctypes.c_void_p(dev_b), ctypes.c_void_p(dev_scratch)))
 
 
+def lbm_batch_get_dims(b, k):
+    """(nx, ny) of instance k."""
+    nx, ny = ctypes.c_int32(), ctypes.c_int32()
+    _check(_L.lbm_batch_get_dims(b, int(k), ctypes.byref(nx), ctypes.byref(ny)))
+    return nx.value, ny.value
+
+
 def lbm_batch_init(b, k, rho, ux, uy):
-    rho, ux, uy = _host(rho), _host(ux), _host(uy)
+    nx, ny = lbm_batch_get_dims(b, k)
+    rho, ux, uy = (_host_in(a, (ny, nx), "lbm_batch_init") for a in (rho, ux, uy))
     return _check(_L.lbm_batch_init(b, int(k), _hp(rho), _hp(ux), _hp(uy)))
 
 
@@ -517,8 +576,8 @@ def lbm_batch_steps_done(b) -> int:
 
 
 def lbm_batch_get_macros(b, k, rho, ux, uy):
-    for a in (rho, ux, uy):
-        assert a.dtype == np.float64 and a.flags.c_contiguous
+    nx, ny = lbm_batch_get_dims(b, k)
+    rho, ux, uy = (_host_out(a, (ny, nx), "lbm_batch_get_macros") for a in (rho, ux, uy))
     return _check(_L.lbm_batch_get_macros(b, int(k), _hp(rho), _hp(ux), _hp(uy)))
 
 

@@ -85,3 +85,46 @@ def test_ordinary_build_reports_no_checker(lib_path):
     if lbm.CHECKED:
         pytest.skip("the bounds-checked library is loaded")
     assert lbm.lbm_check_read() == (False, 0, 0)
+
+
+def test_dims_and_host_array_checks(lib_path):
+    """The binding sizes every host array from lbm_get_dims / lbm_batch_get_dims
+    and refuses a wrong shape, dtype or layout before the library reads or
+    writes a byte (these checks run on the host, without a GPU)."""
+    import numpy as np
+    from paper_2005_08674_gb300 import lbm
+    h = lbm.lbm_create(37, 11, 0.6)
+    try:
+        assert lbm.lbm_get_dims(h) == (37, 11)
+        good = np.ones((11, 37))
+        for bad in (np.ones((11, 36)), np.ones((37, 11)), np.ones(11 * 37)):
+            with pytest.raises(lbm.LbmError, match="shape"):
+                lbm.lbm_init(h, bad, good, good)
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_get_macros(h, good, good, np.ones((11, 37), dtype=np.float32))
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_get_macros(h, good, good, np.ones((37, 11)).T)  # not C-contiguous
+        ro = np.ones((11, 37))
+        ro.flags.writeable = False
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_get_macros(h, good, good, ro)
+        with pytest.raises(lbm.LbmError, match="shape"):
+            lbm.lbm_set_populations(h, np.ones((8, 11, 37)))
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_get_populations(h, np.ones((11, 37)))
+    finally:
+        lbm.lbm_destroy(h)
+    with pytest.raises(lbm.LbmError):
+        lbm.lbm_get_dims(None)
+    b = lbm.lbm_batch_create([(5, 7, 0.6, 1.0, 0.0, 0.0), (64, 3, 0.7, 1.0, 0.01, 0.0)], "f32")
+    try:
+        assert lbm.lbm_batch_get_dims(b, 0) == (5, 7)
+        assert lbm.lbm_batch_get_dims(b, 1) == (64, 3)
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_batch_get_dims(b, 2)
+        with pytest.raises(lbm.LbmError, match="shape"):
+            lbm.lbm_batch_init(b, 1, np.ones((7, 5)), np.ones((3, 64)), np.ones((3, 64)))
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_batch_get_macros(b, 0, np.ones((7, 5)), np.ones((7, 5)), np.ones((5, 7)))
+    finally:
+        lbm.lbm_batch_destroy(b)

@@ -30,6 +30,9 @@ int main(void) {
   if (lbm_set_staged(h, 3) != LBM_OK || lbm_get_staged(h) != 3) return 10;
   if (lbm_set_fused(h, 1) != LBM_OK || lbm_get_fused(h) != 1 || lbm_get_staged(h) != 0) return 11;
   if (lbm_steps_done(h) != 0) return 12;
+  int32_t nx = 0, ny = 0;
+  if (lbm_get_dims(h, &nx, &ny) != LBM_OK || nx != 200 || ny != 100) return 13;
+  if (lbm_get_dims(h, NULL, &ny) != LBM_EINVAL) return 14;
   lbm_destroy(h);
   lbm_destroy(NULL);
   printf("ok\n");
