@@ -463,6 +463,9 @@ class Simulation:
                 and ref.dim() == 3 and ref.shape[0] >= 3 and ref.stride(-1) == 1):
             raise LbmError(LBM_EINVAL, "reduce: ref must be a float64 tensor [3, H, W] with unit stride along W "
                                        f"on {self._a.device}")
+        if ref_pitch is None and (ref.shape[1] < self.ny or ref.shape[2] < self.nx):
+            raise LbmError(LBM_EINVAL, f"reduce: ref of shape {tuple(ref.shape)} does not cover the "
+                                       f"{self.ny} x {self.nx} domain")
         pitch = ref_pitch or ref.stride(-2)
         span = (self.ny - 1) * pitch + self.nx  # elements read from the start of each ref plane
         for c in range(3):

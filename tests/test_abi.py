@@ -128,3 +128,30 @@ def test_dims_and_host_array_checks(lib_path):
             lbm.lbm_batch_get_macros(b, 0, np.ones((7, 5)), np.ones((7, 5)), np.ones((5, 7)))
     finally:
         lbm.lbm_batch_destroy(b)
+
+
+def test_simulation_checks_reference_tensors_on_the_host(lib_path):
+    """Simulation.reduce refuses a reference field that does not cover the
+    domain or whose planes end before the last row the kernel would read,
+    before any call reaches the library (CPU tensors stand in for device
+    ones; the object is built without a device)."""
+    import torch
+    from paper_2005_08674_gb300 import lbm
+    s = lbm.Simulation.__new__(lbm.Simulation)
+    s.nx, s.ny, s.h = 20, 10, None
+    s._a = torch.empty(1, dtype=torch.uint8)
+    f64 = dict(dtype=torch.float64)
+    bad = [(torch.zeros(3, 9, 24, **f64), {}), (torch.zeros(3, 10, 19, **f64), {}),
+           (torch.zeros(3, 10, 24), {}), (torch.zeros(10, 24, **f64), {}),
+           (torch.zeros(3, 30, 40, **f64)[:, 5:, 35:], {}),
+           (torch.zeros(3, 10, 24, **f64), dict(ref_pitch=10)), (torch.zeros(3, 10, 24, **f64), dict(ref_pitch=30))]
+    for ref, kw in bad:
+        with pytest.raises(lbm.LbmError, match="reduce: ref"):
+            s.reduce(ref, **kw)
+    # a well-formed reference (a padded pitch, or a window of a larger field)
+    # passes the checks and reaches the library, which refuses the NULL handle
+    for ref in (torch.zeros(3, 10, 24, **f64), torch.zeros(3, 30, 40, **f64)[:, 5:, 7:]):
+        with pytest.raises(lbm.LbmError, match="lbm_reduce: NULL"):
+            s.reduce(ref)
+    with pytest.raises(lbm.LbmError, match="init_device"):
+        s.init_device(*(torch.zeros(20, 10, **f64),) * 3)
