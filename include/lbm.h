@@ -118,8 +118,9 @@ int lbm_set_precision(lbm_t* h, int32_t storage);
 int lbm_set_stream(lbm_t* h, void* cuda_stream);
 
 /* Node counts of the domain as given to lbm_create, so that a caller or a
- * binding can size the [ny][nx] arrays the other calls read and write.
- * Host-only.  LBM_EINVAL for a NULL argument. */
+ * binding can size the [ny][nx] arrays the other calls read and write (a
+ * library service; the paper has no counterpart).  Host-only.  LBM_EINVAL
+ * for a NULL argument. */
 int lbm_get_dims(const lbm_t* h, int32_t* nx, int32_t* ny);
 
 /* Bytes of ONE population buffer: 9 planes of ny rows of `pitch` elements
