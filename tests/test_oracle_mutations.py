@@ -35,6 +35,10 @@ MUTATIONS = {
     "correction_ignores_kappa": ("(drho + s->kappa * (CX[i] * djx", "(drho + 1.0 * (CX[i] * djx"),
     "second_order_stencil_sign": ("(3.0 * mb[c] - 4.0 * m1[c] + m2[c])", "(3.0 * mb[c] - 4.0 * m1[c] - m2[c])"),
     "mrt_gram_schmidt_skips_projection": ("v[i] -= num / den * s->M[b][i];", "v[i] -= 0.0 * num / den * s->M[b][i];"),
+    "mrt_inverse_not_normalised": ("s->Minv[i][a] = s->M[a][i] / n2;", "s->Minv[i][a] = s->M[a][i];"),
+    "mrt_inverse_transposed": ("d += s->Minv[i][a] * r[a];", "d += s->Minv[a][i] * r[a];"),
+    "mrt_relaxes_away_from_equilibrium": ("r[a] = s->mrt_s[a] * (m[a] - meq[a]);",
+                                          "r[a] = s->mrt_s[a] * (meq[a] - m[a]);"),
     "velocity_edge_ignored": ("      mc[1] = s->uw[side][0];", "      mc[1] = mc[1];"),
     "velocity_edge_axes_swapped": ("      mc[2] = s->uw[side][1];", "      mc[2] = s->uw[side][0];"),
 }
