@@ -44,6 +44,17 @@ MUTATIONS = {
 }
 
 
+# mistakes in the storage emulation (a test instrument of the oracle), caught
+# by its own pins in test_oracle_storage.py
+STORAGE_MUTATIONS = {
+    "bf16_truncates": ("b += 0x7fffu + ((b >> 16) & 1u);", "b += 0u;"),
+    "f16_unscaled": ("(double)(_Float16)(float)(v * 4096.0) / 4096.0", "(double)(_Float16)(float)(v)"),
+    "rounds_absolute_populations": ("F(s, buf, i, x, y) = r[i] + q_store(F(s, buf, i, x, y) - r[i], s->store_fmt);",
+                                    "F(s, buf, i, x, y) = q_store(F(s, buf, i, x, y), s->store_fmt);"),
+    "far_field_shift_ignored": ("  if (s->store_ff)\n    or_equilibrium", "  if (0)\n    or_equilibrium"),
+}
+
+
 @pytest.fixture(scope="module")
 def source():
     return open(SRC).read()
@@ -51,7 +62,16 @@ def source():
 
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_planted_mistake_fails_a_pin(name, source, tmp_path):
-    old, new = MUTATIONS[name]
+    _planted_mistake_fails(MUTATIONS, name, source, tmp_path, "test_oracle_pins.py")
+
+
+@pytest.mark.parametrize("name", sorted(STORAGE_MUTATIONS))
+def test_planted_storage_mistake_fails_a_pin(name, source, tmp_path):
+    _planted_mistake_fails(STORAGE_MUTATIONS, name, source, tmp_path, "test_oracle_storage.py")
+
+
+def _planted_mistake_fails(table, name, source, tmp_path, pins):
+    old, new = table[name]
     assert source.count(old) == 1, f"mutation anchor for {name} not unique"
     mutated = tmp_path / "lbm_oracle_mut.c"
     mutated.write_text(source.replace(old, new))
@@ -60,6 +80,6 @@ def test_planted_mistake_fails_a_pin(name, source, tmp_path):
                            str(mutated), "-lm"])
     env = dict(os.environ, LBM_ORACLE_LIB=str(so))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", pins)],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"no pin caught mutation {name}:\n{r.stdout[-2000:]}"
