@@ -155,3 +155,21 @@ def test_simulation_checks_reference_tensors_on_the_host(lib_path):
             s.reduce(ref)
     with pytest.raises(lbm.LbmError, match="init_device"):
         s.init_device(*(torch.zeros(20, 10, **f64),) * 3)
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """With the CUDA library absent the binding refuses to import: there is no
+    CPU path to fall back to.  (A copy of the binding in a package with no
+    library beside it, imported in a child process.)"""
+    import shutil
+    import subprocess
+    import sys
+    pkg = tmp_path / "paper_2005_08674_gb300"
+    pkg.mkdir()
+    (pkg / "__init__.py").write_text("")
+    shutil.copy(os.path.join(ROOT, "paper_2005_08674_gb300", "lbm.py"), pkg / "lbm.py")
+    r = subprocess.run([sys.executable, "-c", "import paper_2005_08674_gb300.lbm"], cwd=tmp_path,
+                       capture_output=True, text=True, timeout=300,
+                       env={k: v for k, v in os.environ.items() if k not in ("PYTHONPATH", "LBM_CHECKED")})
+    assert r.returncode != 0
+    assert "ImportError" in r.stderr and "is not built" in r.stderr, r.stderr[-1000:]
