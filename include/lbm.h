@@ -177,7 +177,9 @@ int lbm_set_populations(lbm_t* h, const double* f);
  * (lbm_buffer_bytes() bytes, the handle's storage type and layout) to or
  * from HOST memory, with the step count.  A state loaded into a handle of
  * the same size, storage and parameters continues bit for bit like the run
- * it was saved from.  Both synchronise. */
+ * it was saved from.  Both synchronise.  LBM_EINVAL for a NULL argument, a
+ * byte count other than lbm_buffer_bytes(), or (load) a negative step
+ * count; LBM_ESTATE for a save before lbm_init. */
 int lbm_save_state(lbm_t* h, void* host, size_t bytes, int64_t* steps);
 int lbm_load_state(lbm_t* h, const void* host, size_t bytes, int64_t steps);
 

@@ -875,6 +875,7 @@ int lbm_load_state(lbm_t* h, const void* host, size_t bytes, int64_t steps) {
   if (!h || !host) return fail(LBM_EINVAL, "lbm_load_state: NULL argument");
   if (bytes != lbm_buffer_bytes(h))
     return fail(LBM_EINVAL, "lbm_load_state: %zu bytes given, the state is %zu", bytes, lbm_buffer_bytes(h));
+  if (steps < 0) return fail(LBM_EINVAL, "lbm_load_state: step count %lld < 0", (long long)steps);
   int rc = ensure_memory(h);
   if (rc) return rc;
   h->cur = 0;

@@ -72,6 +72,11 @@ def test_host_side_argument_checks(lib_path):
         assert lbm.lbm_get_staged(h) == 3
         lbm.lbm_set_launch(h, 128, 1, 0)  # back to the kernel pair
         assert lbm.lbm_get_staged(h) == 0
+        import numpy as np
+        with pytest.raises(lbm.LbmError, match="bytes given"):
+            lbm.lbm_load_state(h, np.zeros(100, dtype=np.uint8), 0)
+        with pytest.raises(lbm.LbmError, match="step count"):
+            lbm.lbm_load_state(h, np.zeros(lbm.lbm_buffer_bytes(h), dtype=np.uint8), -1)
         lbm.lbm_status(h)  # nothing launched yet: OK without touching the device
         assert lbm.lbm_steps_done(h) == 0
     finally:
