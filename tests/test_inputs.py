@@ -74,3 +74,31 @@ def test_plane_wave_peak_and_direction():
     s = rho60 - 1.0
     assert np.allclose(ux60, inputs.CS * s * 0.5, atol=1e-15)
     assert np.allclose(uy60, inputs.CS * s * math.sqrt(3) / 2, atol=1e-15)
+
+
+def test_batch_recipe():
+    """256 instances: sides uniform in [64, 1024], tau in [0.51, 0.8], even k a
+    centred pulse (amplitude log-uniform in [1e-4, 1e-2], HWHM min side / 20),
+    odd k a vortex in a stream of Mach 0.05..0.15 (swirl half the stream speed,
+    R_c = max(4, min side / 20), centre (nx / 4, ny / 2)); each instance draws
+    from its own SplitMix64 stream, so instance k does not depend on the count."""
+    ws = inputs.batch_instances()
+    assert len(ws) == 256
+    for k, w in enumerate(ws):
+        assert 64 <= w.nx <= 1024 and 64 <= w.ny <= 1024
+        assert 0.51 <= w.tau < 0.8
+        m = min(w.nx, w.ny)
+        if k % 2 == 0:
+            assert w.kind == "pulse" and w.farfield_u == (0.0, 0.0)
+            assert 1e-4 <= w.params["amplitude"] < 1e-2
+            assert w.params["half_width"] == m / 20.0
+            assert w.params["centres"] == [((w.nx - 1) / 2.0, (w.ny - 1) / 2.0)]
+        else:
+            u0 = w.params["u0"]
+            assert w.kind == "vortex" and w.farfield_u == (u0, 0.0)
+            assert 0.05 * inputs.CS <= u0 < 0.15 * inputs.CS
+            assert w.params["beta_u0"] == 0.5 * u0 and w.params["rc"] == max(4.0, m / 20.0)
+            assert (w.params["x0"], w.params["y0"]) == (w.nx / 4.0, w.ny / 2.0)
+    assert len({(w.nx, w.ny) for w in ws}) > 200  # uneven sizes
+    few = inputs.batch_instances(count=5)
+    assert [(w.nx, w.ny, w.tau) for w in few] == [(w.nx, w.ny, w.tau) for w in ws[:5]]
