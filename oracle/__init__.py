@@ -57,6 +57,7 @@ def lib(openmp: bool = False):
             L.or_set_nsbc.argtypes = [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_int]
             L.or_set_periodic.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+            L.or_set_corner_mode.argtypes = [ctypes.c_void_p, ctypes.c_int]
             L.or_set_velocity_edge.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                                ctypes.c_double]
             L.or_set_collision.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
@@ -103,8 +104,11 @@ class Oracle:
     def __init__(self, nx: int, ny: int, tau: float, farfield_rho: float = 1.0,
                  farfield_u=(0.0, 0.0), gamma: float = 0.6, beta: float = 0.0,
                  kappa: float = 3.0, grad_order: int = 1, periodic=(False, False),
-                 collision: str = "bgk", mrt_rates=None, openmp: bool = False, velocity_edges=None):
-        """velocity_edges: {side: (ux, uy)} with side 0 left, 1 right, 2 bottom, 3 top."""
+                 collision: str = "bgk", mrt_rates=None, openmp: bool = False, velocity_edges=None,
+                 corner_mode: int = 0):
+        """velocity_edges: {side: (ux, uy)} with side 0 left, 1 right, 2 bottom, 3 top.
+        corner_mode: 0 = diagonal normal at corners, 1 = mean of the m_c the two
+        edges meeting at the corner predict (readings of Sec. 5, silent on corners)."""
         self._L = lib(openmp)
         h = self._L.or_create(nx, ny, tau, farfield_rho, farfield_u[0], farfield_u[1])
         if not h:
@@ -112,6 +116,7 @@ class Oracle:
         self._h = ctypes.c_void_p(h)
         self.nx, self.ny, self.tau = nx, ny, tau
         self._L.or_set_nsbc(self._h, gamma, beta, kappa, grad_order)
+        self._L.or_set_corner_mode(self._h, int(corner_mode))
         self._L.or_set_periodic(self._h, int(periodic[0]), int(periodic[1]))
         for side, (vx, vy) in (velocity_edges or {}).items():
             self._L.or_set_velocity_edge(self._h, int(side), 1, float(vx), float(vy))

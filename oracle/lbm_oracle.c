@@ -33,7 +33,11 @@
  *     the domain, moments taken from the step-n state:
  *       order 1: d_n m = (m_b - m_{b-n}) / |n|
  *       order 2: d_n m = (3 m_b - 4 m_{b-n} + m_{b-2n}) / (2 |n|)
- *     Corner nodes use the diagonal normal, |n| = sqrt(2).
+ *     Corner nodes (the paper says nothing about them) take one of two
+ *     readings, chosen by corner_mode:
+ *       0 (default): the diagonal normal, |n| = sqrt(2), one prediction;
+ *       1: the mean of the two blended states m_c (Eq. nes_3) that the two
+ *          edges meeting there would predict, each along its own unit normal.
  *   - m = (rho, u_x, u_y): density and velocity are predicted and blended,
  *     not momentum.
  *   - incoming = populations whose pull source lies outside the domain;
@@ -78,6 +82,7 @@ typedef struct or_sim {
   double beta;        /* far-field factor, Eq. (nes_3) */
   double kappa;       /* momentum factor of the correction, Eq. (nes_4) */
   int grad_order;     /* 1 or 2: one-sided difference order for d_n m */
+  int corner_mode;    /* 0: diagonal normal at corners; 1: mean of the two edges' m_c */
   int periodic[2];    /* periodic axes (x, y) instead of NSBC edges */
   int velocity[4];    /* edges (left, right, bottom, top) with a prescribed velocity */
   double uw[4][2];    /* that velocity */
@@ -151,21 +156,12 @@ static void collide_mrt(const or_sim* s, double g[9]) {
   }
 }
 
-/* Sec. 5: fill the unknown populations of edge node (x, y), then correct. */
-static void nsbc(const or_sim* s, int x, int y, double g[9], const int known[9]) {
-  int nxn = 0, nyn = 0; /* outward normal */
-  if (!s->periodic[0]) {
-    if (x == 0) nxn = -1;
-    else if (x == s->nx - 1) nxn = 1;
-  }
-  if (!s->periodic[1]) {
-    if (y == 0) nyn = -1;
-    else if (y == s->ny - 1) nyn = 1;
-  }
+/* Eqs. (nes_2), (nes_3) at node (x, y) for the outward normal (nxn, nyn):
+ * m_p = m - gamma d_n m with a one-sided difference into the domain, then
+ * the far-field criterion m_c = (1 - beta) m_p + beta m_0. */
+static void predict_blend(const or_sim* s, int x, int y, int nxn, int nyn, double mc[3]) {
   const double len = sqrt((double)(nxn * nxn + nyn * nyn));
-
-  /* Eq. (nes_2): m_p = m - gamma d_n m, one-sided difference into the domain */
-  double mb[3], m1[3], m2[3], mp[3], mc[3];
+  double mb[3], m1[3], m2[3], mp[3];
   node_moments(s, x, y, mb);
   node_moments(s, x - nxn, y - nyn, m1);
   if (s->grad_order == 2) node_moments(s, x - 2 * nxn, y - 2 * nyn, m2);
@@ -177,8 +173,31 @@ static void nsbc(const or_sim* s, int x, int y, double g[9], const int known[9])
       dn = (mb[c] - m1[c]) / len;
     mp[c] = mb[c] - s->gamma * dn;
   }
-  /* Eq. (nes_3): far-field criterion */
   for (int c = 0; c < 3; ++c) mc[c] = (1.0 - s->beta) * mp[c] + s->beta * s->m0[c];
+}
+
+/* Sec. 5: fill the unknown populations of edge node (x, y), then correct. */
+static void nsbc(const or_sim* s, int x, int y, double g[9], const int known[9]) {
+  int nxn = 0, nyn = 0; /* outward normal */
+  if (!s->periodic[0]) {
+    if (x == 0) nxn = -1;
+    else if (x == s->nx - 1) nxn = 1;
+  }
+  if (!s->periodic[1]) {
+    if (y == 0) nyn = -1;
+    else if (y == s->ny - 1) nyn = 1;
+  }
+
+  double mc[3];
+  if (s->corner_mode == 1 && nxn != 0 && nyn != 0) {
+    /* a corner: the mean of what the vertical and the horizontal edge predict */
+    double mx[3], my[3];
+    predict_blend(s, x, y, nxn, 0, mx);
+    predict_blend(s, x, y, 0, nyn, my);
+    for (int c = 0; c < 3; ++c) mc[c] = 0.5 * (mx[c] + my[c]);
+  } else {
+    predict_blend(s, x, y, nxn, nyn, mc);
+  }
 
   /* A velocity (Dirichlet) edge: the paper only cites its scheme.  Reading
    * taken: the same reconstruction with the velocity of m_c replaced by the
@@ -304,6 +323,9 @@ void or_set_nsbc(or_sim* s, double gamma, double beta, double kappa, int grad_or
   s->kappa = kappa;
   s->grad_order = grad_order == 2 ? 2 : 1;
 }
+
+/* corner reading: 0 diagonal normal, 1 mean of the two adjacent edges' m_c */
+void or_set_corner_mode(or_sim* s, int mode) { s->corner_mode = mode == 1 ? 1 : 0; }
 
 void or_set_periodic(or_sim* s, int px, int py) {
   s->periodic[0] = px != 0;

@@ -4,9 +4,10 @@ plain Python loops from the paper's definitions (Sec. 3 pull streaming
 Eq. lbe_0 and BGK Eqs. lbe_1/feq_1; Sec. 4 MRT Eq. mrt_lbe with the moment
 basis of Eq. mrt_rm, inverted numerically here; Sec. 5 NSBC Eqs.
 nes_0..nes_4) and the readings the oracle states (outward one-sided normal
-difference, diagonal corner normals of length sqrt(2), both equilibria of the
-mirror at m_c, a doubly unknown pair set to equilibrium, correction factor
-kappa, left/right velocity edges winning at corners).  It shares nothing with
+difference, at a corner either the diagonal normal of length sqrt(2) or the
+mean of the two edges' predictions, both equilibria of the mirror at m_c, a
+doubly unknown pair set to equilibrium, correction factor kappa, left/right
+velocity edges winning at corners).  It shares nothing with
 the oracle but the lattice table of Fig. 1 (read from tests/golden).
 
 4x4, 5x3 and 6x5 grids are almost all boundary: every corner and edge rule
@@ -64,9 +65,23 @@ def mrt_matrix():
     return np.array(rows)
 
 
-def brute_step(f, nx, ny, tau, m0, gamma, beta, kappa, order, periodic=(False, False), vel=None, rates=None):
+def brute_step(f, nx, ny, tau, m0, gamma, beta, kappa, order, periodic=(False, False), vel=None, rates=None,
+               corner_mode=0):
     """One step on f[(x, y)] = list of 9 populations; returns the new dict."""
     vel = vel or {}
+
+    def predicted(x, y, nxn, nyn):
+        """m_c of Eqs. nes_2 and nes_3 at (x, y) for the outward normal (nxn, nyn)."""
+        length = math.sqrt(nxn * nxn + nyn * nyn)
+        mb = moments(f[x, y])
+        m1 = moments(f[x - nxn, y - nyn])
+        if order == 1:
+            dn = [(mb[k] - m1[k]) / length for k in range(3)]
+        else:
+            m2 = moments(f[x - 2 * nxn, y - 2 * nyn])
+            dn = [(3 * mb[k] - 4 * m1[k] + m2[k]) / (2 * length) for k in range(3)]
+        mp = [mb[k] - gamma * dn[k] for k in range(3)]
+        return [(1 - beta) * mp[k] + beta * m0[k] for k in range(3)]
 
     def inside(x, y):
         return 0 <= x < nx and 0 <= y < ny
@@ -95,16 +110,11 @@ def brute_step(f, nx, ny, tau, m0, gamma, beta, kappa, order, periodic=(False, F
         nyn = 0 if periodic[1] else (-1 if y == 0 else (1 if y == ny - 1 else 0))
         if nxn == 0 and nyn == 0:
             continue
-        length = math.sqrt(nxn * nxn + nyn * nyn)
-        mb = moments(f[x, y])
-        m1 = moments(f[x - nxn, y - nyn])
-        if order == 1:
-            dn = [(mb[k] - m1[k]) / length for k in range(3)]
+        if corner_mode == 1 and nxn != 0 and nyn != 0:
+            # a corner read as the mean of its two edges' predictions
+            mc = [(a + b) / 2 for a, b in zip(predicted(x, y, nxn, 0), predicted(x, y, 0, nyn))]
         else:
-            m2 = moments(f[x - 2 * nxn, y - 2 * nyn])
-            dn = [(3 * mb[k] - 4 * m1[k] + m2[k]) / (2 * length) for k in range(3)]
-        mp = [mb[k] - gamma * dn[k] for k in range(3)]
-        mc = [(1 - beta) * mp[k] + beta * m0[k] for k in range(3)]
+            mc = predicted(x, y, nxn, nyn)
         side = next((s for s, hit in ((0, x == 0), (1, x == nx - 1), (2, y == 0), (3, y == ny - 1))
                      if hit and s in vel), None)
         if side is not None:
@@ -162,10 +172,14 @@ CASES = [
     dict(nx=6, ny=4, tau=0.75, gamma=0.3, beta=0.0, kappa=3.0, order=2, periodic=(True, False)),
     dict(nx=6, ny=5, tau=0.66, gamma=0.6, beta=0.0, kappa=3.0, order=1, vel={0: (0.05, 0.01), 2: (0.02, 0.0)}),
     dict(nx=5, ny=5, tau=0.6, gamma=0.6, beta=0.05, kappa=3.0, order=1, rates=(1.4, 1.4, 1.2)),
+    dict(nx=4, ny=5, tau=0.7, gamma=0.6, beta=0.1, kappa=3.0, order=1, corner_mode=1),
+    dict(nx=6, ny=5, tau=0.8, gamma=0.45, beta=0.0, kappa=1.0, order=2, corner_mode=1),
+    dict(nx=6, ny=5, tau=0.66, gamma=0.6, beta=0.0, kappa=3.0, order=1, corner_mode=1,
+         vel={0: (0.05, 0.01), 2: (0.02, 0.0)}),
 ]
 
 
-@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c['nx']}x{c['ny']}")
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c['nx']}x{c['ny']}-corner{c.get('corner_mode', 0)}")
 def test_oracle_matches_brute_force(case):
     case = dict(case)
     nx, ny, tau = case.pop("nx"), case.pop("ny"), case.pop("tau")
@@ -174,8 +188,9 @@ def test_oracle_matches_brute_force(case):
     mrt = case.get("rates")
     m0 = (1.002, 0.03, -0.01)
     fields = _fields(nx, ny, nx * 10 + ny)
+    corner_mode = case.get("corner_mode", 0)
     kw = dict(gamma=case["gamma"], beta=case["beta"], kappa=case["kappa"], grad_order=case["order"],
-              periodic=periodic, velocity_edges=vel)
+              periodic=periodic, velocity_edges=vel, corner_mode=corner_mode)
     rates9 = None
     if mrt:
         e, eps, q = mrt
@@ -185,7 +200,7 @@ def test_oracle_matches_brute_force(case):
     f = _to_dict(o.get_f())
     for _ in range(6):
         f = brute_step(f, nx, ny, tau, m0, case["gamma"], case["beta"], case["kappa"], case["order"],
-                       periodic, vel, rates9)
+                       periodic, vel, rates9, corner_mode)
     got = o.step(6).get_f()
     err = float(np.abs(got - _to_array(f, nx, ny)).max())
     assert err < 1e-13, err

@@ -39,6 +39,9 @@ MUTATIONS = {
     "mrt_inverse_transposed": ("d += s->Minv[i][a] * r[a];", "d += s->Minv[a][i] * r[a];"),
     "mrt_relaxes_away_from_equilibrium": ("r[a] = s->mrt_s[a] * (m[a] - meq[a]);",
                                           "r[a] = s->mrt_s[a] * (meq[a] - m[a]);"),
+    "corner_mean_takes_one_edge_twice": ("mc[c] = 0.5 * (mx[c] + my[c]);", "mc[c] = 0.5 * (mx[c] + mx[c]);"),
+    "corner_mode_ignored": ("if (s->corner_mode == 1 && nxn != 0 && nyn != 0) {", "if (0) {"),
+    "corner_edge_normal_keeps_diagonal": ("predict_blend(s, x, y, nxn, 0, mx);", "predict_blend(s, x, y, nxn, nyn, mx);"),
     "velocity_edge_ignored": ("      mc[1] = s->uw[side][0];", "      mc[1] = mc[1];"),
     "velocity_edge_axes_swapped": ("      mc[2] = s->uw[side][1];", "      mc[2] = s->uw[side][0];"),
 }

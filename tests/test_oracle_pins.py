@@ -167,15 +167,16 @@ def test_sound_speed():
 
 # --- Sec. 5: NSBC -------------------------------------------------------------
 
-@pytest.mark.parametrize("gamma,beta,kappa,order",
-                         [(0.6, 0.0, 3.0, 1), (0.3, 0.4, 3.0, 2), (1.0, 1.0, 1.0, 1), (0.0, 0.1, 3.0, 2)])
-def test_farfield_state_is_invariant(gamma, beta, kappa, order):
+@pytest.mark.parametrize("gamma,beta,kappa,order,corner",
+                         [(0.6, 0.0, 3.0, 1, 0), (0.3, 0.4, 3.0, 2, 0), (1.0, 1.0, 1.0, 1, 0), (0.0, 0.1, 3.0, 2, 0),
+                          (0.6, 0.0, 3.0, 1, 1), (0.3, 0.4, 3.0, 2, 1)])
+def test_farfield_state_is_invariant(gamma, beta, kappa, order, corner):
     """f = f_eq(m0) everywhere is an exact fixed point: the gradient vanishes,
     m_c = m0, the mirrored non-equilibrium part is zero and the correction is zero."""
     m0 = (1.02, 0.04, -0.03)
     nx, ny = 17, 11
     o = oracle.Oracle(nx, ny, 0.6, m0[0], m0[1:], gamma=gamma, beta=beta, kappa=kappa,
-                      grad_order=order)
+                      grad_order=order, corner_mode=corner)
     o.init(*(np.full((ny, nx), v) for v in m0))
     feq = oracle.equilibrium(*m0)
     g = o.step(30).get_f()
@@ -283,6 +284,54 @@ def test_correction_conserves_predicted_moments(gamma, beta):
             assert worst > 1e-6
 
 
+@pytest.mark.parametrize("order", [1, 2])
+def test_corner_mode_mean_of_edge_predictions(order):
+    """The corner reading of corner_mode = 1 (Sec. 5 says nothing about corners):
+    after a step each corner carries exactly the mean of the two states m_c
+    (Eqs. nes_2, nes_3) that the vertical and the horizontal edge through it
+    predict, each along its own unit normal (kappa = 3 makes the correction
+    exact), while the edge nodes next to it are what corner_mode = 0 gives
+    them.  Under corner_mode = 0 the same corner carries the diagonal
+    prediction instead, which differs."""
+    nx, ny, gamma, beta = 13, 9, 0.55, 0.15
+    fields = _smooth_fields(nx, ny, 11)
+    m0 = (1.001, 0.02, 0.01)
+    runs = {}
+    for mode in (0, 1):
+        o = oracle.Oracle(nx, ny, 0.64, m0[0], m0[1:], gamma=gamma, beta=beta, grad_order=order,
+                          corner_mode=mode)
+        o.init(*fields)
+        runs[mode] = (o.macros(), o.step(1).macros())
+    before = runs[1][0]
+
+    def m_c(x, y, n):
+        out = []
+        for c in range(3):
+            mb = before[c][y, x]
+            m1 = before[c][y - n[1], x - n[0]]
+            if order == 1:
+                dn = (mb - m1) / math.hypot(*n)
+            else:
+                m2 = before[c][y - 2 * n[1], x - 2 * n[0]]
+                dn = (3 * mb - 4 * m1 + m2) / (2 * math.hypot(*n))
+            out.append((1 - beta) * (mb - gamma * dn) + beta * m0[c])
+        return out
+
+    for x, y in [(0, 0), (nx - 1, 0), (0, ny - 1), (nx - 1, ny - 1)]:
+        nxn = -1 if x == 0 else 1
+        nyn = -1 if y == 0 else 1
+        mean = [(a + b) / 2 for a, b in zip(m_c(x, y, (nxn, 0)), m_c(x, y, (0, nyn)))]
+        diag = m_c(x, y, (nxn, nyn))
+        for c in range(3):
+            assert abs(runs[1][1][c][y, x] - mean[c]) < 1e-15
+            assert abs(runs[0][1][c][y, x] - diag[c]) < 1e-15
+        assert max(abs(a - b) for a, b in zip(mean, diag)) > 1e-7
+    edge = np.ones((ny, nx), bool)
+    edge[[0, 0, -1, -1], [0, -1, 0, -1]] = False
+    for c in range(3):
+        assert np.array_equal(runs[0][1][c][edge], runs[1][1][c][edge])
+
+
 def test_beta_one_clamps_edge_to_farfield():
     """Eq. nes_3 with beta = 1 gives m_c = m0 whatever the prediction."""
     nx, ny = 11, 13
@@ -310,13 +359,15 @@ def test_second_order_gradient_is_exact_for_quadratic():
     assert abs(r[1, 0] - 1.0) < 1e-15  # zero slope at x = 0
 
 
-def test_centred_pulse_keeps_mirror_symmetries():
+@pytest.mark.parametrize("corner", [0, 1])
+def test_centred_pulse_keeps_mirror_symmetries(corner):
     """A pulse at the exact domain centre stays symmetric under x-mirror, y-mirror
     and transpose once waves have hit every edge and corner: any orientation slip in
-    the edge normals, unknown sets or corner handling breaks this."""
+    the edge normals, unknown sets or corner handling (either corner reading)
+    breaks this."""
     n = 40
     f = inputs.acoustic_pulse(n, n, 1e-3, 4.0, [((n - 1) / 2, (n - 1) / 2)])
-    rho, ux, uy = oracle.Oracle(n, n, 0.55).init(*f).step(120).macros()
+    rho, ux, uy = oracle.Oracle(n, n, 0.55, corner_mode=corner).init(*f).step(120).macros()
     assert np.abs(rho - 1).max() > 1e-7  # mirror images differ only by summation order
     assert np.abs(rho - rho[:, ::-1]).max() < 1e-14
     assert np.abs(rho - rho[::-1, :]).max() < 1e-14
