@@ -73,13 +73,23 @@ void lbm_destroy(lbm_t* h);
 
 /* NSBC parameters (Sec. 5).  gamma: relaxation of the gradient prediction
  * m_p = m - gamma d_n m (Eq. nes_2), d_n a one-sided difference along the
- * outward unit normal with grad_order 1 or 2 points into the domain
- * (corner normals are diagonal).  beta: far-field factor of Eq. nes_3.
- * kappa: momentum factor of the correction of Eq. nes_4,
- * f_i -= w_i (d_rho + kappa c_i . d(rho u)); kappa = 3 makes the corrected
- * node carry exactly rho_c and rho_c u_c, kappa = 1 is the printed formula.
- * Returns LBM_EINVAL for grad_order not in {1, 2} or non-finite values. */
-int lbm_set_nsbc(lbm_t* h, double gamma, double beta, double kappa, int32_t grad_order);
+ * outward unit normal with grad_order 1 or 2 points into the domain.
+ * beta: far-field factor of Eq. nes_3.  kappa: momentum factor of the
+ * correction of Eq. nes_4, f_i -= w_i (d_rho + kappa c_i . d(rho u));
+ * kappa = 3 makes the corrected node carry exactly rho_c and rho_c u_c,
+ * kappa = 1 is the printed formula.  corner_mode: Sec. 5 says nothing about
+ * corner nodes.  LBM_CORNER_DIAGONAL (default) predicts along the diagonal
+ * outward normal (|n| = sqrt 2, points b - n, b - 2n on the diagonal);
+ * LBM_CORNER_MEAN gives the corner the mean of the two blended states m_c
+ * (Eq. nes_3) that the vertical and the horizontal edge through it predict,
+ * each along its own unit normal.  Either way the diagonal pair whose two
+ * members are both unknown gets f^eq(m_c) alone, and Eq. nes_4 then sets the
+ * node's moments.  Host-only; the step graph is recaptured.  Returns
+ * LBM_EINVAL for grad_order not in {1, 2}, an unknown corner_mode or
+ * non-finite values. */
+#define LBM_CORNER_DIAGONAL 0
+#define LBM_CORNER_MEAN 1
+int lbm_set_nsbc(lbm_t* h, double gamma, double beta, double kappa, int32_t corner_mode, int32_t grad_order);
 
 /* Edge types, per side in the order left (x = 0), right (x = nx-1), bottom
  * (y = 0), top (y = ny-1).  LBM_EDGE_NSBC (default): the boundary of Sec. 5.
@@ -173,15 +183,23 @@ int lbm_get_macros_device(lbm_t* h, double* d_rho, double* d_ux, double* d_uy);
 int lbm_get_populations(lbm_t* h, double* f);
 int lbm_set_populations(lbm_t* h, const double* f);
 
-/* Checkpoint / resume: the current population buffer exactly as stored
- * (lbm_buffer_bytes() bytes, the handle's storage type and layout) to or
- * from HOST memory, with the step count.  A state loaded into a handle of
- * the same size, storage and parameters continues bit for bit like the run
- * it was saved from.  Both synchronise.  LBM_EINVAL for a NULL argument, a
- * byte count other than lbm_buffer_bytes(), or (load) a negative step
- * count; LBM_ESTATE for a save before lbm_init. */
+/* Checkpoint / resume (a library service): a record of lbm_state_bytes()
+ * bytes in HOST memory -- a 64-byte header (magic "LBMSTAT1", version,
+ * storage, nx, ny, pitch, step count, far field m0) followed by the current
+ * population buffer exactly as stored (lbm_buffer_bytes() bytes: the
+ * handle's storage type and layout, deviations from f^eq(m0)).  Loading a
+ * record into a handle with the same size, storage and far field continues
+ * bit for bit like the run it was saved from (with the same tau, collision
+ * and NSBC settings; those are the caller's and are not checked), and sets
+ * the step count from the record.  Both synchronise.  LBM_EINVAL for a NULL
+ * argument, a byte count other than lbm_state_bytes(), and (load) a record
+ * that is not this library's, that holds another storage type, size, pitch
+ * or far field (the bytes would mean something else here), or a negative
+ * step count -- all checked before any device work; LBM_ESTATE for a save
+ * before lbm_init. */
+size_t lbm_state_bytes(const lbm_t* h);
 int lbm_save_state(lbm_t* h, void* host, size_t bytes, int64_t* steps);
-int lbm_load_state(lbm_t* h, const void* host, size_t bytes, int64_t steps);
+int lbm_load_state(lbm_t* h, const void* host, size_t bytes);
 
 /* FP64 reductions over all nodes, used for the reflection measure and as an
  * instability check.  Each node's terms are formed in the storage's compute
@@ -263,6 +281,27 @@ int lbm_status(lbm_t* h);
  * staged or the fused form won. */
 int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_rows, double* ms_per_step);
 
+/* Autotuner cache (a library service; the paper has no counterpart).  With
+ * a cache file set, lbm_autotune and lbm_batch_autotune first look up the
+ * key of the problem -- device name, driver and runtime versions, the
+ * library's build id, single domain or batch, storage, collision model,
+ * storage-shift form, and size classes ceil(log2 n) of nx and ny (a batch:
+ * of the instance count and the total nodes) -- and apply the recorded launch
+ * shape without timing; on a miss they time the candidates as usual and then
+ * add the winner to the file.  The file is a small JSON document written by
+ * the library (temporary file renamed over the old one); a missing,
+ * unreadable or malformed file reads as empty, and one that cannot be
+ * written is left as it is, so the cache never makes autotuning fail.
+ * path = NULL turns the cache off.  Until the first call the environment
+ * variable LBM_TUNE_CACHE, if set, names the file.  Process-wide, host-only;
+ * callers that tune from several threads at once should use different
+ * files.  Always LBM_OK. */
+int lbm_set_tune_cache(const char* path);
+/* Lookups that found a usable entry, and autotuner runs that timed the
+ * candidates with the cache on, since the process started.  LBM_EINVAL for
+ * NULL outputs. */
+int lbm_tune_cache_stats(int64_t* hits, int64_t* misses);
+
 /* Allocation-free form of lbm_reduce, for callers that cannot allocate
  * device memory when they need the sums, such as a monitoring hook inside
  * another framework's step loop where that framework owns all device memory
@@ -273,8 +312,9 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
  * inside the library (131,104 bytes, held by every GPU that loads the
  * library until the process exits) instead of the handle's scratch area; the
  * call makes no cudaMalloc, cudaFree or other allocating call.
- * Limit: at most 67,108,864 nodes (8192 x 8192); larger domains get
- * LBM_EINVAL with a message saying so (use lbm_reduce).
+ * The array holds the partial sums of at most 4096 blocks; the reduction
+ * hands whole rows to blocks (min(ny, 4096) of them), so every domain that
+ * lbm_create accepts fits and no size is refused.
  * The first call on a device looks up the array's device address with
  * cudaGetSymbolAddress (once per device, with that device current); make
  * that first call before any stream capture.  All calls on a device share
@@ -308,7 +348,8 @@ lbm_batch_t* lbm_batch_create(int32_t count, const lbm_instance_desc* descs, int
 void lbm_batch_destroy(lbm_batch_t* b);
 /* NSBC parameters (Eqs. nes_2-nes_4) for every instance of the batch: same
  * arguments, ranges and LBM_EINVAL cases as lbm_set_nsbc.  Host-only. */
-int lbm_batch_set_nsbc(lbm_batch_t* b, double gamma, double beta, double kappa, int32_t grad_order);
+int lbm_batch_set_nsbc(lbm_batch_t* b, double gamma, double beta, double kappa, int32_t corner_mode,
+                       int32_t grad_order);
 /* Collision model (LBM_BGK, or LBM_MRT with the rates of Sec. 4) for every
  * instance: same arguments and errors as lbm_set_collision.  Host-only. */
 int lbm_batch_set_collision(lbm_batch_t* b, int32_t model, double omega_e, double omega_eps, double omega_q);
@@ -379,6 +420,17 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
  * the batch was created (the step then left those tiles untouched); LBM_OK
  * otherwise.  Synchronises. */
 int lbm_batch_status(lbm_batch_t* b);
+
+/* Split independent instances over `ranks` processes (one GPU each) so
+ * that every rank steps about the same number of nodes and no data moves
+ * between ranks: the instances, largest first, each go to the rank with the
+ * fewest nodes so far (ties: lower instance index first, lower rank).
+ * Deterministic, so every rank computes the same partition on its own.
+ * cells[k] = nodes of instance k (nx * ny); writes rank_of[k] in
+ * [0, ranks).  Host-only (a library service for sharding the batched mode;
+ * the paper has no counterpart).  LBM_EINVAL for count < 0, ranks < 1, NULL
+ * arrays or a negative node count. */
+int lbm_partition_instances(int32_t count, const int64_t* cells, int32_t ranks, int32_t* rank_of);
 
 /* Failure-detection check of the bounded device-side wait used by the
  * shared-memory path: one block waits on an mbarrier that nothing arrives

@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import glob
+import hashlib
 import os
 import shutil
 import subprocess
@@ -48,6 +49,18 @@ def _stale(lib: str = LIB) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def build_id() -> str:
+    """Hash of the library's sources: part of the autotuner cache's key, so
+    that choices recorded by another build of the kernels are not reused."""
+    h = hashlib.sha256()
+    for path in sorted(glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(INCLUDE, "*.h"))):
+        if path.endswith((".cu", ".cuh", ".h")):
+            h.update(os.path.basename(path).encode())
+            with open(path, "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, check: bool = False) -> str:
     """Build liblbm.so (or, with check=True, the bounds-checked liblbm_check.so)."""
     lib, bdir = (LIB_CHECK, BUILD_DIR_CHECK) if check else (LIB, BUILD_DIR)
@@ -59,6 +72,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, 
     # NVVM optimiser at -O1 (ptxas keeps -O3), which cuts its compile time about
     # threefold; the ordinary library is built at full optimisation
     extra = (["-Xptxas", "-v"] if ptxas_info else []) + (["-DLBM_CHECK", "-Xcicc", "-O1"] if check else [])
+    extra += [f"-DLBM_BUILD_ID=\"{build_id()}{'-check' if check else ''}\""]
 
     def compile_one(src):
         obj = os.path.join(bdir, os.path.basename(src) + ".o")

@@ -53,11 +53,11 @@ __global__ void macros_kernel(const T* __restrict__ A, Geom g, Shift<typename St
   if (x >= g.nx) return;
   for (int y = y0 + (int)blockIdx.y; y < y1; y += (int)gridDim.y) {
     typename Store<T>::C m[3];
-    node_dmoments(A, g, x, y, z, m);
+    node_dmoments(A, g, x, y, z, m);  // deviations from the far field
     const long long k = (long long)y * g.nx + x;
-    rho[k] = 1.0 + (double)m[0];
-    ux[k] = (double)m[1];
-    uy[k] = (double)m[2];
+    rho[k] = z.m0[0] + (double)m[0];
+    ux[k] = z.m0[1] + (double)m[1];
+    uy[k] = z.m0[2] + (double)m[2];
   }
 }
 
@@ -128,11 +128,11 @@ struct KahanSum {
   __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-// Per node: (rho - 1, u) in the storage's compute type and the energy / mass
-// terms formed there; a thread's terms along one row are summed with
-// compensation in that type and every row sum is accumulated in double.
-// Sums: [0] mass sum rho (node count + sum of rho - 1), [1] disturbance
-// energy sum cs^2 (rho - rho_r)^2 / (2 rho_ff) + rho_ff |u - u_r|^2 / 2
+// Per node: (rho - rho_ff, u - u_ff) in the storage's compute type and the
+// energy / mass terms formed there; a thread's terms along one row are summed
+// with compensation in that type and every row sum is accumulated in double.
+// Sums: [0] mass sum rho (node count x rho_ff + sum of rho - rho_ff), [1]
+// disturbance energy sum cs^2 (rho - rho_r)^2 / (2 rho_ff) + rho_ff |u - u_r|^2 / 2
 // against the reference field (or the far field), [2] kinetic energy sum
 // rho |u|^2 / 2, [3] nodes with a non-finite or non-positive density.
 template <typename T, int NT>
@@ -145,33 +145,35 @@ __global__ void __launch_bounds__(NT) reduce_kernel(const T* __restrict__ A, Geo
   long long count = 0, bad = 0;
   const C e_rho = C(0.5 / (3.0 * rho_ff));  // cs^2 / (2 rho_ff), rounded once
   const C e_u = C(0.5 * rho_ff);
-  const C dr_ff = C(rho_ff - 1.0), ur_ff = C(uxf), vr_ff = C(uyf);
+  const C rho0 = C(rho_ff), u0 = C(uxf), v0 = C(uyf);
   // rows over blocks, columns over threads (no integer divisions per node)
   for (int y = blockIdx.x; y < g.ny; y += gridDim.x) {
     KahanSum<C> k0, k1, k2;
     for (int x = threadIdx.x; x < g.nx; x += NT) {
       C m[3];
-      node_dmoments(A, g, x, y, z, m);
-      C drr = dr_ff, ur = ur_ff, vr = vr_ff;
+      node_dmoments(A, g, x, y, z, m);  // (rho - rho_ff, u - u_ff)
+      C drr = C(0), dur = C(0), dvr = C(0);
       if (ref.rho) {
+        // the reference's deviations from the far field, formed in double and
+        // rounded once: no cancellation against the node's deviations
         const long long r = (long long)y * ref.pitch + x;
-        drr = C(ref.rho[r] - 1.0);  // rho_r - 1 rounded once: no cancellation against rho - 1
-        ur = C(ref.ux[r]);
-        vr = C(ref.uy[r]);
+        drr = C(ref.rho[r] - rho_ff);
+        dur = C(ref.ux[r] - uxf);
+        dvr = C(ref.uy[r] - uyf);
       }
-      const C dr = m[0] - drr, du = m[1] - ur, dv = m[2] - vr;
-      const C rho = C(1) + m[0];
+      const C dr = m[0] - drr, du = m[1] - dur, dv = m[2] - dvr;
+      const C rho = rho0 + m[0], ux = u0 + m[1], uy = v0 + m[2];
       ++count;
       k0.add(m[0]);
       k1.add(e_rho * dr * dr + e_u * (du * du + dv * dv));
-      k2.add(C(0.5) * rho * (m[1] * m[1] + m[2] * m[2]));
+      k2.add(C(0.5) * rho * (ux * ux + uy * uy));
       bad += (isfinite(m[0]) && isfinite(m[1]) && isfinite(m[2]) && rho > C(0)) ? 0 : 1;
     }
     s[0] += k0.value();
     s[1] += k1.value();
     s[2] += k2.value();
   }
-  const double sums[4] = {(double)count + s[0], s[1], s[2], (double)bad};
+  const double sums[4] = {(double)count * rho_ff + s[0], s[1], s[2], (double)bad};
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const double t = block_sum<NT>(sums[c], smem);

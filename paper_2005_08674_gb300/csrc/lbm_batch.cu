@@ -36,8 +36,14 @@
 #include "lbm_kernels.cuh"
 #include "lbm_staged.cuh"
 #include "lbm_trace.h"
+#include "lbm_tune_cache.h"
 
 int lbm_internal_fail(int code, const char* msg);
+// the autotuner cache of lbm_runtime.cu (lbm_set_tune_cache)
+std::string lbm_internal_tune_path();
+std::string lbm_internal_tune_key(const char* kind, int storage, int model, bool shift,
+                                  const std::vector<long long>& dims);
+void lbm_internal_tune_count(bool hit);
 int lbm_internal_set_edges(lbmk::Nsbc* p, const int32_t types[4], const double uw[8]);
 
 namespace {
@@ -676,6 +682,7 @@ lbm_batch_t* lbm_batch_create(int32_t count, const lbm_instance_desc* descs, int
   b->nsbc.beta = 0.0;
   b->nsbc.kappa = 3.0;
   b->nsbc.order = 1;
+  b->nsbc.corner = 0;
   long long off = 0;
   for (int k = 0; k < count; ++k) {
     const lbm_instance_desc& s = descs[k];
@@ -772,14 +779,18 @@ void batch_check_read(unsigned long long* count, unsigned long long* first, bool
 }
 }  // namespace lbmk
 
-int lbm_batch_set_nsbc(lbm_batch_t* b, double gamma, double beta, double kappa, int32_t grad_order) {
+int lbm_batch_set_nsbc(lbm_batch_t* b, double gamma, double beta, double kappa, int32_t corner_mode,
+                       int32_t grad_order) {
   if (!b) return bfail(LBM_EINVAL, "lbm_batch_set_nsbc: NULL handle");
-  if (!std::isfinite(gamma) || !std::isfinite(beta) || !std::isfinite(kappa) || (grad_order != 1 && grad_order != 2))
-    return bfail(LBM_EINVAL, "lbm_batch_set_nsbc: need finite gamma, beta, kappa and grad_order 1 or 2");
+  if (!std::isfinite(gamma) || !std::isfinite(beta) || !std::isfinite(kappa) || (grad_order != 1 && grad_order != 2) ||
+      (corner_mode != LBM_CORNER_DIAGONAL && corner_mode != LBM_CORNER_MEAN))
+    return bfail(LBM_EINVAL,
+                 "lbm_batch_set_nsbc: need finite gamma, beta, kappa, corner_mode 0 or 1 and grad_order 1 or 2");
   b->nsbc.gamma = gamma;
   b->nsbc.beta = beta;
   b->nsbc.kappa = kappa;
   b->nsbc.order = grad_order;
+  b->nsbc.corner = corner_mode;
   drop_batch_graphs(b);
   return LBM_OK;
 }
@@ -969,6 +980,29 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
     if (!b->initialised[k]) return bfail(LBM_ESTATE, "lbm_batch_autotune: instance %d not initialised", k);
   int rcs = ensure_batch_streams(b);
   if (rcs) return rcs;
+  // a choice recorded for the same key is applied without timing
+  const std::string tune_path = lbm_internal_tune_path();
+  std::string tune_key;
+  if (!tune_path.empty()) {
+    tune_key = lbm_internal_tune_key("batch", b->storage, b->collision, b->shift, {b->count, b->cells});
+    lbmtune::Entry e;
+    double v[7];
+    const char* names[7] = {"threads_x", "rows", "blocks", "prefetch_rows", "split", "tma_tile", "ms_per_step"};
+    bool ok = lbmtune::lookup(tune_path, tune_key, &e);
+    for (int k = 0; ok && k < 7; ++k) ok = e.get(names[k], &v[k]);
+    if (ok && lbm_batch_set_launch(b, (int32_t)v[0], (int32_t)v[1], (int32_t)v[2], (int32_t)v[3], (int32_t)v[4],
+                                   (int32_t)v[5]) == LBM_OK) {
+      lbm_internal_tune_count(true);
+      if (threads_x) *threads_x = b->bx;
+      if (rows) *rows = b->rows;
+      if (blocks) *blocks = b->blocks;
+      if (prefetch_rows) *prefetch_rows = b->pf;
+      if (split) *split = b->split ? 1 : 0;
+      if (tma_tile) *tma_tile = b->tile;
+      if (ms_per_step) *ms_per_step = v[6];
+      return LBM_OK;
+    }
+  }
   // keep the state: current pool copied aside and restored
   const size_t pb = lbm_batch_buffer_bytes(b);
   void* backup = nullptr;
@@ -1068,6 +1102,13 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
   cudaEventDestroy(e1);
   if (rc) return rc;
   if (rc2) return rc2;
+  if (!tune_path.empty()) {
+    lbm_internal_tune_count(false);
+    lbmtune::Entry e{tune_key,
+                     {{"threads_x", bb}, {"rows", br}, {"blocks", bk}, {"prefetch_rows", bp}, {"split", bs ? 1 : 0},
+                      {"tma_tile", bt}, {"ms_per_step", best}}};
+    lbmtune::store(tune_path, e);  // a cache that cannot be written is only not reused
+  }
   if (threads_x) *threads_x = bb;
   if (rows) *rows = br;
   if (blocks) *blocks = bk;
@@ -1075,6 +1116,28 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
   if (split) *split = bs ? 1 : 0;
   if (tma_tile) *tma_tile = bt;
   if (ms_per_step) *ms_per_step = best;
+  return LBM_OK;
+}
+
+int lbm_partition_instances(int32_t count, const int64_t* cells, int32_t ranks, int32_t* rank_of) {
+  if (count < 0 || ranks < 1 || (count > 0 && (!cells || !rank_of)))
+    return bfail(LBM_EINVAL, "lbm_partition_instances: need count >= 0, ranks >= 1 and non-NULL arrays");
+  for (int k = 0; k < count; ++k)
+    if (cells[k] < 0) return bfail(LBM_EINVAL, "lbm_partition_instances: instance %d has %lld nodes", k,
+                                   (long long)cells[k]);
+  // largest first, each to the rank with the fewest nodes so far (ties: the
+  // lower index, the lower rank), so every rank computes the same partition
+  std::vector<int> order(count);
+  for (int k = 0; k < count; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return cells[a] > cells[c]; });
+  std::vector<long long> load(ranks, 0);
+  for (int k : order) {
+    int r = 0;
+    for (int q = 1; q < ranks; ++q)
+      if (load[q] < load[r]) r = q;
+    rank_of[k] = r;
+    load[r] += cells[k];
+  }
   return LBM_OK;
 }
 

@@ -330,17 +330,21 @@ __device__ __forceinline__ void equilibrium(C drho, C ux, C uy, C (&e)[9], C s =
 }
 
 // Storage shift.  A stored population is h_i = f_i - f_i^eq(m0) (times the
-// storage scale), m0 = (rho0, u0) the far field: sh_i = f_i^eq(m0) - w_i is
-// added back to a deviation from w_i, and shm = (sum sh, sum c sh) = (rho0 - 1,
-// rho0 u0) to its moments.  For a far field at rest everything is zero and
-// h_i = f_i - w_i; with a mean flow the stored numbers stay as small as the
-// disturbance instead of carrying the stream's equilibrium (a 16-bit storage
-// keeps its relative precision for what changes).
+// storage scale), m0 = (rho0, u0) the far field, so that with a mean flow the
+// stored numbers stay as small as the disturbance instead of carrying the
+// stream's equilibrium (a 16-bit storage keeps its relative precision for
+// what changes); for a far field at rest h_i = f_i - w_i.  The step kernels
+// compute in deviations from m0 as well (d = rho - rho0, v = u - u0,
+// equilibrium_dev), which needs P_i(u0), u0 and rho0; sh_i = f_i^eq(m0) - w_i
+// converts to and from absolute populations outside the step.
 template <typename C>
 struct Shift {
-  C sh[9];
-  C shm[3];
-  bool on;  // false: all zero (far field at rest)
+  C sh[9];        // f_i^eq(m0) - w_i
+  C p0[9];        // P_i(u0) = 1 + 3 c_i.u0 + 4.5 (c_i.u0)^2 - 1.5 u0.u0
+  C u0[2];        // u0
+  C rho0;         // rho0
+  double m0[3];   // (rho0, u0x, u0y) in double
+  bool on;        // false: far field at rest (rho0 = 1, u0 = 0)
 };
 
 // The shift of far field m0 = (rho0, u0x, u0y), formed in double on the host
@@ -354,7 +358,11 @@ template <typename C>
 __host__ __device__ inline Shift<C> shift_as(const Shift<double>& z) {
   Shift<C> o;
   for (int i = 0; i < 9; ++i) o.sh[i] = C(z.sh[i]);
-  for (int c = 0; c < 3; ++c) o.shm[c] = C(z.shm[c]);
+  for (int i = 0; i < 9; ++i) o.p0[i] = C(z.p0[i]);
+  o.u0[0] = C(z.u0[0]);
+  o.u0[1] = C(z.u0[1]);
+  o.rho0 = C(z.rho0);
+  for (int c = 0; c < 3; ++c) o.m0[c] = z.m0[c];
   o.on = z.on;
   return o;
 }
@@ -375,6 +383,9 @@ __device__ __forceinline__ double fma_rn(double a, double b, double c) { return 
 // a - b rounded on its own (never fused with a product that formed a)
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+// a * b rounded on its own (never fused into a later add)
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
 
 // a / rho for the velocity u = (rho u) / rho: in float the fast division
 // intrinsic (within 2 ulp for rho in the normal range; rho is near 1 here),
@@ -382,38 +393,99 @@ __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(
 __device__ __forceinline__ float div_rho(float a, float rho) { return __fdividef(a, rho); }
 __device__ __forceinline__ double div_rho(double a, double rho) { return a / rho; }
 
+// Equilibrium in deviations from the far field: E_i = f_i^eq(rho, u) -
+// f_i^eq(rho0, u0) (Eq. feq_1 at two states, cs^2 = 1/3) times the weight
+// scale ws, from d = rho - rho0, v = u - u0 and the momentum deviation
+// J = rho v (= rho u - rho0 u0 - d u0).  With
+//   P_i(u) = 1 + 3 c_i.u + 4.5 (c_i.u)^2 - 1.5 u.u   (so f_i^eq = w_i rho P_i(u)),
+//   E_i = w_i [ d P_i(u0) + 3 c_i.J + rho Q_i ],
+//   Q_i = 4.5 (c_i.v)(c_i.s) - 1.5 v.s,   s = u + u0 = 2 u0 + v,
+// (rho (P_i(u) - P_i(u0)) = 3 c_i.J + rho Q_i), every term is of the size of
+// the disturbance, so float rounding is relative to it even in a mean flow:
+// forming f^eq(rho, u) and subtracting f^eq(m0) instead rounds terms of the
+// size of the stream's equilibrium (0.04 per population at Ma 0.1) every
+// step, and in a steady flow those roundings -- which do not conserve mass or
+// momentum -- add up step after step.  The first-order term takes J as summed
+// from the populations, not rho times a rounded quotient, so the momentum a
+// BGK relaxation puts back is the node's own to the rounding of each term.
+// For a far field at rest (SHIFT false: rho0 = 1, u0 = 0, P_i(u0) = 1) this
+// is w_i (d + 3 c_i.J + rho (4.5 (c_i.u)^2 - 1.5 u.u)).
+template <bool SHIFT, typename C>
+__device__ __forceinline__ void equilibrium_dev(C d, C vx, C vy, C jx, C jy, const Shift<C>& z, C (&e)[9],
+                                                C ws = C(1)) {
+  // every multiply-add is explicit, so that the shifted form with a zero
+  // shift (rho0 = 1, u0 = 0, P_i(u0) = 1) rounds exactly like the plain one
+  C rho, sx, sy;
+  if constexpr (SHIFT) {
+    rho = z.rho0 + d;
+    sx = fma_rn(C(2), z.u0[0], vx);
+    sy = fma_rn(C(2), z.u0[1], vy);
+  } else {
+    rho = C(1) + d;
+    sx = vx;
+    sy = vy;
+  }
+  C dp[9];  // d P_i(u0)
+#pragma unroll
+  for (int i = 0; i < 9; ++i) dp[i] = SHIFT ? mul_rn(d, z.p0[i]) : d;
+  const C vs = C(1.5) * fma_rn(vx, sx, mul_rn(vy, sy));
+  const C w0 = wt<C>(0) * ws, wa = wt<C>(1) * ws, wd = wt<C>(5) * ws;
+  e[0] = w0 * fma_rn(-rho, vs, dp[0]);
+  // axis directions: c.v = +-vx, +-vy
+  {
+    const C q = fma_rn(C(4.5) * vx, sx, -vs), b = C(3) * jx;
+    e[1] = wa * (fma_rn(rho, q, dp[1]) + b);
+    e[2] = wa * (fma_rn(rho, q, dp[2]) - b);
+  }
+  {
+    const C q = fma_rn(C(4.5) * vy, sy, -vs), b = C(3) * jy;
+    e[3] = wa * (fma_rn(rho, q, dp[3]) + b);
+    e[4] = wa * (fma_rn(rho, q, dp[4]) - b);
+  }
+  {
+    const C cv = vx + vy, cs = sx + sy;  // c_5 = -c_6 = (1, 1)
+    const C q = fma_rn(C(4.5) * cv, cs, -vs), b = C(3) * (jx + jy);
+    e[5] = wd * (fma_rn(rho, q, dp[5]) + b);
+    e[6] = wd * (fma_rn(rho, q, dp[6]) - b);
+  }
+  {
+    const C cv = vy - vx, cs = sy - sx;  // c_7 = -c_8 = (-1, 1)
+    const C q = fma_rn(C(4.5) * cv, cs, -vs), b = C(3) * (jy - jx);
+    e[7] = wd * (fma_rn(rho, q, dp[7]) + b);
+    e[8] = wd * (fma_rn(rho, q, dp[8]) - b);
+  }
+}
+
 // BGK collision, Eq. (lbe_1) with dt = 1, on shifted populations held as
 // s * h (s = storage scale; the relaxation is linear in h, only the moments
 // need 1/s).  Written as h* = (1 - omega) h + omega h^eq with omega folded
 // into the equilibrium weights: one fused multiply-add per population.
-// With a storage shift (SHIFT: a far field not at rest) the moments gain shm
-// and the equilibrium loses sh_i.  The relaxation is one explicitly rounded
-// fused multiply-add per population in both forms, so that the shifted form
-// with a zero shift gives the same bits as the plain one.
+// With a storage shift (SHIFT: a far field not at rest) the velocity enters
+// as its deviation v = u - u0 = (sum c h - d u0) / rho and the equilibrium as
+// its deviation from f^eq(m0) (equilibrium_dev), so no term of the size of
+// the stream's equilibrium is ever rounded.  The relaxation is one explicitly
+// rounded fused multiply-add per population in both forms, and the shifted
+// form with a zero shift gives the same bits as the plain one.
 template <bool SHIFT, typename C>
 __device__ __forceinline__ void collide_bgk(C (&h)[9], const Rates<C>& r, C s = C(1)) {
   const C omega = r.omega;
   C sd, sjx, sjy;
   moments(h, sd, sjx, sjy);
   const C is = C(1) / s;
-  if constexpr (SHIFT) {
-    sd = fma_rn(s, r.z.shm[0], sd);
-    sjx = fma_rn(s, r.z.shm[1], sjx);
-    sjy = fma_rn(s, r.z.shm[2], sjy);
-  }
-  const C drho = sd * is;
-  const C inv = div_rho(is, C(1) + drho);
+  const C d = sd * is;  // rho - rho0
   C e[9];
-  equilibrium(drho, sjx * inv, sjy * inv, e, s * omega);
-  const C keep = C(1) - omega;
   if constexpr (SHIFT) {
-    const C so = s * omega;
-#pragma unroll
-    for (int i = 0; i < 9; ++i) h[i] = fma_rn(keep, h[i], fma_rn(-so, r.z.sh[i], e[i]));
+    // J = rho (u - u0) = sum c h - d u0 and v = J / rho, from small quantities only
+    const C inv = div_rho(is, r.z.rho0 + d);
+    const C jx = fma_rn(-sd, r.z.u0[0], sjx), jy = fma_rn(-sd, r.z.u0[1], sjy);
+    equilibrium_dev<true>(d, jx * inv, jy * inv, jx * is, jy * is, r.z, e, s * omega);
   } else {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) h[i] = fma_rn(keep, h[i], e[i]);
+    const C inv = div_rho(is, C(1) + d);
+    equilibrium_dev<false>(d, sjx * inv, sjy * inv, sjx * is, sjy * is, r.z, e, s * omega);
   }
+  const C keep = C(1) - omega;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) h[i] = fma_rn(keep, h[i], e[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -436,18 +508,15 @@ __device__ __forceinline__ void collide_mrt(C (&h)[9], const Rates<C>& r, C s = 
   C sd, sjx, sjy;
   moments(h, sd, sjx, sjy);
   const C is = C(1) / s;
-  if constexpr (SHIFT) {
-    sd = fma_rn(s, r.z.shm[0], sd);
-    sjx = fma_rn(s, r.z.shm[1], sjx);
-    sjy = fma_rn(s, r.z.shm[2], sjy);
-  }
-  const C drho = sd * is;
-  const C inv = div_rho(is, C(1) + drho);
+  const C dr = sd * is;  // rho - rho0
   C e[9];
-  equilibrium(drho, sjx * inv, sjy * inv, e, s);
   if constexpr (SHIFT) {
-#pragma unroll
-    for (int i = 0; i < 9; ++i) e[i] = fma_rn(-s, r.z.sh[i], e[i]);
+    const C inv = div_rho(is, r.z.rho0 + dr);
+    const C jx = fma_rn(-sd, r.z.u0[0], sjx), jy = fma_rn(-sd, r.z.u0[1], sjy);
+    equilibrium_dev<true>(dr, jx * inv, jy * inv, jx * is, jy * is, r.z, e, s);
+  } else {
+    const C inv = div_rho(is, C(1) + dr);
+    equilibrium_dev<false>(dr, sjx * inv, sjy * inv, sjx * is, sjy * is, r.z, e, s);
   }
   C n[9];
 #pragma unroll
@@ -496,6 +565,7 @@ struct Nsbc {
   double gamma, beta, kappa;
   double m0[3];  // far-field (rho, ux, uy)
   int order;     // 1 or 2
+  int corner;    // corner reading: 0 diagonal normal, 1 mean of the two edges' m_c
   int periodic_x, periodic_y;  // axes closed periodically instead of by NSBC edges
   int vel[4];                  // edges (left, right, bottom, top) with a prescribed velocity
   double uw[4][2];             // that velocity
@@ -521,10 +591,10 @@ __device__ __forceinline__ void perimeter_node(int k, int nx, int ny, int& x, in
   }
 }
 
-// (rho - 1, ux, uy) at node (x, y) from the stored state, in the compute
-// type of the storage: float for f32 / f16 / bf16 (the shifted populations
-// keep rho - 1 free of cancellation, so float loses nothing the storage kept),
-// double in the f64 parity mode.
+// Deviations (rho - rho0, u - u0) from the far field at node (x, y) of the
+// stored state, in the compute type of the storage: float for f32 / f16 /
+// bf16 (the shifted populations keep them free of cancellation, so float
+// loses nothing the storage kept), double in the f64 parity mode.
 template <typename T>
 __device__ __forceinline__ void node_dmoments(const T* __restrict__ A, const Geom& g, int x, int y,
                                               const Shift<typename Store<T>::C>& z, typename Store<T>::C (&m)[3]) {
@@ -534,33 +604,33 @@ __device__ __forceinline__ void node_dmoments(const T* __restrict__ A, const Geo
   C h[9];
 #pragma unroll
   for (int i = 0; i < 9; ++i) h[i] = S::ldg1(A + i * g.plane + o);
-  C drho, jx, jy;
-  moments(h, drho, jx, jy);
-  drho += z.shm[0];
-  jx += z.shm[1];
-  jy += z.shm[2];
-  const C inv = div_rho(C(1), C(1) + drho);
-  m[0] = drho;
-  m[1] = jx * inv;
-  m[2] = jy * inv;
+  C d, jx, jy;
+  moments(h, d, jx, jy);
+  const C inv = div_rho(C(1), z.rho0 + d);
+  m[0] = d;
+  m[1] = fma_rn(-d, z.u0[0], jx) * inv;
+  m[2] = fma_rn(-d, z.u0[1], jy) * inv;
 }
 
-// (rho - 1, ux, uy) of a node's shifted populations (physical units) in the
-// compute type of the storage: the shifted populations keep d_rho free of
-// cancellation, so float is exact to float rounding of the perturbation.
+// Deviations (rho - rho0, u - u0) from the far field of a node's shifted
+// populations (physical units) in the compute type of the storage: every
+// quantity is of the size of the disturbance, so float is exact to float
+// rounding of the perturbation.  For a far field at rest (SHIFT false) they
+// are (rho - 1, u).
 template <bool SHIFT, typename C>
-__device__ __forceinline__ void dmoments_of(const C (&h)[9], const Shift<C>& z, C (&m)[3]) {
-  C drho, jx, jy;
-  moments(h, drho, jx, jy);
+__device__ __forceinline__ void dmoments_of(const C (&h)[9], C rho0, C u0x, C u0y, C (&m)[3]) {
+  C d, jx, jy;
+  moments(h, d, jx, jy);
+  m[0] = d;
   if constexpr (SHIFT) {
-    drho += z.shm[0];
-    jx += z.shm[1];
-    jy += z.shm[2];
+    const C inv = C(1) / (rho0 + d);
+    m[1] = fma_rn(-d, u0x, jx) * inv;
+    m[2] = fma_rn(-d, u0y, jy) * inv;
+  } else {
+    const C inv = C(1) / (C(1) + d);
+    m[1] = jx * inv;
+    m[2] = jy * inv;
   }
-  const C inv = C(1) / (C(1) + drho);
-  m[0] = drho;
-  m[1] = jx * inv;
-  m[2] = jy * inv;
 }
 
 }  // namespace lbmk

@@ -153,11 +153,12 @@ __global__ void __launch_bounds__(BX) bulk_kernel(const T* __restrict__ A, T* __
 }
 
 // ---------------------------------------------------------------------------
-// NSBC.  The moments (rho - 1, ux, uy) are formed in the compute type at
-// b, b - n and (second-order difference) b - 2n; m_c is predicted and
-// blended in double (the prediction is linear, so predicting rho - 1 is
-// predicting rho); the node is then rebuilt, corrected and collided in the
-// compute type.
+// NSBC.  The moments are formed in the compute type at b, b - n and
+// (second-order difference) b - 2n as deviations (rho - rho0, u - u0) from
+// the far field m0; m_c is predicted and blended in double (Eqs. nes_2 and
+// nes_3 are linear, so predicting the deviation is predicting m, and the
+// blend towards m0 scales the deviation by 1 - beta); the node is then
+// rebuilt, corrected and collided in the compute type.
 // ---------------------------------------------------------------------------
 // Perimeter node `node`: coordinates and outward normal (zero along a
 // periodic axis, which has no boundary there).
@@ -193,25 +194,73 @@ __device__ __forceinline__ void edge_pull(const T* __restrict__ A, const Geom& g
 }
 
 // Eq. (nes_2): m_p = m_b - gamma d_n m, d_n along the outward unit normal by
-// the one-sided difference of the given order (1 / |n| = 1/sqrt(2) at
-// corners); Eq. (nes_3): m_c = (1 - beta) m_p + beta m_0.  Component c of
-// (rho - 1, ux, uy) from its values at b, b - n, b - 2n, in FP64 with every
-// rounding explicit (no contraction left to the compiler), so that every
-// caller gets the same bits.  GB300's FP64 divide is slow: no divides.
+// the one-sided difference of the given order (1 / |n| = 1/sqrt(2) along a
+// corner's diagonal); Eq. (nes_3): m_c = (1 - beta) m_p + beta m_0, which
+// for the deviation m - m_0 is (1 - beta) (m_p - m_0).  Component c of the
+// deviation (rho - rho0, u - u0) from its values at b, b - n, b - 2n, in FP64
+// with every rounding explicit (no contraction left to the compiler), so that
+// every caller gets the same bits.  GB300's FP64 divide is slow: no divides.
+// The settings Eqs. nes_2 and nes_3 use, and the far field in the compute
+// type: small values passed by value (also to the out-of-line corner pass,
+// where a reference would move the caller's structures to local memory).
+struct Predict {
+  double gamma, beta;
+  int order;
+};
 template <typename C>
-__device__ __forceinline__ C edge_predict(C vb, C v1, C v2, int c, bool diagonal, const Nsbc& p) {
+struct Far {
+  C rho0, u0x, u0y;
+};
+__device__ __forceinline__ Predict predict_of(const Nsbc& p) { return Predict{p.gamma, p.beta, p.order}; }
+template <typename C>
+__device__ __forceinline__ Far<C> far_of(const Shift<C>& z) { return Far<C>{z.rho0, z.u0[0], z.u0[1]}; }
+
+template <typename C>
+__device__ __forceinline__ double edge_predict(C vb, C v1, C v2, bool diagonal, Predict p) {
   const double mb = (double)vb, m1 = (double)v1, m2 = (double)v2;
-  const double m0 = c == 0 ? p.m0[0] - 1.0 : (c == 1 ? p.m0[1] : p.m0[2]);  // static indices only
   const double inv_len = diagonal ? 0.70710678118654752 : 1.0;
   const double dn = p.order == 2 ? __dmul_rn(__fma_rn(3.0, mb, __fma_rn(-4.0, m1, m2)), 0.5 * inv_len)
                                  : __dmul_rn(__dsub_rn(mb, m1), inv_len);
   const double mp = __fma_rn(-p.gamma, dn, mb);
-  return C(__fma_rn(1.0 - p.beta, mp, __dmul_rn(p.beta, m0)));
+  return __dmul_rn(1.0 - p.beta, mp);
+}
+
+// Lane q of a quad: the deviations (rho - rho0, u - u0) of node b - q n (zeros for
+// lanes beyond the difference order), transposed across the quad so that
+// lane c (c < 3) gets component c at b, b - n, b - 2n, predicted and blended
+// in FP64 by edge_predict.  All four lanes call this together.
+template <typename T, bool SHIFT>
+__device__ __forceinline__ double quad_predict(const typename Store<T>::C (&v)[9], Far<typename Store<T>::C> z,
+                                               unsigned quad, int cq, bool diagonal, Predict p) {
+  using C = typename Store<T>::C;
+  C mq[3];
+  dmoments_of<SHIFT>(v, z.rho0, z.u0x, z.u0y, mq);  // lanes that loaded nothing get unused values
+  C t0[3], t1[3], t2[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    t0[c] = __shfl_sync(quad, mq[c], 0, 4);
+    t1[c] = __shfl_sync(quad, mq[c], 1, 4);
+    t2[c] = __shfl_sync(quad, mq[c], 2, 4);
+  }
+  return edge_predict(cq == 0 ? t0[0] : (cq == 1 ? t0[1] : t0[2]), cq == 0 ? t1[0] : (cq == 1 ? t1[1] : t1[2]),
+                      cq == 0 ? t2[0] : (cq == 1 ? t2[1] : t2[2]), diagonal, p);
+}
+
+// The populations of node (x, y), or zeros if !want.
+template <typename T>
+__device__ __forceinline__ void load_node(const T* __restrict__ A, long long plane, int pitch, int x, int y,
+                                          bool want, typename Store<T>::C (&v)[9]) {
+  using S = Store<T>;
+  using C = typename S::C;
+  const long long o = (long long)y * pitch + x;
+#pragma unroll
+  for (int i = 0; i < 9; ++i) v[i] = want ? S::ldg1(A + i * plane + o) : C(0);
 }
 
 // The rest of the node, given its pulled populations and the blended
-// (rho_c - 1, u_c): velocity override, reconstruction of the unknown
-// populations, correction, collision and the store.
+// deviation m_c - m0 = (rho_c - rho0, u_c - u0): velocity override,
+// reconstruction of the unknown populations, correction, collision and the
+// store.
 template <typename T, int MODEL, bool SHIFT = false>
 __device__ __forceinline__ void edge_finish(T* __restrict__ B, const Geom& g, const Nsbc& p,
                                             const Rates<typename Store<T>::C>& rates, const EdgeNode& en,
@@ -222,25 +271,26 @@ __device__ __forceinline__ void edge_finish(T* __restrict__ B, const Geom& g, co
   const int x = en.x, y = en.y;
   if (en.open) {
     // a velocity edge keeps the predicted density and imposes its velocity
-    // (left/right edges win at corners)
+    // (left/right edges win at corners); its deviation u_w - u0 is formed in
+    // double
     const int side = (x == 0 && p.vel[0])             ? 0
                      : (x == g.nx - 1 && p.vel[1])    ? 1
                      : (y == 0 && p.vel[2])           ? 2
                      : (y == g.ny - 1 && p.vel[3])    ? 3
                                                       : -1;
     if (side >= 0) {
-      mc[1] = C(side == 0 ? p.uw[0][0] : side == 1 ? p.uw[1][0] : side == 2 ? p.uw[2][0] : p.uw[3][0]);
-      mc[2] = C(side == 0 ? p.uw[0][1] : side == 1 ? p.uw[1][1] : side == 2 ? p.uw[2][1] : p.uw[3][1]);
+      const double ux = side == 0 ? p.uw[0][0] : side == 1 ? p.uw[1][0] : side == 2 ? p.uw[2][0] : p.uw[3][0];
+      const double uy = side == 0 ? p.uw[0][1] : side == 1 ? p.uw[1][1] : side == 2 ? p.uw[2][1] : p.uw[3][1];
+      mc[1] = C(ux - p.m0[1]);
+      mc[2] = C(uy - p.m0[2]);
     }
 
     // Eqs. (nes_0), (nes_1): f_in = f_in^eq(m_c) + f_out - f_out^eq(m_c)
-    // (in stored deviations: h^eq = f^eq - f^eq(m0), the same relation)
-    const C drho_c = mc[0];
+    // (in stored deviations: f^eq(m_c) - f^eq(m0), the same relation)
     C e[9];
-    equilibrium(drho_c, mc[1], mc[2], e);
-    if constexpr (SHIFT) {
-#pragma unroll
-      for (int i = 0; i < 9; ++i) e[i] = sub_rn(e[i], rates.z.sh[i]);
+    {
+      const C rho_c = (SHIFT ? rates.z.rho0 : C(1)) + mc[0];
+      equilibrium_dev<SHIFT>(mc[0], mc[1], mc[2], rho_c * mc[1], rho_c * mc[2], rates.z, e);
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -248,17 +298,22 @@ __device__ __forceinline__ void edge_finish(T* __restrict__ B, const Geom& g, co
       if (!known[i]) h[i] = known[o] ? e[i] + (h[o] - e[o]) : e[i];
     }
 
-    // Eq. (nes_4): f_i -= w_i (d_rho + kappa c_i . d(rho u))
+    // Eq. (nes_4): f_i -= w_i (d_rho + kappa c_i . d(rho u)), with the node's
+    // moments and the targets (rho_c, rho_c u_c) both taken relative to m0:
+    // rho_c u_c - rho0 u0 = rho_c (u_c - u0) + (rho_c - rho0) u0
     C drho, jx, jy;
     moments(h, drho, jx, jy);
+    const C d_rho = drho - mc[0];
+    C d_jx, d_jy;  // explicit multiply-adds: a zero shift rounds like the plain form
     if constexpr (SHIFT) {
-      drho += rates.z.shm[0];
-      jx += rates.z.shm[1];
-      jy += rates.z.shm[2];
+      const C rho_c = rates.z.rho0 + mc[0];
+      d_jx = fma_rn(-rho_c, mc[1], fma_rn(-mc[0], rates.z.u0[0], jx));
+      d_jy = fma_rn(-rho_c, mc[2], fma_rn(-mc[0], rates.z.u0[1], jy));
+    } else {
+      const C rho_c = C(1) + mc[0];
+      d_jx = fma_rn(-rho_c, mc[1], jx);
+      d_jy = fma_rn(-rho_c, mc[2], jy);
     }
-    const C d_rho = drho - drho_c;
-    const C d_jx = jx - (C(1) + mc[0]) * mc[1];
-    const C d_jy = jy - (C(1) + mc[0]) * mc[2];
     const C kap = C(p.kappa);
 #pragma unroll
     for (int i = 0; i < 9; ++i) h[i] -= wt<C>(i) * (d_rho + kap * (C(cx(i)) * d_jx + C(cy(i)) * d_jy));
@@ -270,6 +325,18 @@ __device__ __forceinline__ void edge_finish(T* __restrict__ B, const Geom& g, co
   for (int i = 0; i < 9; ++i) S::st1(B + i * g.plane + o, h[i]);
 }
 
+// The second prediction of a corner under corner reading 1, along the
+// horizontal edge's normal (0, nyn).  Kept out of line: only the quads that
+// hold a corner call it, and inlined it would cost every NSBC node registers.
+template <typename T, bool SHIFT>
+__device__ __noinline__ double corner_second_prediction(const T* __restrict__ A, long long plane, int pitch, int x,
+                                                        int y, Far<typename Store<T>::C> z, unsigned quad, int q,
+                                                        Predict p) {
+  typename Store<T>::C w[9];
+  load_node(A, plane, pitch, x, y, q <= p.order, w);
+  return quad_predict<T, SHIFT>(w, z, quad, q < 3 ? q : 0, false, p);
+}
+
 // K perimeter nodes, each handled by the four lanes of one quad (q = lane &
 // 3); all four lanes must call this together with the same nodes.  Lane q
 // forms (rho - 1, ux, uy) at b - q n in the compute type; the quad then
@@ -279,6 +346,10 @@ __device__ __forceinline__ void edge_finish(T* __restrict__ B, const Geom& g, co
 // blended components and finishes the node.  Every load of the K nodes is
 // issued before the first is used (one round trip for all of them); nodes
 // with valid[k] false are computed (from in-range addresses) but not stored.
+// A corner under corner reading 1 is predicted twice, along the normals of
+// the vertical edge (n = (nxn, 0)) and of the horizontal one (n = (0, nyn)),
+// and gets the mean of the two blended states; the second pass runs only in
+// the quads that hold a corner.
 template <typename T, int MODEL, int K, bool SHIFT = false>
 __device__ __forceinline__ void nsbc_nodes(const T* __restrict__ A, T* __restrict__ B, const Geom& g, const Nsbc& p,
                                            const Rates<typename Store<T>::C>& rates, const int (&node)[K],
@@ -296,30 +367,24 @@ __device__ __forceinline__ void nsbc_nodes(const T* __restrict__ A, T* __restric
   }
 #pragma unroll
   for (int k = 0; k < K; ++k) {  // lane q: the node b - q n (zeros if not needed)
-    const bool want = en[k].open && q <= p.order;
-    const long long o = (long long)(en[k].y - q * en[k].nyn) * g.pitch + (en[k].x - q * en[k].nxn);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) v[k][i] = want ? S::ldg1(A + i * g.plane + o) : C(0);
+    const bool split = p.corner == 1 && en[k].nxn != 0 && en[k].nyn != 0;
+    const int ny1 = split ? 0 : en[k].nyn;  // a split corner: the vertical edge's normal first
+    load_node(A, g.plane, g.pitch, en[k].x - q * en[k].nxn, en[k].y - q * ny1, en[k].open && q <= p.order, v[k]);
   }
   const int cq = q < 3 ? q : 0;
-  C mc[K][3];  // (rho_c - 1, u_c)
+  C mc[K][3];  // (rho_c - rho0, u_c - u0)
 #pragma unroll
   for (int k = 0; k < K; ++k) {
-    C mq[3];
-    dmoments_of<SHIFT>(v[k], rates.z, mq);  // lanes that loaded nothing get unused values
-    C t0[3], t1[3], t2[3];
+    const bool corner = en[k].nxn != 0 && en[k].nyn != 0;
+    const bool split = p.corner == 1 && corner;  // the same for all four lanes of the quad
+    double mine = quad_predict<T, SHIFT>(v[k], far_of(rates.z), quad, cq, corner && !split, predict_of(p));
+    if (split)
+      mine = __dmul_rn(0.5, __dadd_rn(mine, corner_second_prediction<T, SHIFT>(A, g.plane, g.pitch, en[k].x,
+                                                                              en[k].y - q * en[k].nyn, far_of(rates.z),
+                                                                              quad, q, predict_of(p))));
+    const C mcq = C(mine);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      t0[c] = __shfl_sync(quad, mq[c], 0, 4);
-      t1[c] = __shfl_sync(quad, mq[c], 1, 4);
-      t2[c] = __shfl_sync(quad, mq[c], 2, 4);
-    }
-    const C mine = edge_predict(cq == 0 ? t0[0] : (cq == 1 ? t0[1] : t0[2]),
-                                cq == 0 ? t1[0] : (cq == 1 ? t1[1] : t1[2]),
-                                cq == 0 ? t2[0] : (cq == 1 ? t2[1] : t2[2]), cq,
-                                en[k].nxn != 0 && en[k].nyn != 0, p);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) mc[k][c] = __shfl_sync(quad, mine, c, 4);
+    for (int c = 0; c < 3; ++c) mc[k][c] = __shfl_sync(quad, mcq, c, 4);
   }
   if (q != 0) return;
 #pragma unroll

@@ -11,6 +11,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -20,6 +21,7 @@
 #include "lbm_kernels.cuh"
 #include "lbm_staged.cuh"
 #include "lbm_trace.h"
+#include "lbm_tune_cache.h"
 
 namespace lbmk {
 Shift<double> far_field_shift(const double m0[3]) {
@@ -30,9 +32,14 @@ Shift<double> far_field_shift(const double m0[3]) {
     const double cu = cx(i) * ux + cy(i) * uy;
     z.sh[i] = wt<double>(i) * (drho + rho * (3.0 * cu + 4.5 * cu * cu - usq));
   }
-  z.shm[0] = drho;
-  z.shm[1] = rho * ux;
-  z.shm[2] = rho * uy;
+  for (int i = 0; i < 9; ++i) {
+    const double cu = cx(i) * ux + cy(i) * uy;
+    z.p0[i] = 1.0 + 3.0 * cu + 4.5 * cu * cu - usq;
+  }
+  z.u0[0] = ux;
+  z.u0[1] = uy;
+  z.rho0 = rho;
+  for (int c = 0; c < 3; ++c) z.m0[c] = m0[c];
   z.on = !(drho == 0.0 && ux == 0.0 && uy == 0.0);
   return z;
 }
@@ -541,6 +548,7 @@ lbm_t* lbm_create(int32_t nx, int32_t ny, double tau, double farfield_rho, const
   h->nsbc.beta = 0.0;
   h->nsbc.kappa = 3.0;
   h->nsbc.order = 1;
+  h->nsbc.corner = 0;
   h->nsbc.m0[0] = farfield_rho;
   h->nsbc.m0[1] = farfield_u[0];
   h->nsbc.m0[2] = farfield_u[1];
@@ -576,19 +584,76 @@ void lbm_destroy(lbm_t* h) {
   delete h;
 }
 
-int lbm_set_nsbc(lbm_t* h, double gamma, double beta, double kappa, int32_t grad_order) {
+int lbm_set_nsbc(lbm_t* h, double gamma, double beta, double kappa, int32_t corner_mode, int32_t grad_order) {
   if (!h) return fail(LBM_EINVAL, "lbm_set_nsbc: NULL handle");
-  if (!std::isfinite(gamma) || !std::isfinite(beta) || !std::isfinite(kappa) || (grad_order != 1 && grad_order != 2))
-    return fail(LBM_EINVAL, "lbm_set_nsbc: need finite gamma, beta, kappa and grad_order 1 or 2");
+  if (!std::isfinite(gamma) || !std::isfinite(beta) || !std::isfinite(kappa) || (grad_order != 1 && grad_order != 2) ||
+      (corner_mode != LBM_CORNER_DIAGONAL && corner_mode != LBM_CORNER_MEAN))
+    return fail(LBM_EINVAL, "lbm_set_nsbc: need finite gamma, beta, kappa, corner_mode 0 or 1 and grad_order 1 or 2");
   h->nsbc.gamma = gamma;
   h->nsbc.beta = beta;
   h->nsbc.kappa = kappa;
   h->nsbc.order = grad_order;
+  h->nsbc.corner = corner_mode;
   drop_graphs(h);
   return LBM_OK;
 }
 
 }  // extern "C"
+
+// Autotuner cache (lbm_set_tune_cache), shared with the batched mode: the
+// file path ("" = off; the LBM_TUNE_CACHE environment variable sets it until
+// the first lbm_set_tune_cache) and the hit / miss counts.
+#ifndef LBM_BUILD_ID
+#define LBM_BUILD_ID "unversioned"
+#endif
+namespace {
+std::mutex g_tune_mutex;
+std::string g_tune_path;
+bool g_tune_set = false;
+long long g_tune_hits = 0, g_tune_misses = 0;
+}  // namespace
+
+std::string lbm_internal_tune_path() {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  if (!g_tune_set) {
+    const char* env = std::getenv("LBM_TUNE_CACHE");
+    g_tune_path = env ? env : "";
+    g_tune_set = true;
+  }
+  return g_tune_path;
+}
+
+// The key of a tuning problem on the current device (see lbm_tune_cache.h).
+std::string lbm_internal_tune_key(const char* kind, int storage, int model, bool shift,
+                                  const std::vector<long long>& dims) {
+  int dev = 0, drv = 0, rt = 0;
+  cudaGetDevice(&dev);
+  cudaDriverGetVersion(&drv);
+  cudaRuntimeGetVersion(&rt);
+  cudaDeviceProp prop{};
+  const char* name = cudaGetDeviceProperties(&prop, dev) == cudaSuccess ? prop.name : "unknown-device";
+  return lbmtune::make_key(name, drv, rt, LBM_BUILD_ID, kind, storage, model, shift, dims);
+}
+
+void lbm_internal_tune_count(bool hit) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  (hit ? g_tune_hits : g_tune_misses) += 1;
+}
+
+extern "C" int lbm_set_tune_cache(const char* path) {
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_path = path ? path : "";
+  g_tune_set = true;
+  return LBM_OK;
+}
+
+extern "C" int lbm_tune_cache_stats(int64_t* hits, int64_t* misses) {
+  if (!hits || !misses) return fail(LBM_EINVAL, "lbm_tune_cache_stats: NULL argument");
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  *hits = g_tune_hits;
+  *misses = g_tune_misses;
+  return LBM_OK;
+}
 
 // Shared with the batched mode: validate edge types and fill the NSBC block.
 int lbm_internal_set_edges(lbmk::Nsbc* p, const int32_t types[4], const double uw[8]) {
@@ -860,30 +925,74 @@ int lbm_set_populations(lbm_t* h, const double* f) {
   return LBM_OK;
 }
 
+}  // extern "C"
+
+// Checkpoint record: this header, then the population buffer as stored.
+namespace {
+struct StateHeader {
+  char magic[8];  // "LBMSTAT1"
+  int32_t version, storage, nx, ny, pitch, reserved;
+  int64_t steps;
+  double m0[3];  // far field: the stored populations are deviations from f^eq(m0)
+};
+static_assert(sizeof(StateHeader) == 64, "checkpoint header layout");
+constexpr char kStateMagic[8] = {'L', 'B', 'M', 'S', 'T', 'A', 'T', '1'};
+}  // namespace
+
+extern "C" {
+
+size_t lbm_state_bytes(const lbm_t* h) { return h ? sizeof(StateHeader) + lbm_buffer_bytes(h) : 0; }
+
 int lbm_save_state(lbm_t* h, void* host, size_t bytes, int64_t* steps) {
   if (!h || !host) return fail(LBM_EINVAL, "lbm_save_state: NULL argument");
   if (!h->initialised) return fail(LBM_ESTATE, "lbm_save_state: call lbm_init first");
-  if (bytes != lbm_buffer_bytes(h))
-    return fail(LBM_EINVAL, "lbm_save_state: %zu bytes given, the state is %zu", bytes, lbm_buffer_bytes(h));
-  LBM_CUDA(cudaMemcpyAsync(host, h->buf[h->cur], bytes, cudaMemcpyDeviceToHost, h->stream));
+  if (bytes != lbm_state_bytes(h))
+    return fail(LBM_EINVAL, "lbm_save_state: %zu bytes given, the record is %zu", bytes, lbm_state_bytes(h));
+  StateHeader hd{};
+  std::memcpy(hd.magic, kStateMagic, sizeof hd.magic);
+  hd.version = 1;
+  hd.storage = h->storage;
+  hd.nx = h->nx;
+  hd.ny = h->ny;
+  hd.pitch = h->pitch;
+  hd.steps = h->steps;
+  for (int c = 0; c < 3; ++c) hd.m0[c] = h->nsbc.m0[c];
+  std::memcpy(host, &hd, sizeof hd);
+  LBM_CUDA(cudaMemcpyAsync(static_cast<char*>(host) + sizeof hd, h->buf[h->cur], lbm_buffer_bytes(h),
+                           cudaMemcpyDeviceToHost, h->stream));
   LBM_CUDA(cudaStreamSynchronize(h->stream));
   if (steps) *steps = h->steps;
   return LBM_OK;
 }
 
-int lbm_load_state(lbm_t* h, const void* host, size_t bytes, int64_t steps) {
+int lbm_load_state(lbm_t* h, const void* host, size_t bytes) {
   if (!h || !host) return fail(LBM_EINVAL, "lbm_load_state: NULL argument");
-  if (bytes != lbm_buffer_bytes(h))
-    return fail(LBM_EINVAL, "lbm_load_state: %zu bytes given, the state is %zu", bytes, lbm_buffer_bytes(h));
-  if (steps < 0) return fail(LBM_EINVAL, "lbm_load_state: step count %lld < 0", (long long)steps);
+  if (bytes != lbm_state_bytes(h))
+    return fail(LBM_EINVAL, "lbm_load_state: %zu bytes given, the record is %zu", bytes, lbm_state_bytes(h));
+  // the record must describe this handle's layout and far field, or its
+  // bytes mean something else here
+  StateHeader hd;
+  std::memcpy(&hd, host, sizeof hd);
+  if (std::memcmp(hd.magic, kStateMagic, sizeof hd.magic) != 0 || hd.version != 1)
+    return fail(LBM_EINVAL, "lbm_load_state: not a checkpoint record of this library");
+  if (hd.storage != h->storage || hd.nx != h->nx || hd.ny != h->ny || hd.pitch != h->pitch)
+    return fail(LBM_EINVAL, "lbm_load_state: record holds storage %d, %d x %d (pitch %d); handle has %d, %d x %d (%d)",
+                hd.storage, hd.nx, hd.ny, hd.pitch, h->storage, h->nx, h->ny, h->pitch);
+  for (int c = 0; c < 3; ++c)
+    if (std::memcmp(&hd.m0[c], &h->nsbc.m0[c], sizeof(double)) != 0)
+      return fail(LBM_EINVAL, "lbm_load_state: record's far field (%.17g, %.17g, %.17g) differs from the handle's",
+                  hd.m0[0], hd.m0[1], hd.m0[2]);
+  if (hd.steps < 0) return fail(LBM_EINVAL, "lbm_load_state: step count %lld < 0", (long long)hd.steps);
   int rc = ensure_memory(h);
   if (rc) return rc;
   h->cur = 0;
-  LBM_CUDA(cudaMemcpyAsync(h->buf[0], host, bytes, cudaMemcpyHostToDevice, h->stream));
-  LBM_CUDA(cudaMemcpyAsync(h->buf[1], h->buf[0], bytes, cudaMemcpyDeviceToDevice, h->stream));
+  const size_t bb = lbm_buffer_bytes(h);
+  LBM_CUDA(cudaMemcpyAsync(h->buf[0], static_cast<const char*>(host) + sizeof hd, bb, cudaMemcpyHostToDevice,
+                           h->stream));
+  LBM_CUDA(cudaMemcpyAsync(h->buf[1], h->buf[0], bb, cudaMemcpyDeviceToDevice, h->stream));
   LBM_CUDA(cudaStreamSynchronize(h->stream));
   h->initialised = true;
-  h->steps = steps;
+  h->steps = hd.steps;
   return LBM_OK;
 }
 
@@ -994,6 +1103,26 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
   if (!h->initialised) return fail(LBM_ESTATE, "lbm_autotune: call lbm_init first");
   int rc = ensure_streams(h);
   if (rc) return rc;
+  // a choice recorded for the same key is applied without timing
+  const std::string tune_path = lbm_internal_tune_path();
+  std::string tune_key;
+  if (!tune_path.empty()) {
+    tune_key = lbm_internal_tune_key("domain", h->storage, h->collision, zshift(h).on, {h->nx, h->ny});
+    lbmtune::Entry e;
+    double bx = 0, r = 0, pf = 0, st = -1, fz = -1, ms = 0;
+    if (lbmtune::lookup(tune_path, tune_key, &e) && e.get("threads_x", &bx) && e.get("rows", &r) &&
+        e.get("prefetch_rows", &pf) && e.get("staged", &st) && e.get("fused", &fz) && e.get("ms_per_step", &ms) &&
+        (st == 0 || st == 3 || st == 4) && (fz == 0 || fz == 1) &&
+        lbm_set_launch(h, (int32_t)bx, (int32_t)r, (int32_t)pf) == LBM_OK &&
+        (st == 0 || lbm_set_staged(h, (int32_t)st) == LBM_OK) && (fz == 0 || lbm_set_fused(h, 1) == LBM_OK)) {
+      lbm_internal_tune_count(true);
+      if (threads_x) *threads_x = h->bx;
+      if (rows) *rows = h->rows;
+      if (prefetch_rows) *prefetch_rows = h->pf;
+      if (ms_per_step) *ms_per_step = ms;
+      return LBM_OK;
+    }
+  }
   // keep the state: copy the current buffer aside, restore it at the end
   const size_t bb = lbm_buffer_bytes(h);
   void* backup = nullptr;
@@ -1064,6 +1193,13 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc) return rc;
+  if (!tune_path.empty()) {
+    lbm_internal_tune_count(false);
+    lbmtune::Entry e{tune_key,
+                     {{"threads_x", best_bx}, {"rows", best_rows}, {"prefetch_rows", best_pf},
+                      {"staged", h->staged}, {"fused", h->fused ? 1 : 0}, {"ms_per_step", best}}};
+    lbmtune::store(tune_path, e);  // a cache that cannot be written is only not reused
+  }
   if (threads_x) *threads_x = best_bx;
   if (rows) *rows = best_rows;
   if (prefetch_rows) *prefetch_rows = best_pf;
@@ -1094,9 +1230,11 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
 // =========================================================================
 namespace {
 
+// reduce_kernel hands whole rows to blocks (row y to block y mod grid) and
+// columns to threads, so any domain works with at most kNoAllocMaxBlocks
+// blocks: the grid is min(ny, kNoAllocMaxBlocks), one block per row up to that.
 constexpr int kNoAllocThreads = kReduceThreads;
-constexpr int kNoAllocNodesPerThread = 64;                  // grid = nodes / (256 * 64) blocks
-constexpr int kNoAllocMaxBlocks = 4096;                     // -> at most 67,108,864 nodes (8192^2)
+constexpr int kNoAllocMaxBlocks = 4096;
 constexpr int kNoAllocDoubles = kNoAllocMaxBlocks * 4 + 4;  // partials + out[4]: 131,104 bytes
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
@@ -1129,15 +1267,7 @@ int noalloc_scratch(double** out) {
 extern "C" int lbm_reduce_noalloc(lbm_t* h, const double* ref_rho, const double* ref_ux, const double* ref_uy,
                                   int32_t ref_pitch, double out[4]) {
   if (!h || !out) return fail(LBM_EINVAL, "lbm_reduce_noalloc: NULL argument");
-  const long long n = (long long)h->nx * h->ny;
-  const long long per_block = (long long)kNoAllocThreads * kNoAllocNodesPerThread;
-  const long long blocks = (n + per_block - 1) / per_block;
-  if (blocks > kNoAllocMaxBlocks)
-    return fail(LBM_EINVAL,
-                "lbm_reduce_noalloc: %lld nodes exceed the fixed scratch limit of %lld nodes "
-                "(%d blocks x %d threads x %d nodes); use lbm_reduce",
-                n, (long long)kNoAllocMaxBlocks * per_block, kNoAllocMaxBlocks, kNoAllocThreads,
-                kNoAllocNodesPerThread);
+  const int blocks = std::min(h->ny, kNoAllocMaxBlocks);
   if (!h->initialised) return fail(LBM_ESTATE, "lbm_reduce_noalloc: call lbm_init first");
   if (ref_rho && (!ref_ux || !ref_uy || ref_pitch < h->nx))
     return fail(LBM_EINVAL, "lbm_reduce_noalloc: reference needs rho, ux, uy and pitch >= nx");
@@ -1155,11 +1285,11 @@ extern "C" int lbm_reduce_noalloc(lbm_t* h, const double* ref_rho, const double*
   lbmk::RefField ref{ref_rho, ref_ux, ref_uy, ref_pitch};
   dispatch(h->storage, [&](auto tag) {
     using T = decltype(tag);
-    lbmk::reduce_kernel<T, kNoAllocThreads><<<(int)blocks, kNoAllocThreads, 0, h->stream>>>(
+    lbmk::reduce_kernel<T, kNoAllocThreads><<<blocks, kNoAllocThreads, 0, h->stream>>>(
         static_cast<const T*>(h->buf[h->cur]), geom(h), lbmk::shift_as<typename lbmk::Store<T>::C>(zshift(h)), ref,
         h->nsbc.m0[0], h->nsbc.m0[1], h->nsbc.m0[2], partials);
   });
-  lbmk::reduce_finish<kNoAllocThreads><<<1, kNoAllocThreads, 0, h->stream>>>(partials, (int)blocks, d_out);
+  lbmk::reduce_finish<kNoAllocThreads><<<1, kNoAllocThreads, 0, h->stream>>>(partials, blocks, d_out);
   rc = check_launch();
   if (rc) return rc;
   LBM_CUDA(cudaMemcpyAsync(out, d_out, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));

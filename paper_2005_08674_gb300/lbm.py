@@ -41,7 +41,7 @@ _i32p = ctypes.POINTER(ctypes.c_int32)
 _SIGS = {
     "lbm_create": (_vp, [_i32, _i32, _dbl, _dbl, _dp]),
     "lbm_destroy": (None, [_vp]),
-    "lbm_set_nsbc": (ctypes.c_int, [_vp, _dbl, _dbl, _dbl, _i32]),
+    "lbm_set_nsbc": (ctypes.c_int, [_vp, _dbl, _dbl, _dbl, _i32, _i32]),
     "lbm_set_precision": (ctypes.c_int, [_vp, _i32]),
     "lbm_set_collision": (ctypes.c_int, [_vp, _i32, _dbl, _dbl, _dbl]),
     "lbm_set_edges": (ctypes.c_int, [_vp, _vp, _vp]),
@@ -61,7 +61,8 @@ _SIGS = {
     "lbm_set_populations": (ctypes.c_int, [_vp, _vp]),
     "lbm_reduce": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _dp]),
     "lbm_save_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_int64)]),
-    "lbm_load_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t, ctypes.c_int64]),
+    "lbm_load_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
+    "lbm_state_bytes": (ctypes.c_size_t, [_vp]),
     "lbm_set_launch": (ctypes.c_int, [_vp, _i32, _i32, _i32]),
     "lbm_autotune": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _dp]),
     "lbm_set_staged": (ctypes.c_int, [_vp, _i32]),
@@ -70,11 +71,13 @@ _SIGS = {
     "lbm_get_fused": (ctypes.c_int32, [_vp]),
     "lbm_status": (ctypes.c_int, [_vp]),
     "lbm_reduce_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _dp]),
+    "lbm_set_tune_cache": (ctypes.c_int, [ctypes.c_char_p]),
+    "lbm_tune_cache_stats": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "lbm_profile": (ctypes.c_int, [_vp, _i32]),
     "lbm_profile_read": (ctypes.c_int, [_vp, _dp]),
     "lbm_batch_create": (_vp, [_i32, _vp, _i32]),
     "lbm_batch_destroy": (None, [_vp]),
-    "lbm_batch_set_nsbc": (ctypes.c_int, [_vp, _dbl, _dbl, _dbl, _i32]),
+    "lbm_batch_set_nsbc": (ctypes.c_int, [_vp, _dbl, _dbl, _dbl, _i32, _i32]),
     "lbm_batch_set_collision": (ctypes.c_int, [_vp, _i32, _dbl, _dbl, _dbl]),
     "lbm_batch_set_stream": (ctypes.c_int, [_vp, _vp]),
     "lbm_batch_cells": (ctypes.c_int64, [_vp]),
@@ -91,6 +94,7 @@ _SIGS = {
     "lbm_batch_autotune": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _dp]),
     "lbm_batch_status": (ctypes.c_int, [_vp]),
     "lbm_wait_selftest": (ctypes.c_int, [ctypes.c_int64]),
+    "lbm_partition_instances": (ctypes.c_int, [_i32, ctypes.POINTER(ctypes.c_int64), _i32, _i32p]),
     "lbm_last_error": (ctypes.c_char_p, []),
     "lbm_check_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_uint64), _i32]),
 }
@@ -158,8 +162,8 @@ def lbm_destroy(h):
     _L.lbm_destroy(h)
 
 
-def lbm_set_nsbc(h, gamma=0.6, beta=0.0, kappa=3.0, grad_order=1):
-    return _check(_L.lbm_set_nsbc(h, gamma, beta, kappa, grad_order))
+def lbm_set_nsbc(h, gamma=0.6, beta=0.0, kappa=3.0, corner_mode=0, grad_order=1):
+    return _check(_L.lbm_set_nsbc(h, gamma, beta, kappa, corner_mode, grad_order))
 
 
 def lbm_set_precision(h, storage):
@@ -278,17 +282,21 @@ def lbm_reduce(h, ref_rho: int = 0, ref_ux: int = 0, ref_uy: int = 0, ref_pitch:
     return list(out)
 
 
+def lbm_state_bytes(h) -> int:
+    return int(_L.lbm_state_bytes(h))
+
+
 def lbm_save_state(h):
-    """(raw state bytes as a numpy uint8 array, step count)."""
-    buf = np.empty(lbm_buffer_bytes(h), dtype=np.uint8)
+    """(checkpoint record as a numpy uint8 array, step count)."""
+    buf = np.empty(lbm_state_bytes(h), dtype=np.uint8)
     steps = ctypes.c_int64()
     _check(_L.lbm_save_state(h, _hp(buf), buf.nbytes, ctypes.byref(steps)))
     return buf, steps.value
 
 
-def lbm_load_state(h, buf, steps: int = 0):
+def lbm_load_state(h, buf):
     buf = np.ascontiguousarray(buf, dtype=np.uint8)
-    return _check(_L.lbm_load_state(h, _hp(buf), buf.nbytes, int(steps)))
+    return _check(_L.lbm_load_state(h, _hp(buf), buf.nbytes))
 
 
 def lbm_reduce_noalloc(h, ref_rho: int = 0, ref_ux: int = 0, ref_uy: int = 0, ref_pitch: int = 0,
@@ -305,6 +313,18 @@ def lbm_reduce_noalloc(h, ref_rho: int = 0, ref_ux: int = 0, ref_uy: int = 0, re
         return list(out)
     _check(rc)
     return list(out)
+
+
+def lbm_set_tune_cache(path):
+    """Autotuner cache file (None turns it off); see lbm.h."""
+    return _check(_L.lbm_set_tune_cache(None if path is None else os.fsencode(path)))
+
+
+def lbm_tune_cache_stats():
+    """(hits, misses) of the autotuner cache since the process started."""
+    hits, misses = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(_L.lbm_tune_cache_stats(ctypes.byref(hits), ctypes.byref(misses)))
+    return hits.value, misses.value
 
 
 def lbm_set_launch(h, threads_x: int, rows: int, prefetch_rows: int = 0):
@@ -356,14 +376,14 @@ class Simulation:
 
     def __init__(self, nx, ny, tau, farfield_rho=1.0, farfield_u=(0.0, 0.0), storage="f32",
                  gamma=0.6, beta=0.0, kappa=3.0, grad_order=1, stream=None, collision="bgk",
-                 mrt_rates=(1.0, 1.0, 1.0), edges=None):
+                 mrt_rates=(1.0, 1.0, 1.0), edges=None, corner_mode=0):
         import torch
         self.nx, self.ny, self.tau = nx, ny, tau
         self.storage = storage
         self.h = lbm_create(nx, ny, tau, farfield_rho, farfield_u)
         try:
             lbm_set_precision(self.h, storage)
-            lbm_set_nsbc(self.h, gamma, beta, kappa, grad_order)
+            lbm_set_nsbc(self.h, gamma, beta, kappa, corner_mode, grad_order)
             lbm_set_collision(self.h, collision, *mrt_rates)
             if edges is not None:
                 lbm_set_edges(self.h, edges)
@@ -397,8 +417,8 @@ class Simulation:
     def __exit__(self, *exc):
         self.close()
 
-    def set_nsbc(self, gamma=0.6, beta=0.0, kappa=3.0, grad_order=1):
-        lbm_set_nsbc(self.h, gamma, beta, kappa, grad_order)
+    def set_nsbc(self, gamma=0.6, beta=0.0, kappa=3.0, grad_order=1, corner_mode=0):
+        lbm_set_nsbc(self.h, gamma, beta, kappa, corner_mode, grad_order)
         return self
 
     def init(self, rho, ux, uy):
@@ -528,8 +548,8 @@ def lbm_batch_destroy(b):
     _L.lbm_batch_destroy(b)
 
 
-def lbm_batch_set_nsbc(b, gamma=0.6, beta=0.0, kappa=3.0, grad_order=1):
-    return _check(_L.lbm_batch_set_nsbc(b, gamma, beta, kappa, grad_order))
+def lbm_batch_set_nsbc(b, gamma=0.6, beta=0.0, kappa=3.0, corner_mode=0, grad_order=1):
+    return _check(_L.lbm_batch_set_nsbc(b, gamma, beta, kappa, corner_mode, grad_order))
 
 
 def lbm_batch_set_collision(b, model, omega_e=1.0, omega_eps=1.0, omega_q=1.0):
@@ -607,6 +627,15 @@ def lbm_batch_status(b):
     return _check(_L.lbm_batch_status(b))
 
 
+def lbm_partition_instances(cells, ranks: int):
+    """Rank of each instance for a node-balanced split over `ranks` (see lbm.h)."""
+    n = len(cells)
+    c = (ctypes.c_int64 * max(n, 1))(*[int(v) for v in cells])
+    out = (ctypes.c_int32 * max(n, 1))()
+    _check(_L.lbm_partition_instances(n, c, int(ranks), out))
+    return [int(out[k]) for k in range(n)]
+
+
 def lbm_wait_selftest(budget_cycles: int) -> int:
     """Status code of the bounded-wait check (LBM_ETIMEOUT expected)."""
     return int(_L.lbm_wait_selftest(int(budget_cycles)))
@@ -616,13 +645,13 @@ class Batch:
     """Independent instances stepped by one launch per step; torch allocates the pools."""
 
     def __init__(self, workloads, storage="f32", collision="bgk", mrt_rates=(1.0, 1.0, 1.0),
-                 gamma=0.6, beta=0.0, kappa=3.0, grad_order=1, stream=None, edges=None):
+                 gamma=0.6, beta=0.0, kappa=3.0, grad_order=1, stream=None, edges=None, corner_mode=0):
         import torch
         self.shapes = [(w.nx, w.ny) for w in workloads]
         descs = [(w.nx, w.ny, w.tau, w.farfield_rho, w.farfield_u[0], w.farfield_u[1]) for w in workloads]
         self.b = lbm_batch_create(descs, storage)
         try:
-            lbm_batch_set_nsbc(self.b, gamma, beta, kappa, grad_order)
+            lbm_batch_set_nsbc(self.b, gamma, beta, kappa, corner_mode, grad_order)
             lbm_batch_set_collision(self.b, collision, *mrt_rates)
             if edges is not None:
                 lbm_batch_set_edges(self.b, edges)

@@ -42,7 +42,9 @@ def main():
     kws = [dict(beta=0.1), dict(collision="mrt", mrt_rates=(1.4, 1.4, 1.2), grad_order=2),
            dict(edges=[("velocity", 0.03, 0.0), "nsbc", "periodic", "periodic"]),
            # a far field with a mean flow: the shifted form of every step kernel
-           dict(farfield_rho=1.001, farfield_u=(0.04, -0.01), beta=0.1, collision="mrt", mrt_rates=(1.4, 1.4, 1.2))]
+           dict(farfield_rho=1.001, farfield_u=(0.04, -0.01), beta=0.1, collision="mrt", mrt_rates=(1.4, 1.4, 1.2)),
+           # the second corner reading (an out-of-line second prediction at corners)
+           dict(farfield_u=(0.02, 0.01), corner_mode=1, grad_order=2)]
     for nx, ny in SIZES:
         fields = inputs.acoustic_pulse(nx, ny, 1e-3, 2.0, [((nx - 1) / 2, (ny - 1) / 2)])
         ref = oracle.Oracle(nx, ny, 0.6, beta=0.1).init(*fields).step(STEPS).macros()
@@ -64,8 +66,8 @@ def main():
     ws += [inputs.Workload("thin", 517, 4, 0.6, 0, farfield_u=(0.02, 0.0), kind="pulse",
                            params=dict(amplitude=1e-3, half_width=3.0, centres=[(100.0, 1.5)]))]
     for storage in ("f64", "f32", "f16"):
-        for launch in BATCH_LAUNCHES:
-            with lbm.Batch(ws, storage=storage, beta=0.05) as b:
+        for j, launch in enumerate(BATCH_LAUNCHES):
+            with lbm.Batch(ws, storage=storage, beta=0.05, corner_mode=j % 2) as b:
                 for k, w in enumerate(ws):
                     b.init(k, *w.fields())
                 b.set_launch(*launch)

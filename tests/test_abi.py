@@ -56,7 +56,10 @@ def test_host_side_argument_checks(lib_path):
     try:
         assert lbm.lbm_buffer_bytes(h) == 9 * 100 * 256 * 4  # pitch 200 -> 256, f32
         with pytest.raises(lbm.LbmError):
-            lbm.lbm_set_nsbc(h, 0.6, 0.0, 3.0, 3)
+            lbm.lbm_set_nsbc(h, 0.6, 0.0, 3.0, grad_order=3)
+        with pytest.raises(lbm.LbmError):
+            lbm.lbm_set_nsbc(h, 0.6, 0.0, 3.0, corner_mode=2)
+        lbm.lbm_set_nsbc(h, 0.6, 0.0, 3.0, corner_mode=1, grad_order=2)
         with pytest.raises(lbm.LbmError):
             lbm.lbm_set_precision(h, 7)
         lbm.lbm_set_precision(h, "f16")
@@ -74,14 +77,47 @@ def test_host_side_argument_checks(lib_path):
         assert lbm.lbm_get_staged(h) == 0
         import numpy as np
         with pytest.raises(lbm.LbmError, match="bytes given"):
-            lbm.lbm_load_state(h, np.zeros(100, dtype=np.uint8), 0)
-        with pytest.raises(lbm.LbmError, match="step count"):
-            lbm.lbm_load_state(h, np.zeros(lbm.lbm_buffer_bytes(h), dtype=np.uint8), -1)
+            lbm.lbm_load_state(h, np.zeros(100, dtype=np.uint8))
+        with pytest.raises(lbm.LbmError, match="not a checkpoint record"):
+            lbm.lbm_load_state(h, np.zeros(lbm.lbm_state_bytes(h), dtype=np.uint8))
         lbm.lbm_status(h)  # nothing launched yet: OK without touching the device
         assert lbm.lbm_steps_done(h) == 0
     finally:
         lbm.lbm_destroy(h)
     lbm.lbm_destroy(None)
+
+
+def _record(lbm, h, storage, nx, ny, pitch, steps, m0):
+    """A checkpoint record of lbm_state_bytes(h) bytes with the given header."""
+    import struct
+    import numpy as np
+    buf = np.zeros(lbm.lbm_state_bytes(h), dtype=np.uint8)
+    head = struct.pack("<8s6iq3d", b"LBMSTAT1", 1, storage, nx, ny, pitch, 0, steps, *m0)
+    buf[:64] = np.frombuffer(head, dtype=np.uint8)
+    return buf
+
+
+def test_checkpoint_record_is_checked_before_any_device_work():
+    """A record saved from an f16 handle has the byte count of a bf16 one of the
+    same size; loading it there would continue on garbage, so the header is
+    checked first (storage, size, pitch, far field, step count).  Host-only."""
+    from paper_2005_08674_gb300 import lbm
+    h = lbm.lbm_create(200, 100, 0.6, farfield_rho=1.0, farfield_u=(0.02, 0.0))
+    try:
+        lbm.lbm_set_precision(h, "bf16")
+        assert lbm.lbm_state_bytes(h) == 64 + lbm.lbm_buffer_bytes(h)
+        m0 = (1.0, 0.02, 0.0)
+        with pytest.raises(lbm.LbmError, match="storage") as e:
+            lbm.lbm_load_state(h, _record(lbm, h, lbm.LBM_F16, 200, 100, 256, 5, m0))
+        assert e.value.code == lbm.LBM_EINVAL
+        with pytest.raises(lbm.LbmError, match="storage"):
+            lbm.lbm_load_state(h, _record(lbm, h, lbm.LBM_BF16, 100, 200, 256, 5, m0))
+        with pytest.raises(lbm.LbmError, match="far field"):
+            lbm.lbm_load_state(h, _record(lbm, h, lbm.LBM_BF16, 200, 100, 256, 5, (1.0, 0.0, 0.0)))
+        with pytest.raises(lbm.LbmError, match="step count"):
+            lbm.lbm_load_state(h, _record(lbm, h, lbm.LBM_BF16, 200, 100, 256, -1, m0))
+    finally:
+        lbm.lbm_destroy(h)
 
 
 def test_ordinary_build_reports_no_checker(lib_path):

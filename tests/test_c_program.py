@@ -24,8 +24,9 @@ int main(void) {
   if (lbm_buffer_bytes(h) != (size_t)9 * 100 * 256 * 4) return 4; /* f32, pitch 256 */
   if (lbm_set_precision(h, LBM_F16) != LBM_OK) return 5;
   if (lbm_buffer_bytes(h) != (size_t)9 * 100 * 256 * 2) return 6;
-  if (lbm_set_nsbc(h, 0.6, 0.1, 3.0, 2) != LBM_OK) return 7;
-  if (lbm_set_nsbc(h, 0.6, 0.0, 3.0, 3) != LBM_EINVAL) return 8; /* order 3 does not exist */
+  if (lbm_set_nsbc(h, 0.6, 0.1, 3.0, LBM_CORNER_MEAN, 2) != LBM_OK) return 7;
+  if (lbm_set_nsbc(h, 0.6, 0.0, 3.0, LBM_CORNER_DIAGONAL, 3) != LBM_EINVAL) return 8; /* order 3 does not exist */
+  if (lbm_set_nsbc(h, 0.6, 0.0, 3.0, 2, 1) != LBM_EINVAL) return 8; /* no third corner reading */
   if (lbm_step(h, 1) != LBM_ESTATE) return 9;                     /* not initialised */
   if (lbm_set_staged(h, 3) != LBM_OK || lbm_get_staged(h) != 3) return 10;
   if (lbm_set_fused(h, 1) != LBM_OK || lbm_get_fused(h) != 1 || lbm_get_staged(h) != 0) return 11;

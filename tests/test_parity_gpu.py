@@ -1,7 +1,11 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
 Tolerances: GPU FP64 storage within 1e-12 of the oracle in rho and u; FP32
-storage within 1e-6 after 1000 steps at 200^2.  Sizes span several blocks
+storage within 1e-6 -- for pulse-200 after 1000 steps and for every other
+case too, the flows in a mean stream included: the kernels compute in
+deviations from the far field (rounding relative to the disturbance), which
+keeps the FP32 error of a 300-step vortex in a Ma 0.1 stream near 1e-7 and of
+the 4000-step 400^2 vortex near 1e-8.  Sizes span several blocks
 and a ragged row tail.  At the full 8192^2 size, sampled nodes are checked
 against oracle runs on small windows around them: after k steps a node
 depends only on nodes within distance k, and a window edge that is not a
@@ -73,7 +77,7 @@ def test_vortex_in_stream(lbm, storage, nsbc):
     ref = oracle_run(w, 300, **nsbc)
     got = gpu_run(lbm, w, storage, 300, **nsbc)
     err = max_err(got, ref)
-    assert err <= TOL[storage] * (10 if storage == "f32" else 1), err
+    assert err <= TOL[storage], err
 
 
 @pytest.mark.parametrize("nx,ny", [(3, 3), (4, 3), (5, 7), (33, 17), (65, 3), (131, 67), (257, 130), (1031, 9)])
@@ -196,13 +200,52 @@ def test_full_size_8192_sampled(lbm, storage, launch):
     assert worst <= TOL[storage], worst
 
 
-def _sampled_error(sim, fields, nx, ny, tau, k, samples):
+EDGE_K = 20
+EDGE_CENTRES_8192 = [(12.0, 9.0), (8178.0, 11.0), (10.0, 8178.0), (8182.0, 8181.0),
+                     (4097.0, 14.0), (16.0, 5000.0), (8170.0, 3333.0), (6000.0, 8173.0)]
+EDGE_SAMPLES_8192 = [(0, 0), (8191, 0), (0, 8191), (8191, 8191), (1, 0), (0, 1), (8190, 8191),
+                     (4097, 0), (4090, 0), (0, 5000), (0, 4993), (8191, 3333), (8191, 3340),
+                     (6000, 8191), (6011, 8191)]
+
+
+@pytest.mark.parametrize("launch", ["staged", "autotuned"])
+def test_full_size_8192_edges_and_corners(lbm, launch):
+    """8192^2 in f32 with eight narrow pulses (HWHM 8, amplitude 1e-3) within 9-22
+    nodes of the edges: four next to the corners, four next to the middle of
+    each edge.  After 20 steps every sampled edge and corner node carries a
+    disturbance of at least 1e-5 (checked on the oracle windows), so the NSBC
+    arithmetic of Sec. 5 (Eqs. nes_0-nes_4, corners included) is compared with
+    the oracle at the bench's size and in its launch forms: the staged step
+    kernel (perimeter chunks interleaved with the interior tiles) and the
+    autotuned launch.  Tolerance 1e-6, as for pulse-200."""
+    import torch
+    nx = ny = 8192
+    tau = 0.55
+    fields = inputs.acoustic_pulse(nx, ny, 1e-3, 8.0, EDGE_CENTRES_8192)
+    sim = lbm.Simulation(nx, ny, tau, storage="f32")
+    sim.init(*fields)
+    if launch == "staged":
+        sim.set_staged(3)
+    else:
+        sim.autotune()
+    sim.step(EDGE_K)
+    sim.status()
+    worst, weakest = _sampled_error(sim, fields, nx, ny, tau, EDGE_K, EDGE_SAMPLES_8192, disturbance=True)
+    sim.close()
+    del fields
+    torch.cuda.empty_cache()
+    assert weakest >= 1e-5, weakest
+    assert worst <= TOL["f32"], worst
+
+
+def _sampled_error(sim, fields, nx, ny, tau, k, samples, disturbance=False):
     """Largest |difference| of (rho, ux, uy) between the device state after k
     steps and oracle runs on windows around the sample nodes: a window of
     radius k + 4 evolves like the whole domain, k steps on, wherever its own
     cut edges cannot reach (information moves one node per step)."""
     mac = sim.macros_device()
     worst = 0.0
+    weakest = math.inf  # smallest disturbance |rho - 1| + |u| at a sample node (oracle)
     for (cx, cy) in samples:
         x0, x1, y0, y1 = _window(nx, ny, cx, cy, k)
         sub = [np.ascontiguousarray(a[y0:y1, x0:x1]) for a in fields]
@@ -217,8 +260,10 @@ def _sampled_error(sim, fields, nx, ny, tau, k, samples):
         assert ex1 > ex0 and ey1 > ey0
         for c in range(3):
             worst = max(worst, float(np.abs(got[c][ey0:ey1, ex0:ex1] - ref[c][ey0:ey1, ex0:ex1]).max()))
+        sy, sx = cy - y0, cx - x0
+        weakest = min(weakest, abs(ref[0][sy, sx] - 1) + abs(ref[1][sy, sx]) + abs(ref[2][sy, sx]))
     del mac
-    return worst
+    return (worst, weakest) if disturbance else worst
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
@@ -265,7 +310,7 @@ def test_mrt_vortex_in_stream(lbm, storage, rates):
     ref = oracle_run(w, 300, beta=0.05, collision="mrt", mrt_rates=_oracle_mrt_rates(rates, w.tau))
     got = gpu_run(lbm, w, storage, 300, beta=0.05, collision="mrt", mrt_rates=rates)
     err = max_err(got, ref)
-    assert err <= TOL[storage] * (10 if storage == "f32" else 1), err
+    assert err <= TOL[storage], err
 
 
 def test_vortex_400_mrt_4000_steps(lbm):
@@ -279,7 +324,7 @@ def test_vortex_400_mrt_4000_steps(lbm):
     assert all(np.isfinite(a).all() for a in ref)
     got = gpu_run(lbm, w, "f32", 4000, collision="mrt", mrt_rates=rates)
     err = max_err(got, ref)
-    assert err <= 1e-5, err
+    assert err <= TOL["f32"], err
 
 
 def test_instability_is_reported_not_faulted(lbm):
@@ -337,7 +382,7 @@ def test_paper_vortex_setup_f32(lbm):
                      mrt_rates=_oracle_mrt_rates(PAPER_VORTEX_RATES, tau))
     got = gpu_run(lbm, w, "f32", 1200, edges=[("velocity", u0, 0.0), "nsbc", "periodic", "periodic"],
                   collision="mrt", mrt_rates=PAPER_VORTEX_RATES)
-    assert max_err(got, ref) <= 1e-5
+    assert max_err(got, ref) <= TOL["f32"]
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])
@@ -352,7 +397,7 @@ def test_paper_plane_wave_setup(lbm, storage):
     ref = oracle_run(w, 240, collision="mrt", mrt_rates=_oracle_mrt_rates(PAPER_WAVE_RATES, tau))
     got = gpu_run(lbm, w, storage, 240, collision="mrt", mrt_rates=PAPER_WAVE_RATES)
     err = max_err(got, ref)
-    assert err <= TOL[storage] * (10 if storage == "f32" else 1), err
+    assert err <= TOL[storage], err
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
@@ -367,7 +412,7 @@ def test_checkpoint_resume_is_bit_exact(lbm, storage):
         straight = a.populations()
     assert steps == 70
     with lbm.Simulation(w.nx, w.ny, w.tau, storage=storage) as b:
-        lbm.lbm_load_state(b.h, state, steps)
+        lbm.lbm_load_state(b.h, state)
         b.step(45)
         assert b.steps == 115
         resumed = b.populations()

@@ -70,12 +70,16 @@ def test_noalloc_on_a_small_domain_after_a_large_one(lbm):
     small.close()
 
 
-def test_noalloc_rejects_domains_beyond_its_limit(lbm):
-    """Host-side check, before any device work: more than 8192^2 nodes is refused."""
-    h = lbm.lbm_create(8193, 8192, 0.6)
-    try:
-        with pytest.raises(lbm.LbmError) as e:
-            lbm.lbm_reduce_noalloc(h)
-        assert e.value.code == lbm.LBM_EINVAL and "limit" in str(e.value)
-    finally:
-        lbm.lbm_destroy(h)
+@pytest.mark.gpu
+@pytest.mark.parametrize("nx,ny", [(65536, 5), (8193, 8192)])
+def test_noalloc_wide_and_large_domains(lbm, nx, ny):
+    """A domain wider than it is tall (65,536 x 5: five blocks, one per row)
+    and one with more rows than the array has block slots (8193 x 8192: 4096
+    blocks, two rows each) give lbm_reduce's sums."""
+    import torch
+    fields = inputs.acoustic_pulse(nx, ny, 1e-3, 3.0, [(nx / 3, ny / 2)])
+    with lbm.Simulation(nx, ny, 0.6, storage="f32") as sim:
+        sim.init(*fields).step(3)
+        _close(lbm.lbm_reduce(sim.h), lbm.lbm_reduce_noalloc(sim.h))
+    del fields
+    torch.cuda.empty_cache()
