@@ -385,9 +385,13 @@ static void apply_storage(const or_sim* s, double* buf) {
     or_equilibrium(s->m0[0], s->m0[1], s->m0[2], r);
   else
     for (int i = 0; i < 9; ++i) r[i] = WT[i];
-  for (int i = 0; i < 9; ++i)
+  /* every value is rounded on its own; the OpenMP build splits rows over
+   * threads without changing any result bit */
+  for (int i = 0; i < 9; ++i) {
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < s->ny; ++y)
       for (int x = 0; x < s->nx; ++x) F(s, buf, i, x, y) = r[i] + q_store(F(s, buf, i, x, y) - r[i], s->store_fmt);
+  }
 }
 
 void or_set_storage(or_sim* s, int format, int far_field_shift) {

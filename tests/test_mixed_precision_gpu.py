@@ -11,6 +11,14 @@ measured the same way, and a convected vortex crossing the outflow edge
 (200^2, MRT, 800 steps) is measured likewise with its mean flow through the
 edges.  If LBM_RESULTS_DIR is
 set, the figures are written there as JSON.
+
+f32 and f16 are held to the bars.  bf16 does not meet them: on both flows its
+8 significant bits alone -- the oracle with only its stored populations
+rounded through bfloat16, all arithmetic in double -- already miss a bar
+(R_max by 1.2 % on the pulse, density by 1.4e-4 on the vortex).  Its tests
+record whether the bars are met (they are not) and hold the GPU to what the
+format loses: density error and R_max change within 3x of that storage
+emulation's.
 """
 import json
 import os
@@ -45,22 +53,49 @@ def reference():
     test = oracle.Oracle(w.nx, w.ny, w.tau, openmp=True).init(*f0)
     z = np.zeros_like(f0[0])
     e0 = R.energy(*f0, np.ones_like(z), z, z)
+    # what each 16-bit format alone loses: the oracle with its stored
+    # populations rounded through that format, arithmetic in double
+    emul = {fmt: oracle.Oracle(w.nx, w.ny, w.tau, openmp=True).storage(fmt, True).init(*f0)
+            for fmt in ("f16", "bf16")}
     refs, rs = [], []
+    rs_emul = {fmt: [] for fmt in emul}
     for _ in range(STEPS // EVERY):
         big.step(EVERY)
         test.step(EVERY)
         ref = R.window(big.macros(), P, w.nx, w.ny)
         refs.append(ref)
         rs.append(R.energy(*test.macros(), *ref) / e0)
+        for fmt, o in emul.items():
+            rs_emul[fmt].append(R.energy(*o.step(EVERY).macros(), *ref) / e0)
     final = test.macros()
-    return dict(w=w, f0=f0, refs=refs, e0=e0, r_max=max(rs), final=final)
+    emulated = {fmt: dict(drho=float(np.abs(o.macros()[0] - final[0]).max()),
+                          r_change=abs(max(rs_emul[fmt]) - max(rs)) / max(rs)) for fmt, o in emul.items()}
+    return dict(w=w, f0=f0, refs=refs, e0=e0, r_max=max(rs), final=final, emulated=emulated)
 
 
-# Bars: density error 1e-4 and reflection change 1 % for f16 (the target for the
-# 16-bit form).  bf16 keeps only 8 significant bits: its rounding noise adds
-# energy of its own, and R_max lands 0.4 % to 1.6 % above the oracle's depending
-# on rounding details of the boundary arithmetic; it is held to 2 %.
-@pytest.mark.parametrize("storage,rho_tol,r_tol", [("f16", 1e-4, 0.01), ("bf16", 1e-4, 0.02), ("f32", 1e-6, 0.01)])
+def _check(res, storage, rho_tol, r_tol, emulated):
+    """f32 / f16: the bars.  bf16: within 3x of what the format alone loses
+    (its storage emulation), with the bar verdict recorded."""
+    res["meets_bar"] = bool(res["max_abs_drho"] <= rho_tol and res["r_change"] <= r_tol)
+    out = os.environ.get("LBM_RESULTS_DIR")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, f"{res['case']}_{storage}.json"), "w") as f:
+            json.dump(res, f)
+    print(res)
+    if storage == "bf16":
+        e = emulated["bf16"]
+        assert res["max_abs_drho"] <= 3.0 * e["drho"], res
+        assert res["r_change"] <= 3.0 * max(e["r_change"], 1e-3), res
+    else:
+        assert res["meets_bar"], res
+        if storage in emulated:
+            assert res["max_abs_drho"] <= 3.0 * emulated[storage]["drho"], res
+
+
+# Bars: density error 1e-4 and reflection change 1 % for the 16-bit forms
+# (f32: 1e-6).  bf16 misses the R_max bar here (emulated: 1.2 %).
+@pytest.mark.parametrize("storage,rho_tol,r_tol", [("f16", 1e-4, 0.01), ("bf16", 1e-4, 0.01), ("f32", 1e-6, 0.01)])
 def test_storage_error_and_reflection(lbm, reference, storage, rho_tol, r_tol):
     w = reference["w"]
     sim = lbm.Simulation(w.nx, w.ny, w.tau, storage=storage).init(*reference["f0"])
@@ -75,16 +110,11 @@ def test_storage_error_and_reflection(lbm, reference, storage, rho_tol, r_tol):
     d_u = float(max(np.abs(got[1] - ref_final[1]).max(), np.abs(got[2] - ref_final[2]).max()))
     r_max = max(rs)
     change = abs(r_max - reference["r_max"]) / reference["r_max"]
-    res = dict(storage=storage, workload="pulse-1024, 2000 steps", max_abs_drho=d_rho, max_abs_du=d_u,
-               r_max=r_max, r_max_oracle=reference["r_max"], r_change=change)
-    out = os.environ.get("LBM_RESULTS_DIR")
-    if out:
-        os.makedirs(out, exist_ok=True)
-        with open(os.path.join(out, f"mixed_{storage}.json"), "w") as f:
-            json.dump(res, f)
-    print(res)
-    assert d_rho <= rho_tol, res
-    assert change <= r_tol, res
+    emulated = reference["emulated"]
+    res = dict(case="mixed", storage=storage, workload="pulse-1024, 2000 steps", max_abs_drho=d_rho,
+               max_abs_du=d_u, r_max=r_max, r_max_oracle=reference["r_max"], r_change=change,
+               oracle_storage_emulation=emulated.get(storage))
+    _check(res, storage, rho_tol, r_tol, emulated)
 
 
 # A convected vortex leaving the domain (Sec. 7's situation): 200^2, tau 0.505,
@@ -125,15 +155,15 @@ def vortex_reference():
     emulated = {}
     for fmt in ("f16", "bf16"):
         o = oracle.Oracle(V_N, V_N, V_TAU, 1.0, (u0, 0.0), **kw).storage(fmt, True).init(*f0)
-        emulated[fmt] = float(np.abs(o.step(V_STEPS).macros()[0] - final[0]).max())
+        re = [R.energy(*o.step(V_EVERY).macros(), *r) / e0 for r in refs]
+        emulated[fmt] = dict(drho=float(np.abs(o.macros()[0] - final[0]).max()),
+                             r_change=abs(max(re) - max(rs)) / max(rs))
     return dict(u0=u0, f0=f0, refs=refs, e0=e0, r_max=max(rs), final=final, emulated=emulated)
 
 
-# f32 and f16 meet the bars (density error 1e-4 for 16-bit storage, R_max
-# change 1 %).  bf16 keeps 8 significant bits: on this flow its density error
-# is 1.4e-4, above the 1e-4 bar, and R_max moves by 2.8 %; it is reported
-# beside the others and held to 5e-4 and 10 %.
-@pytest.mark.parametrize("storage,rho_tol,r_tol", [("f32", 1e-5, 0.01), ("f16", 1e-4, 0.01), ("bf16", 5e-4, 0.10)])
+# Bars: density error 1e-4 for 16-bit storage (f32: 1e-6), R_max change 1 %.
+# bf16 misses the density bar on this flow (emulated: 1.4e-4).
+@pytest.mark.parametrize("storage,rho_tol,r_tol", [("f32", 1e-6, 0.01), ("f16", 1e-4, 0.01), ("bf16", 1e-4, 0.01)])
 def test_vortex_storage_error_and_reflection(lbm, vortex_reference, storage, rho_tol, r_tol):
     ref = vortex_reference
     sim = lbm.Simulation(V_N, V_N, V_TAU, 1.0, (ref["u0"], 0.0), storage=storage, collision="mrt",
@@ -148,18 +178,10 @@ def test_vortex_storage_error_and_reflection(lbm, vortex_reference, storage, rho
     d_u = float(max(np.abs(got[1] - ref["final"][1]).max(), np.abs(got[2] - ref["final"][2]).max()))
     r_max = max(rs)
     change = abs(r_max - ref["r_max"]) / ref["r_max"]
-    res = dict(storage=storage, workload=f"vortex leaving a {V_N}^2 domain, MRT, {V_STEPS} steps",
+    emulated = ref["emulated"]
+    res = dict(case="vortex", storage=storage, workload=f"vortex leaving a {V_N}^2 domain, MRT, {V_STEPS} steps",
                max_abs_drho=d_rho, max_abs_du=d_u, r_max=r_max, r_max_oracle=ref["r_max"], r_change=change,
-               oracle_storage_emulation_drho=ref["emulated"].get(storage))
-    out = os.environ.get("LBM_RESULTS_DIR")
-    if out:
-        os.makedirs(out, exist_ok=True)
-        with open(os.path.join(out, f"vortex_{storage}.json"), "w") as f:
-            json.dump(res, f)
-    print(res)
-    assert d_rho <= rho_tol, res
-    assert change <= r_tol, res
-    if storage in ref["emulated"]:
-        # the 16-bit error is the storage format's: within a factor of 3 of the
-        # oracle run that loses only what that storage loses
-        assert d_rho <= 3.0 * ref["emulated"][storage], res
+               oracle_storage_emulation=emulated.get(storage))
+    # the 16-bit error is the storage format's: within a factor of 3 of the
+    # oracle run that loses only what that storage loses
+    _check(res, storage, rho_tol, r_tol, emulated)
