@@ -52,6 +52,8 @@ def parse():
                         "(both in one launch) or 'staged3' / 'staged4' instead of autotuning")
     p.add_argument("--batched-only", action="store_true", help="time only the batched workload")
     p.add_argument("--batch-launch", default="", help="batched launch 'threads_x,rows,blocks,prefetch,split'")
+    p.add_argument("--batch-count", type=int, default=256,
+                   help="instances of the batched workload (--batched-only; fewer for profiling captures)")
     return p.parse_args()
 
 
@@ -241,13 +243,29 @@ def aggregate_mlups(cells_per_rank: int, steps: int, ms_max: float, world: int) 
     return world * cells_per_rank * steps / (ms_max * 1e-3) / 1e6
 
 
-BATCH_WHAT = ("256 instances 64..1024 per side, tau 0.51..0.8, pulses and vortices, "
-              "one persistent launch per step replayed from a CUDA graph")
+def batch_what(count: int = 256) -> str:
+    return (f"{count} instances 64..1024 per side, tau 0.51..0.8, pulses and vortices, "
+            "one persistent launch per step replayed from a CUDA graph")
 
 
-def run_batched(lbm, ws, bfields, storage, steps, warmup, world, peak, launch=None):
-    """The batched workload: MLUPS over all instances, CUDA events on the stream."""
+def shard(cells, rank: int, world: int, partition):
+    """Indices of the instances this rank steps: a node-balanced split of the
+    independent instances over the ranks (no data moves between ranks)."""
+    if world == 1:
+        return list(range(len(cells)))
+    owner = partition(cells, world)
+    return [k for k, r in enumerate(owner) if r == rank]
+
+
+def run_batched(lbm, ws, bfields, storage, steps, warmup, world, peak, launch=None, rank=0, device="cuda"):
+    """The batched workload: MLUPS over all instances, CUDA events on the
+    stream.  With several ranks the instances are sharded (lbm_partition_
+    instances) and the job time is the slowest rank's."""
     import torch
+    all_ws = ws
+    total_cells = sum(w.nx * w.ny for w in ws)
+    mine = shard([w.nx * w.ny for w in ws], rank, world, lbm.lbm_partition_instances)
+    ws, bfields = [ws[k] for k in mine], [bfields[k] for k in mine]
     bt = lbm.Batch(ws, storage=storage)
     for k, f in enumerate(bfields):
         bt.init(k, *f)
@@ -268,11 +286,15 @@ def run_batched(lbm, ws, bfields, storage, steps, warmup, world, peak, launch=No
     bt.status()  # raises if a bounded device-side wait gave up
     bad = sum(bt.unstable_nodes(k) for k in range(len(ws)))
     gbs = BYTES_PER_CELL[storage] * bt.cells * steps / (bms * 1e-3) / 1e9
-    out = {"mlups": world * bt.cells * steps / (bms * 1e-3) / 1e6, "steps": steps, "ms_per_step": bms / steps,
+    ms_max = max_over_ranks(bms, device) if world > 1 else bms
+    out = {"mlups": total_cells * steps / (ms_max * 1e-3) / 1e6, "steps": steps, "ms_per_step": ms_max / steps,
            "instances": len(ws), "cells": bt.cells, "step_gbs": gbs, "step_frac": gbs / peak,
+           "sharding": (f"{world} ranks, instances split by nodes (lbm_partition_instances), no exchange; "
+                        f"rank {rank} steps {len(ws)} instances, {bt.cells} nodes of {total_cells}")
+           if world > 1 else "one rank, all instances",
            "launch": {"threads_x": tb, "rows": tr, "blocks": tg, "prefetch_rows": tp, "split": ts,
                       "tma_tile": tt},
-           "unstable_nodes": bad, "what": BATCH_WHAT}
+           "unstable_nodes": bad, "what": batch_what(len(all_ws))}
     bt.close()
     del bt
     torch.cuda.empty_cache()
@@ -309,17 +331,19 @@ def run_batched_only(args, rank, world, local_rank):
     build.build()
     from paper_2005_08674_gb300 import inputs, lbm
     torch.cuda.set_device(local_rank)
-    ws = inputs.batch_instances()
+    ws = inputs.batch_instances(count=args.batch_count)
     bfields = [w.fields() for w in ws]
     peak, _ = measured_peak_gbs()
     launch = [int(v) for v in args.batch_launch.split(",")] if args.batch_launch else None
-    r = run_batched(lbm, ws, bfields, args.storage, args.steps, args.warmup, world, peak, launch)
+    r = run_batched(lbm, ws, bfields, args.storage, args.steps, args.warmup, world, peak, launch, rank)
     if rank == 0:
         print(json.dumps({"metric": METRIC, "value": r["mlups"], "unit": UNIT, "n_gpus": world,
                           "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
-                          "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                          "dtype": args.storage, "data": "synthetic",
-                          "config": {"workload": "batched: " + BATCH_WHAT}, "batched": r}), flush=True)
+                          "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
+                          "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+                          "config": {"workload": "batched: " + batch_what(len(ws)),
+                                     "parallelism": "instances sharded by nodes" if world > 1 else "single-gpu"},
+                          "batched": r}), flush=True)
 
 
 def run_ours(args, rank, world, local_rank):
@@ -538,9 +562,10 @@ def run_ours(args, rank, world, local_rank):
         bfields = [w.fields() for w in ws]
         bsteps = min(args.steps, 1000)
         for st in ("f32", "f16"):
-            variants[f"batched_{st}"] = run_batched(lbm, ws, bfields, st, bsteps, args.warmup, world, peak)
+            variants[f"batched_{st}"] = run_batched(lbm, ws, bfields, st, bsteps, args.warmup, world, peak,
+                                                    rank=rank)
             one = run_one_at_a_time(lbm, ws, bfields, st, 64)
-            one["batched_speedup"] = variants[f"batched_{st}"]["mlups"] / world / one["mlups"]
+            one["batched_speedup"] = variants[f"batched_{st}"]["mlups"] / world / one["mlups"]  # per GPU
             variants[f"batched_{st}"]["one_at_a_time"] = one
         del bfields
         if line is not None:
