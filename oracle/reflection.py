@@ -2,8 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
-The paper judges reflections from figures only ("nearly zero" for the
-acoustic test of Sec. 6, "fully absorbed" for the vortex of Sec. 7), so the
+The paper judges reflections from figures only (close to zero for the
+acoustic test of Sec. 6, complete absorption for the vortex of Sec. 7), so the
 number used here is defined for this project:
 
   E[a, b] = sum over the window of  ( cs^2 (rho_a - rho_b)^2 / rho0 + rho0 |u_a - u_b|^2 ) / 2

@@ -5,7 +5,7 @@ itself: they check closed forms (equilibrium moment identities, the BGK
 relaxation factor, exact transport of the far-field state), physical laws the
 scheme must reproduce (viscosity nu = cs^2 (tau - 1/2), sound speed cs), the
 paper's stated findings (gamma = 0.6 gives the least reflection for D2Q9,
-reflections "nearly zero"), and special cases where the boundary rule reduces
+reflections close to zero), and special cases where the boundary rule reduces
 to an exact answer (the symmetry assumption of Eq. nes_0 holding exactly,
 beta = 1, second-order differences of a quadratic).
 """
@@ -253,7 +253,7 @@ def _smooth_fields(nx, ny, seed):
 
 @pytest.mark.parametrize("gamma,beta", [(0.6, 0.0), (0.45, 0.25)])
 def test_correction_conserves_predicted_moments(gamma, beta):
-    """Eq. nes_4 exists to 'guarantee conservation of the macroscopic moments':
+    """Eq. nes_4 is meant to make the corrected node carry the predicted moments:
     after a step, each edge node carries exactly rho_c and u_c of Eqs. nes_2/nes_3
     (the collision keeps them).  That holds with momentum factor 1/cs^2 = 3; the
     factor 1 as printed leaves 2/3 of the momentum error (the reading taken)."""
@@ -377,7 +377,7 @@ def test_centred_pulse_keeps_mirror_symmetries(corner):
 
 
 def test_pulse_reflection_nearly_zero():
-    """Sec. 6 reports reflections 'nearly zero'.  For a 2-D pulse reaching all four
+    """Sec. 6 reports reflections close to zero.  For a 2-D pulse reaching all four
     edges and corners, R_max with gamma = 0.6 is below 1e-3 and more than 50x below the
     far-field clamp (beta = 1)."""
     n, T = 48, 100
@@ -463,7 +463,7 @@ def test_paper_vortex_setup_is_fully_absorbed():
     """Sec. 7's set-up: 128^2, u0 = 0.1, beta u0 = 0.05, R_c = 20, Re = 1000 (tau from
     nu = u0 l / Re), velocity inlet on the left, NSBC on the right, periodic top and
     bottom, MRT with omega_e = omega_eps = 1.4, omega_q = 1.2.  The paper reports the
-    vortex 'fully absorbed': after it has crossed the outlet, the disturbance energy
+    vortex as absorbed completely: after it has crossed the outlet, the disturbance energy
     left in the domain is below 1e-4 of the initial one."""
     n, u0 = 128, 0.1
     tau = 0.5 + 3 * u0 * n / 1000

@@ -1,7 +1,7 @@
 """Sec. 6's acoustic experiment on the FP64 oracle: a Gaussian plane wave at
 60 degrees on 128^2 (zeta = 0.01, lambda = l/32, MRT rates 1.9, viscosity
 close to zero: tau = 0.5001 stands in for tau = 0.5), NSBC on every edge.
-The paper shows the reflections only as a figure ("nearly zero").  The
+The paper shows the reflections only as a figure (close to zero).  The
 number here is the reflected-energy ratio R of oracle/reflection.py against
 the same initial state on a padded domain, and the check is the ordering the
 paper's claim implies: the NSBC reflects several times less than two edges
