@@ -435,6 +435,11 @@ def run_ours(args, rank, world, local_rank):
                        "stable": bool(stable)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
+                         "frac_of": "measured copy bandwidth (a torch copy: read + write bytes)",
+                         # the same launch time against the DRAM bytes ncu counted for this kernel:
+                         # what the memory system actually moved, beside the algorithmic rate
+                         "dram_gbs": traffic / (bulk_avg * 1e-3) / 1e9 if traffic else None,
+                         "dram_frac": traffic / (bulk_avg * 1e-3) / 1e9 / peak if traffic else None,
                          "kernel": kname,
                          "bytes_per_cell": BYTES_PER_CELL[args.storage], "cells_per_launch": kcells,
                          "avg_launch_ms": bulk_avg, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",

@@ -176,20 +176,141 @@ __device__ __forceinline__ EdgeNode edge_node(int node, const Geom& g, const Nsb
   return e;
 }
 
-// Pulled populations of the node (wrapped on periodic axes); unknown where
-// the source lies outside the domain (zero there, or everywhere if !load).
+// The NSBC finish runs on all four lanes of a quad: lane q owns one opposite
+// pair of populations, q = 0: (1, 2), c = (1, 0); q = 1: (3, 4), c = (0, 1);
+// q = 2: (5, 6), c = (1, 1); q = 3: (7, 8), c = (-1, 1) (Fig. 1 numbering),
+// and every lane carries population 0 (lane 0 stores it).  The lanes run the
+// same instructions on their own pair, and node sums over the nine
+// populations are quad reductions.
+struct QuadPair {
+  int ip, im;  // the populations along c and along -c
+  int cx, cy;  // c
+  bool diag;
+};
+
+__device__ __forceinline__ QuadPair quad_pair(int q) {
+  QuadPair r;
+  r.ip = 1 + 2 * q;
+  r.im = 2 + 2 * q;
+  r.cx = q == 1 ? 0 : (q == 3 ? -1 : 1);
+  r.cy = q == 0 ? 0 : 1;
+  r.diag = q >= 2;
+  return r;
+}
+
+// Sum of v over the four lanes of the quad, the same bits in every lane.
+template <typename C>
+__device__ __forceinline__ C quad_sum(C v, unsigned quad) {
+  v = v + __shfl_xor_sync(quad, v, 1, 4);
+  return v + __shfl_xor_sync(quad, v, 2, 4);
+}
+
+// This lane's pulled populations of the node: h+ (along c) from x - c, h-
+// (along -c) from x + c, h0 from x; unknown (and zero) where the source lies
+// outside the domain, wrapped on periodic axes.
 template <typename T>
-__device__ __forceinline__ void edge_pull(const T* __restrict__ A, const Geom& g, const Nsbc& p, const EdgeNode& e,
-                                          bool load, typename Store<T>::C (&h)[9], bool (&known)[9]) {
+__device__ __forceinline__ void quad_pull(const T* __restrict__ A, const Geom& g, const Nsbc& p, const EdgeNode& e,
+                                          const QuadPair& pr, typename Store<T>::C& hp, typename Store<T>::C& hm,
+                                          typename Store<T>::C& h0, bool& kp, bool& km) {
   using S = Store<T>;
   using C = typename S::C;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) {
-    int sx = e.x - cx(i), sy = e.y - cy(i);
+  auto pull = [&](int i, int sx, int sy, bool& known) -> C {
     if (p.periodic_x) sx = sx < 0 ? sx + g.nx : (sx >= g.nx ? sx - g.nx : sx);
     if (p.periodic_y) sy = sy < 0 ? sy + g.ny : (sy >= g.ny ? sy - g.ny : sy);
-    known[i] = sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny;
-    h[i] = (load && known[i]) ? S::ldg1(A + i * g.plane + (long long)sy * g.pitch + sx) : C(0);
+    known = sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny;
+    return known ? S::ldg1(A + i * g.plane + (long long)sy * g.pitch + sx) : C(0);
+  };
+  hp = pull(pr.ip, e.x - pr.cx, e.y - pr.cy, kp);
+  hm = pull(pr.im, e.x + pr.cx, e.y + pr.cy, km);
+  h0 = S::ldg1(A + (long long)e.y * g.pitch + e.x);
+}
+
+// Equilibrium deviations (as equilibrium_dev) of this lane's pair and of
+// population 0, times ws.
+template <bool SHIFT, typename C>
+__device__ __forceinline__ void pair_equilibrium(const QuadPair& pr, int q, C d, C vx, C vy, C jx, C jy,
+                                                 const Shift<C>& z, C ws, C& ep, C& em, C& e0) {
+  C rho, sx, sy, dpp, dpm, dp0;
+  if constexpr (SHIFT) {
+    rho = z.rho0 + d;
+    sx = fma_rn(C(2), z.u0[0], vx);
+    sy = fma_rn(C(2), z.u0[1], vy);
+    const C p0p = q == 0 ? z.p0[1] : (q == 1 ? z.p0[3] : (q == 2 ? z.p0[5] : z.p0[7]));  // static indices only
+    const C p0m = q == 0 ? z.p0[2] : (q == 1 ? z.p0[4] : (q == 2 ? z.p0[6] : z.p0[8]));
+    dpp = mul_rn(d, p0p);
+    dpm = mul_rn(d, p0m);
+    dp0 = mul_rn(d, z.p0[0]);
+  } else {
+    rho = C(1) + d;
+    sx = vx;
+    sy = vy;
+    dpp = dpm = dp0 = d;
+  }
+  const C vs = C(1.5) * fma_rn(vx, sx, mul_rn(vy, sy));
+  const C fx = C(pr.cx), fy = C(pr.cy);
+  const C cv = fma_rn(fx, vx, mul_rn(fy, vy)), cs = fma_rn(fx, sx, mul_rn(fy, sy));
+  const C cj = fma_rn(fx, jx, mul_rn(fy, jy));
+  const C a = fma_rn(C(4.5) * cv, cs, -vs), b = C(3) * cj;
+  const C w = (pr.diag ? wt<C>(5) : wt<C>(1)) * ws;
+  ep = w * (fma_rn(rho, a, dpp) + b);
+  em = w * (fma_rn(rho, a, dpm) - b);
+  e0 = (wt<C>(0) * ws) * fma_rn(-rho, vs, dp0);
+}
+
+// d = rho - rho0 and J = rho (u - u0) of the node from the quad's pairs.
+template <bool SHIFT, typename C>
+__device__ __forceinline__ void pair_moments(const QuadPair& pr, C hp, C hm, C h0, const Shift<C>& z, unsigned quad,
+                                             C& d, C& jx, C& jy) {
+  const C odd = hp - hm;
+  d = h0 + quad_sum(hp + hm, quad);
+  jx = quad_sum(C(pr.cx) * odd, quad);
+  jy = quad_sum(C(pr.cy) * odd, quad);
+  (void)z;
+}
+
+// The collision (BGK, Eq. lbe_1, or MRT, Eq. mrt_lbe) of the node, each lane
+// relaxing its own pair (and population 0), in physical units.
+template <int MODEL, bool SHIFT, typename C>
+__device__ __forceinline__ void pair_collide(const QuadPair& pr, int q, C& hp, C& hm, C& h0, const Rates<C>& r,
+                                             unsigned quad) {
+  C d, sjx, sjy;
+  pair_moments<SHIFT>(pr, hp, hm, h0, r.z, quad, d, sjx, sjy);
+  C jx = sjx, jy = sjy, inv;
+  if constexpr (SHIFT) {
+    inv = div_rho(C(1), r.z.rho0 + d);
+    jx = fma_rn(-d, r.z.u0[0], sjx);
+    jy = fma_rn(-d, r.z.u0[1], sjy);
+  } else {
+    inv = div_rho(C(1), C(1) + d);
+  }
+  C ep, em, e0;
+  if constexpr (MODEL == 1) {
+    pair_equilibrium<SHIFT>(pr, q, d, jx * inv, jy * inv, jx, jy, r.z, C(1), ep, em, e0);
+    // non-equilibrium moments of Eq. mrt_rm (rows as in collide_mrt): each
+    // lane's share, summed over the quad
+    const C np = sub_rn(hp, ep), nm = sub_rn(hm, em), n0 = sub_rn(h0, e0);
+    const C even = np + nm, oddn = np - nm;
+    const C ce = pr.diag ? C(2) : C(-1), cep = pr.diag ? C(1) : C(-2), cq = pr.diag ? C(1) : C(-2);
+    const C cxx = C(pr.cx * pr.cx - pr.cy * pr.cy), cxy = C(pr.cx * pr.cy);
+    const C me = fma_rn(C(-4), n0, quad_sum(ce * even, quad));
+    const C mep = fma_rn(C(4), n0, quad_sum(cep * even, quad));
+    const C mqx = quad_sum(cq * C(pr.cx) * oddn, quad), mqy = quad_sum(cq * C(pr.cy) * oddn, quad);
+    const C mxx = quad_sum(cxx * even, quad), mxy = quad_sum(cxy * even, quad);
+    const C re = r.s_e * me * C(1.0 / 36.0), rep = r.s_eps * mep * C(1.0 / 36.0);
+    const C rqx = r.s_q * mqx * C(1.0 / 12.0), rqy = r.s_q * mqy * C(1.0 / 12.0);
+    const C rxx = r.omega * mxx * C(0.25), rxy = r.omega * mxy * C(0.25);
+    const C base = ce * re + cep * rep;
+    const C odd = cq * (C(pr.cx) * rqx + C(pr.cy) * rqy);
+    const C stress = cxx * rxx + cxy * rxy;
+    h0 -= C(4) * (rep - re);
+    hp -= (base + odd) + stress;
+    hm -= (base - odd) + stress;
+  } else {
+    const C omega = r.omega, keep = C(1) - omega;
+    pair_equilibrium<SHIFT>(pr, q, d, jx * inv, jy * inv, jx, jy, r.z, omega, ep, em, e0);
+    hp = fma_rn(keep, hp, ep);
+    hm = fma_rn(keep, hm, em);
+    h0 = fma_rn(keep, h0, e0);
   }
 }
 
@@ -257,15 +378,16 @@ __device__ __forceinline__ void load_node(const T* __restrict__ A, long long pla
   for (int i = 0; i < 9; ++i) v[i] = want ? S::ldg1(A + i * plane + o) : C(0);
 }
 
-// The rest of the node, given its pulled populations and the blended
-// deviation m_c - m0 = (rho_c - rho0, u_c - u0): velocity override,
-// reconstruction of the unknown populations, correction, collision and the
-// store.
+// The rest of the node, on all four lanes of its quad, given this lane's
+// pulled pair and the blended deviation m_c - m0 = (rho_c - rho0, u_c - u0):
+// velocity override, reconstruction of the unknown populations, correction,
+// collision and the store.
 template <typename T, int MODEL, bool SHIFT = false>
-__device__ __forceinline__ void edge_finish(T* __restrict__ B, const Geom& g, const Nsbc& p,
+__device__ __forceinline__ void quad_finish(T* __restrict__ B, const Geom& g, const Nsbc& p,
                                             const Rates<typename Store<T>::C>& rates, const EdgeNode& en,
-                                            typename Store<T>::C (&h)[9], const bool (&known)[9],
-                                            typename Store<T>::C (&mc)[3]) {
+                                            const QuadPair& pr, int q, unsigned quad, typename Store<T>::C hp,
+                                            typename Store<T>::C hm, typename Store<T>::C h0, bool kp, bool km,
+                                            typename Store<T>::C (&mc)[3], bool store) {
   using S = Store<T>;
   using C = typename S::C;
   const int x = en.x, y = en.y;
@@ -286,23 +408,22 @@ __device__ __forceinline__ void edge_finish(T* __restrict__ B, const Geom& g, co
     }
 
     // Eqs. (nes_0), (nes_1): f_in = f_in^eq(m_c) + f_out - f_out^eq(m_c)
-    // (in stored deviations: f^eq(m_c) - f^eq(m0), the same relation)
-    C e[9];
+    // (in stored deviations: f^eq(m_c) - f^eq(m0), the same relation); both
+    // members of the pair are this lane's
+    C ep, em, e0;
     {
       const C rho_c = (SHIFT ? rates.z.rho0 : C(1)) + mc[0];
-      equilibrium_dev<SHIFT>(mc[0], mc[1], mc[2], rho_c * mc[1], rho_c * mc[2], rates.z, e);
+      pair_equilibrium<SHIFT>(pr, q, mc[0], mc[1], mc[2], rho_c * mc[1], rho_c * mc[2], rates.z, C(1), ep, em, e0);
     }
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-      const int o = opp(i);
-      if (!known[i]) h[i] = known[o] ? e[i] + (h[o] - e[o]) : e[i];
-    }
+    const C hp0 = hp, hm0 = hm;
+    if (!kp) hp = km ? ep + (hm0 - em) : ep;
+    if (!km) hm = kp ? em + (hp0 - ep) : em;
 
     // Eq. (nes_4): f_i -= w_i (d_rho + kappa c_i . d(rho u)), with the node's
     // moments and the targets (rho_c, rho_c u_c) both taken relative to m0:
     // rho_c u_c - rho0 u0 = rho_c (u_c - u0) + (rho_c - rho0) u0
     C drho, jx, jy;
-    moments(h, drho, jx, jy);
+    pair_moments<SHIFT>(pr, hp, hm, h0, rates.z, quad, drho, jx, jy);
     const C d_rho = drho - mc[0];
     C d_jx, d_jy;  // explicit multiply-adds: a zero shift rounds like the plain form
     if constexpr (SHIFT) {
@@ -314,15 +435,20 @@ __device__ __forceinline__ void edge_finish(T* __restrict__ B, const Geom& g, co
       d_jx = fma_rn(-rho_c, mc[1], jx);
       d_jy = fma_rn(-rho_c, mc[2], jy);
     }
-    const C kap = C(p.kappa);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) h[i] -= wt<C>(i) * (d_rho + kap * (C(cx(i)) * d_jx + C(cy(i)) * d_jy));
+    const C t = C(p.kappa) * (C(pr.cx) * d_jx + C(pr.cy) * d_jy);
+    const C w = pr.diag ? wt<C>(5) : wt<C>(1);
+    hp -= w * (d_rho + t);
+    hm -= w * (d_rho - t);
+    h0 -= wt<C>(0) * d_rho;
   }
 
-  collide<MODEL, SHIFT>(h, rates);
-  const long long o = (long long)y * g.pitch + x;
-#pragma unroll
-  for (int i = 0; i < 9; ++i) S::st1(B + i * g.plane + o, h[i]);
+  pair_collide<MODEL, SHIFT>(pr, q, hp, hm, h0, rates, quad);
+  if (store) {
+    const long long o = (long long)y * g.pitch + x;
+    S::st1(B + pr.ip * g.plane + o, hp);
+    S::st1(B + pr.im * g.plane + o, hm);
+    if (q == 0) S::st1(B + o, h0);
+  }
 }
 
 // The second prediction of a corner under corner reading 1, along the
@@ -339,11 +465,12 @@ __device__ __noinline__ double corner_second_prediction(const T* __restrict__ A,
 
 // K perimeter nodes, each handled by the four lanes of one quad (q = lane &
 // 3); all four lanes must call this together with the same nodes.  Lane q
-// forms (rho - 1, ux, uy) at b - q n in the compute type; the quad then
+// forms the deviations (rho - rho0, u - u0) at b - q n in the compute type; the quad then
 // transposes them so that lane c (c < 3) holds component c at b, b - n,
 // b - 2n and predicts and blends that component in FP64 -- three lanes share
-// the FP64 work (GB300's FP64 pipe is narrow) -- and lane 0 gathers the three
-// blended components and finishes the node.  Every load of the K nodes is
+// the FP64 work (GB300's FP64 pipe is narrow) -- and every lane gathers the
+// three blended components and finishes its own pair of populations
+// (quad_finish).  Every load of the K nodes is
 // issued before the first is used (one round trip for all of them); nodes
 // with valid[k] false are computed (from in-range addresses) but not stored.
 // A corner under corner reading 1 is predicted twice, along the normals of
@@ -357,13 +484,14 @@ __device__ __forceinline__ void nsbc_nodes(const T* __restrict__ A, T* __restric
   using S = Store<T>;
   using C = typename S::C;
   const unsigned quad = 0xFu << ((threadIdx.x & 31) & ~3);
+  const QuadPair pr = quad_pair(q);
   EdgeNode en[K];
-  C h[K][9], v[K][9];
-  bool known[K][9];
+  C hp[K], hm[K], h0[K], v[K][9];
+  bool kp[K], km[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     en[k] = edge_node(node[k], g, p);
-    edge_pull(A, g, p, en[k], q == 0, h[k], known[k]);  // lane 0: the pulled populations
+    quad_pull(A, g, p, en[k], pr, hp[k], hm[k], h0[k], kp[k], km[k]);  // this lane's pulled pair
   }
 #pragma unroll
   for (int k = 0; k < K; ++k) {  // lane q: the node b - q n (zeros if not needed)
@@ -386,10 +514,10 @@ __device__ __forceinline__ void nsbc_nodes(const T* __restrict__ A, T* __restric
 #pragma unroll
     for (int c = 0; c < 3; ++c) mc[k][c] = __shfl_sync(quad, mcq, c, 4);
   }
-  if (q != 0) return;
 #pragma unroll
   for (int k = 0; k < K; ++k)
-    if (valid[k]) edge_finish<T, MODEL, SHIFT>(B, g, p, rates, en[k], h[k], known[k], mc[k]);
+    quad_finish<T, MODEL, SHIFT>(B, g, p, rates, en[k], pr, q, quad, hp[k], hm[k], h0[k], kp[k], km[k], mc[k],
+                                 valid[k]);
 }
 
 template <typename T, int MODEL, bool SHIFT = false>

@@ -13,8 +13,11 @@ recomputes the CPU-sized ones and pins the orderings they show:
     difference reflects a little less, and the corner reading makes no
     difference (the wave's energy has left before it matters);
   * the vortex leaving a 200^2 domain (MRT, tau 0.505): with the first-order
-    difference R stays below 0.2, with the second-order one the run grows
-    without bound (R_max > 10 by step 800) under either corner reading;
+    difference R stays below 0.2 and the corner reading changes it by under
+    0.1 %; with the second-order one the oracle run grows without bound by
+    step 800 -- not because of the vortex: the second-order difference is
+    unstable on the inflow edge (tests/test_nsbc_stability.py), and the
+    oracle's rounding of absolute populations there seeds it;
   * the 400^2 BGK vortex at tau 0.505 blows up under every reading, more than
     twice as soon with the second-order difference, and the corner reading
     moves the step by at most 2 %: it does not cure the instability.
@@ -57,7 +60,8 @@ def test_orderings(measured):
     assert p["order1_mean"] < p["order1_diagonal"] < p["order2_mean"] < p["order2_diagonal"]
     assert w["order2_diagonal"] < 0.99 * w["order1_diagonal"]
     assert w["order1_mean"] == pytest.approx(w["order1_diagonal"], rel=1e-6)
-    assert v["order1_diagonal"] < 0.2 and v["order1_mean"] < 0.2
+    assert v["order1_diagonal"] < 0.2
+    assert v["order1_mean"] == pytest.approx(v["order1_diagonal"], rel=1e-3)
     assert v["order2_diagonal"] > 10 and v["order2_mean"] > 10
 
 
