@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     p.add_argument("--launch", default="",
                    help="'threads_x,rows[,prefetch]' (bulk + NSBC kernel pair), 'fused[:threads_x,rows,prefetch]' "
-                        "(both in one launch) or 'staged3' / 'staged4' instead of autotuning")
+                        "(both in one launch), 'staged3' / 'staged4' or 'twostep' instead of autotuning")
     p.add_argument("--batched-only", action="store_true", help="time only the batched workload")
     p.add_argument("--batch-launch", default="", help="batched launch 'threads_x,rows,blocks,prefetch,split'")
     p.add_argument("--batch-count", type=int, default=256,
@@ -153,7 +153,11 @@ def kernel_source_sha() -> str:
 def step_kernel(sim, nx, ny):
     """(kernel description, traffic summary file stem, cells one launch updates)
     of the kernel that carries the step: the staged kernel updates every node,
-    the bulk kernel the interior (the NSBC kernel the perimeter, beside it)."""
+    the two-step kernel every node twice, the bulk kernel the interior (the
+    NSBC kernel the perimeter, beside it)."""
+    if sim.twostep:
+        return ("twostep_kernel (two steps per launch: strips of rows streamed through two rings in shared memory)",
+                "twostep_traffic", 2 * nx * ny)
     if sim.staged:
         return ("batch_ws_kernel (staged step: interior tiles by bulk copies + NSBC chunks, "
                 f"{sim.staged} stages)", "staged_step_traffic", nx * ny)
@@ -365,7 +369,10 @@ def run_ours(args, rank, world, local_rank):
 
     sim = lbm.Simulation(w.nx, w.ny, w.tau, w.farfield_rho, w.farfield_u, storage=args.storage)
     sim.init(*fields)
-    if args.launch.startswith("staged"):
+    if args.launch == "twostep":
+        bx, rows, pf = 0, 0, 0
+        sim.set_twostep(True)
+    elif args.launch.startswith("staged"):
         bx, rows, pf = 0, 0, 0
         sim.set_staged(int(args.launch[len("staged"):] or 3))
     elif args.launch.startswith("fused"):
@@ -428,8 +435,10 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
             "config": {"workload": describe(w, args.storage), "nx": w.nx, "ny": w.ny,
-                       "step_kernel": {"staged_stages": sim.staged} if sim.staged else
-                       {"bulk_threads_x": bx, "bulk_rows": rows, "prefetch_rows": pf, "fused": sim.fused},
+                       "step_kernel": ({"twostep": True} if sim.twostep else
+                                       {"staged_stages": sim.staged} if sim.staged else
+                                       {"bulk_threads_x": bx, "bulk_rows": rows, "prefetch_rows": pf,
+                                        "fused": sim.fused}),
                        "l2": f"inputs larger than L2: {lbm.lbm_buffer_bytes(sim.h) / 1e9:.2f} GB per population buffer",
                        "parallelism": "replicas" if world > 1 else "single-gpu",
                        "stable": bool(stable)},
@@ -445,7 +454,8 @@ def run_ours(args, rank, world, local_rank):
                          "avg_launch_ms": bulk_avg, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "nsbc_avg_launch_ms": nsbc_avg if nn else None,
                          "timing": f"per-launch CUDA events over {kprof} steps after the timed region"},
-            "gpu_launches": (1 if sim.staged or sim.fused else 2) * args.steps,
+            "gpu_launches": (args.steps // 2 + 2 * (args.steps % 2) if sim.twostep else
+                             (1 if sim.staged or sim.fused else 2) * args.steps),
             "clocks": clk,
         }
 
@@ -506,7 +516,7 @@ def run_ours(args, rank, world, local_rank):
             gbs = BYTES_PER_CELL[st] * vcells / (bavg * 1e-3) / 1e9
             variants[st] = {"mlups": world * cells * vsteps / (vms * 1e-3) / 1e6, "steps": vsteps,
                             "kernel_gbs": gbs, "kernel_frac": gbs / peak, "kernel": vname,
-                            "bulk_launch": None if s2.staged else [vb, vr, vp]}
+                            "bulk_launch": None if (s2.staged or s2.twostep) else [vb, vr, vp]}
             s2.close()
             del s2
             torch.cuda.empty_cache()
@@ -554,8 +564,8 @@ def run_ours(args, rank, world, local_rank):
             vms = a0.elapsed_time(a1)
             mlups = world * wn.cells * nsteps / (vms * 1e-3) / 1e6
             sizes[f"pulse-{n}"] = {"mlups": mlups, "steps": nsteps, "frac_of_72B_roofline": mlups * 1e6 * 72 / 1e9 / peak,
-                                   "step_kernel": (f"staged {s4.staged}" if s4.staged else
-                                                   "fused" if s4.fused else "bulk + NSBC pair"),
+                                   "step_kernel": ("twostep" if s4.twostep else f"staged {s4.staged}" if s4.staged
+                                                   else "fused" if s4.fused else "bulk + NSBC pair"),
                                    "mb_per_buffer": lbm.lbm_buffer_bytes(s4.h) / 1e6}
             s4.close()
             del s4

@@ -176,6 +176,29 @@ __device__ __forceinline__ EdgeNode edge_node(int node, const Geom& g, const Nsb
   return e;
 }
 
+// Where the boundary code reads the state it updates and writes the result:
+// population i of node (x, y), in physical units (the storage scale undone).
+// GlobalSrc / GlobalDst address a population buffer in device memory; other
+// sources (rows staged in shared memory) provide the same two calls.
+template <typename T>
+struct GlobalSrc {
+  const T* __restrict__ a;
+  long long plane;
+  int pitch;
+  __device__ __forceinline__ typename Store<T>::C ld(int i, int x, int y) const {
+    return Store<T>::ldg1(a + i * plane + (long long)y * pitch + x);
+  }
+};
+template <typename T>
+struct GlobalDst {
+  T* __restrict__ b;
+  long long plane;
+  int pitch;
+  __device__ __forceinline__ void st(int i, int x, int y, typename Store<T>::C v) const {
+    Store<T>::st1(b + i * plane + (long long)y * pitch + x, v);
+  }
+};
+
 // The NSBC finish runs on all four lanes of a quad: lane q owns one opposite
 // pair of populations, q = 0: (1, 2), c = (1, 0); q = 1: (3, 4), c = (0, 1);
 // q = 2: (5, 6), c = (1, 1); q = 3: (7, 8), c = (-1, 1) (Fig. 1 numbering),
@@ -208,21 +231,20 @@ __device__ __forceinline__ C quad_sum(C v, unsigned quad) {
 // This lane's pulled populations of the node: h+ (along c) from x - c, h-
 // (along -c) from x + c, h0 from x; unknown (and zero) where the source lies
 // outside the domain, wrapped on periodic axes.
-template <typename T>
-__device__ __forceinline__ void quad_pull(const T* __restrict__ A, const Geom& g, const Nsbc& p, const EdgeNode& e,
+template <typename T, typename Src>
+__device__ __forceinline__ void quad_pull(const Src& A, const Geom& g, const Nsbc& p, const EdgeNode& e,
                                           const QuadPair& pr, typename Store<T>::C& hp, typename Store<T>::C& hm,
                                           typename Store<T>::C& h0, bool& kp, bool& km) {
-  using S = Store<T>;
-  using C = typename S::C;
+  using C = typename Store<T>::C;
   auto pull = [&](int i, int sx, int sy, bool& known) -> C {
     if (p.periodic_x) sx = sx < 0 ? sx + g.nx : (sx >= g.nx ? sx - g.nx : sx);
     if (p.periodic_y) sy = sy < 0 ? sy + g.ny : (sy >= g.ny ? sy - g.ny : sy);
     known = sx >= 0 && sx < g.nx && sy >= 0 && sy < g.ny;
-    return known ? S::ldg1(A + i * g.plane + (long long)sy * g.pitch + sx) : C(0);
+    return known ? A.ld(i, sx, sy) : C(0);
   };
   hp = pull(pr.ip, e.x - pr.cx, e.y - pr.cy, kp);
   hm = pull(pr.im, e.x + pr.cx, e.y + pr.cy, km);
-  h0 = S::ldg1(A + (long long)e.y * g.pitch + e.x);
+  h0 = A.ld(0, e.x, e.y);
 }
 
 // Equilibrium deviations (as equilibrium_dev) of this lane's pair and of
@@ -368,22 +390,19 @@ __device__ __forceinline__ double quad_predict(const typename Store<T>::C (&v)[9
 }
 
 // The populations of node (x, y), or zeros if !want.
-template <typename T>
-__device__ __forceinline__ void load_node(const T* __restrict__ A, long long plane, int pitch, int x, int y,
-                                          bool want, typename Store<T>::C (&v)[9]) {
-  using S = Store<T>;
-  using C = typename S::C;
-  const long long o = (long long)y * pitch + x;
+template <typename T, typename Src>
+__device__ __forceinline__ void load_node(const Src& A, int x, int y, bool want, typename Store<T>::C (&v)[9]) {
+  using C = typename Store<T>::C;
 #pragma unroll
-  for (int i = 0; i < 9; ++i) v[i] = want ? S::ldg1(A + i * plane + o) : C(0);
+  for (int i = 0; i < 9; ++i) v[i] = want ? A.ld(i, x, y) : C(0);
 }
 
 // The rest of the node, on all four lanes of its quad, given this lane's
 // pulled pair and the blended deviation m_c - m0 = (rho_c - rho0, u_c - u0):
 // velocity override, reconstruction of the unknown populations, correction,
 // collision and the store.
-template <typename T, int MODEL, bool SHIFT = false>
-__device__ __forceinline__ void quad_finish(T* __restrict__ B, const Geom& g, const Nsbc& p,
+template <typename T, int MODEL, bool SHIFT = false, typename Dst>
+__device__ __forceinline__ void quad_finish(const Dst& B, const Geom& g, const Nsbc& p,
                                             const Rates<typename Store<T>::C>& rates, const EdgeNode& en,
                                             const QuadPair& pr, int q, unsigned quad, typename Store<T>::C hp,
                                             typename Store<T>::C hm, typename Store<T>::C h0, bool kp, bool km,
@@ -444,22 +463,20 @@ __device__ __forceinline__ void quad_finish(T* __restrict__ B, const Geom& g, co
 
   pair_collide<MODEL, SHIFT>(pr, q, hp, hm, h0, rates, quad);
   if (store) {
-    const long long o = (long long)y * g.pitch + x;
-    S::st1(B + pr.ip * g.plane + o, hp);
-    S::st1(B + pr.im * g.plane + o, hm);
-    if (q == 0) S::st1(B + o, h0);
+    B.st(pr.ip, x, y, hp);
+    B.st(pr.im, x, y, hm);
+    if (q == 0) B.st(0, x, y, h0);
   }
 }
 
 // The second prediction of a corner under corner reading 1, along the
 // horizontal edge's normal (0, nyn).  Kept out of line: only the quads that
 // hold a corner call it, and inlined it would cost every NSBC node registers.
-template <typename T, bool SHIFT>
-__device__ __noinline__ double corner_second_prediction(const T* __restrict__ A, long long plane, int pitch, int x,
-                                                        int y, Far<typename Store<T>::C> z, unsigned quad, int q,
-                                                        Predict p) {
+template <typename T, bool SHIFT, typename Src>
+__device__ __noinline__ double corner_second_prediction(Src A, int x, int y, Far<typename Store<T>::C> z,
+                                                        unsigned quad, int q, Predict p) {
   typename Store<T>::C w[9];
-  load_node(A, plane, pitch, x, y, q <= p.order, w);
+  load_node<T>(A, x, y, q <= p.order, w);
   return quad_predict<T, SHIFT>(w, z, quad, q < 3 ? q : 0, false, p);
 }
 
@@ -477,8 +494,8 @@ __device__ __noinline__ double corner_second_prediction(const T* __restrict__ A,
 // the vertical edge (n = (nxn, 0)) and of the horizontal one (n = (0, nyn)),
 // and gets the mean of the two blended states; the second pass runs only in
 // the quads that hold a corner.
-template <typename T, int MODEL, int K, bool SHIFT = false>
-__device__ __forceinline__ void nsbc_nodes(const T* __restrict__ A, T* __restrict__ B, const Geom& g, const Nsbc& p,
+template <typename T, int MODEL, int K, bool SHIFT = false, typename Src, typename Dst>
+__device__ __forceinline__ void nsbc_nodes(const Src& A, const Dst& B, const Geom& g, const Nsbc& p,
                                            const Rates<typename Store<T>::C>& rates, const int (&node)[K],
                                            const bool (&valid)[K], int q) {
   using S = Store<T>;
@@ -491,13 +508,13 @@ __device__ __forceinline__ void nsbc_nodes(const T* __restrict__ A, T* __restric
 #pragma unroll
   for (int k = 0; k < K; ++k) {
     en[k] = edge_node(node[k], g, p);
-    quad_pull(A, g, p, en[k], pr, hp[k], hm[k], h0[k], kp[k], km[k]);  // this lane's pulled pair
+    quad_pull<T>(A, g, p, en[k], pr, hp[k], hm[k], h0[k], kp[k], km[k]);  // this lane's pulled pair
   }
 #pragma unroll
   for (int k = 0; k < K; ++k) {  // lane q: the node b - q n (zeros if not needed)
     const bool split = p.corner == 1 && en[k].nxn != 0 && en[k].nyn != 0;
     const int ny1 = split ? 0 : en[k].nyn;  // a split corner: the vertical edge's normal first
-    load_node(A, g.plane, g.pitch, en[k].x - q * en[k].nxn, en[k].y - q * ny1, en[k].open && q <= p.order, v[k]);
+    load_node<T>(A, en[k].x - q * en[k].nxn, en[k].y - q * ny1, en[k].open && q <= p.order, v[k]);
   }
   const int cq = q < 3 ? q : 0;
   C mc[K][3];  // (rho_c - rho0, u_c - u0)
@@ -507,9 +524,9 @@ __device__ __forceinline__ void nsbc_nodes(const T* __restrict__ A, T* __restric
     const bool split = p.corner == 1 && corner;  // the same for all four lanes of the quad
     double mine = quad_predict<T, SHIFT>(v[k], far_of(rates.z), quad, cq, corner && !split, predict_of(p));
     if (split)
-      mine = __dmul_rn(0.5, __dadd_rn(mine, corner_second_prediction<T, SHIFT>(A, g.plane, g.pitch, en[k].x,
-                                                                              en[k].y - q * en[k].nyn, far_of(rates.z),
-                                                                              quad, q, predict_of(p))));
+      mine = __dmul_rn(0.5, __dadd_rn(mine, corner_second_prediction<T, SHIFT>(A, en[k].x, en[k].y - q * en[k].nyn,
+                                                                              far_of(rates.z), quad, q,
+                                                                              predict_of(p))));
     const C mcq = C(mine);
 #pragma unroll
     for (int c = 0; c < 3; ++c) mc[k][c] = __shfl_sync(quad, mcq, c, 4);
@@ -525,7 +542,8 @@ __device__ __forceinline__ void nsbc_node(const T* __restrict__ A, T* __restrict
                                           const Rates<typename Store<T>::C>& rates, int node, int q) {
   const int n[1] = {node};
   const bool ok[1] = {true};
-  nsbc_nodes<T, MODEL, 1, SHIFT>(A, B, g, p, rates, n, ok, q);
+  nsbc_nodes<T, MODEL, 1, SHIFT>(GlobalSrc<T>{A, g.plane, g.pitch}, GlobalDst<T>{B, g.plane, g.pitch}, g, p, rates,
+                                 n, ok, q);
 }
 
 // One launch for the whole step (the "fused" form, for domains small enough

@@ -10,8 +10,9 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
-#include <cstring>
 #include <cstdlib>
+#include <cstring>
+#include <type_traits>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -21,6 +22,7 @@
 #include "lbm_kernels.cuh"
 #include "lbm_staged.cuh"
 #include "lbm_trace.h"
+#include "lbm_twostep.cuh"
 #include "lbm_tune_cache.h"
 
 namespace lbmk {
@@ -122,6 +124,10 @@ struct lbm {
   // fused step kernel (lbm_set_fused): the bulk grid of the current shape and
   // the NSBC quads in one launch per step
   bool fused = false;
+  // two-step kernel (lbm_set_twostep): two steps per launch, the step in
+  // between kept in shared memory; its grid of strips x bands of rows
+  bool twostep = false;
+  int ts_strips = 0, ts_bands = 0, ts_band = 0;
   int4* d_items = nullptr;
   lbmk::InstDev* d_inst = nullptr;
   void* d_shift = nullptr;  // the far field's storage shift in the compute type (staged kernel)
@@ -336,6 +342,71 @@ void launch_staged(const lbm_t* h, const void* a, void* b, cudaStream_t s) {
   });
 }
 
+// Two-step kernel: grid and launch.  Strips of W columns; bands of rows
+// chosen so that the blocks (one per SM: the rings take ~190 KB of shared
+// memory) fill whole waves of the GPU where the band stays between 32 and 1024
+// rows, the fewest bands among equally good choices.
+template <typename T>
+void twostep_grid(lbm_t* h) {
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  const int W = lbmk::TwoStep<T>::W;
+  h->ts_strips = (h->nx + W - 1) / W;
+  double best = 1e30;
+  const int lo = std::max(1, (h->ny + 1023) / 1024), hi = std::max(lo, (h->ny + 31) / 32);
+  for (int nb = lo; nb <= hi; ++nb) {
+    const int band = (h->ny + nb - 1) / nb;
+    const int blocks = h->ts_strips * ((h->ny + band - 1) / band);
+    const int waves = (blocks + sms - 1) / sms;
+    // time ~ waves x (band + 4 halo rows); a row costs the same in every wave
+    const double t = (double)waves * (band + 4);
+    if (t < best - 1e-9) {
+      best = t;
+      h->ts_band = band;
+    }
+  }
+  h->ts_bands = (h->ny + h->ts_band - 1) / h->ts_band;
+}
+
+template <typename T, int MODEL, bool SHIFT>
+void launch_twostep_k(const lbm_t* h, const T* A, T* B, cudaStream_t s) {
+  auto k = lbmk::twostep_kernel<T, MODEL, SHIFT>;
+  k<<<h->ts_strips * h->ts_bands, lbmk::kTwoStepThreads, lbmk::TwoStep<T>::kSmem, s>>>(
+      A, B, lbmk::Geom{h->nx, h->ny, h->pitch, h->plane}, h->nsbc, rates<typename lbmk::Store<T>::C>(h), h->ts_band,
+      h->ts_strips);
+}
+
+template <typename T>
+void launch_twostep(const lbm_t* h, const void* a, void* b, cudaStream_t s) {
+  const T* A = static_cast<const T*>(a);
+  T* B = static_cast<T*>(b);
+  with_shift(h, [&](auto zc) {
+    constexpr bool Z = decltype(zc)::value;
+    if (h->collision == 1)
+      launch_twostep_k<T, 1, Z>(h, A, B, s);
+    else
+      launch_twostep_k<T, 0, Z>(h, A, B, s);
+  });
+}
+
+// the two-step kernel serves this handle (f32 / f16 / bf16, no periodic axis, 8 x 8 nodes or more)
+bool twostep_ok(const lbm_t* h) {
+  return h->storage != LBM_F64 && !h->nsbc.periodic_x && !h->nsbc.periodic_y && h->nx >= 8 && h->ny >= 8;
+}
+
+template <typename T>
+int twostep_prepare(lbm_t* h) {
+  twostep_grid<T>(h);
+  const int smem = (int)lbmk::TwoStep<T>::kSmem;
+  cudaError_t e = cudaSuccess;
+  for (const void* k : {(const void*)lbmk::twostep_kernel<T, 0, false>, (const void*)lbmk::twostep_kernel<T, 0, true>,
+                        (const void*)lbmk::twostep_kernel<T, 1, false>, (const void*)lbmk::twostep_kernel<T, 1, true>})
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e == cudaSuccess ? LBM_OK
+                          : fail(LBM_ECUDA, "two-step kernel: %d bytes of shared memory refused: %s", smem,
+                                 cudaGetErrorString(e));
+}
+
 template <typename F>
 void dispatch(int storage, F&& f) {
   switch (storage) {
@@ -422,6 +493,26 @@ void enqueue_macros_rows(const lbm_t* h, double* d_rho, double* d_ux, double* d_
 // One step from buffer `from` to 1 - from.  With `fork`, the NSBC kernel runs
 // on the side stream concurrently with the bulk kernel (both only read
 // buffer `from` and write disjoint nodes of the other buffer).
+// Two-step launches need the kernels' shared-memory attribute and the grid
+// (once the storage is fixed); 0 when the two-step kernel is off.
+int ensure_twostep(lbm_t* h) {
+  if (!h->twostep || !twostep_ok(h)) return LBM_OK;
+  int rc = LBM_OK;
+  dispatch(h->storage, [&](auto tag) {
+    using T = decltype(tag);
+    if constexpr (!std::is_same<T, double>::value) rc = twostep_prepare<T>(h);
+  });
+  return rc;
+}
+
+// Two steps from buffer `from` to 1 - from in one launch.
+void enqueue_twostep(const lbm_t* h, int from, cudaStream_t s) {
+  dispatch(h->storage, [&](auto tag) {
+    using T = decltype(tag);
+    if constexpr (!std::is_same<T, double>::value) launch_twostep<T>(h, h->buf[from], h->buf[1 - from], s);
+  });
+}
+
 void enqueue_step(const lbm_t* h, int from, cudaStream_t s, bool fork) {
   const void* a = h->buf[from];
   void* b = h->buf[1 - from];
@@ -452,7 +543,12 @@ void enqueue_step(const lbm_t* h, int from, cudaStream_t s, bool fork) {
 int capture_graph(lbm_t* h, int from) {
   cudaGraph_t g = nullptr;
   LBM_CUDA(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
-  for (int k = 0; k < kGraphSteps; ++k) enqueue_step(h, (from + k) & 1, h->cap, true);
+  if (h->twostep && twostep_ok(h)) {
+    // kGraphSteps / 2 launches of two steps: an even number of buffer swaps
+    for (int k = 0; k < kGraphSteps / 2; ++k) enqueue_twostep(h, (from + k) & 1, h->cap);
+  } else {
+    for (int k = 0; k < kGraphSteps; ++k) enqueue_step(h, (from + k) & 1, h->cap, true);
+  }
   cudaError_t e = cudaStreamEndCapture(h->cap, &g);
   if (e != cudaSuccess) return fail(LBM_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
   e = cudaGraphInstantiate(&h->graph[from], g, 0);
@@ -501,6 +597,18 @@ int enqueue_step_profiled(lbm_t* h, int from) {
       cudaEventRecord(e[3], h->stream);
     }
   });
+  return LBM_OK;
+}
+
+// Two steps in one launch with an event pair around it (counted as one bulk
+// launch; it carries two steps).
+int enqueue_twostep_profiled(lbm_t* h, int from) {
+  cudaEvent_t e[2];
+  int rc = profiled_pair(h, 0, e);
+  if (rc) return rc;
+  cudaEventRecord(e[0], h->stream);
+  enqueue_twostep(h, from, h->stream);
+  cudaEventRecord(e[1], h->stream);
   return LBM_OK;
 }
 
@@ -797,9 +905,16 @@ int lbm_step(lbm_t* h, int32_t n) {
   if (!h->initialised) return fail(LBM_ESTATE, "lbm_step: call lbm_init first");
   int rc = ensure_streams(h);
   if (!rc) rc = ensure_staged(h);
+  if (!rc) rc = ensure_twostep(h);
   if (rc) return rc;
+  const bool two = h->twostep && twostep_ok(h);
   int left = n;
   if (h->profiling) {
+    for (; two && left >= 2; left -= 2) {
+      rc = enqueue_twostep_profiled(h, h->cur);
+      if (rc) return rc;
+      h->cur ^= 1;
+    }
     for (; left > 0; --left) {
       rc = enqueue_step_profiled(h, h->cur);
       if (rc) return rc;
@@ -816,7 +931,11 @@ int lbm_step(lbm_t* h, int32_t n) {
       left -= kGraphSteps;  // kGraphSteps is even: h->cur is unchanged
     }
   }
-  for (; left > 0; --left) {
+  for (; two && left >= 2; left -= 2) {
+    enqueue_twostep(h, h->cur, h->stream);
+    h->cur ^= 1;
+  }
+  for (; left > 0; --left) {  // an odd last step: the kernel pair
     enqueue_step(h, h->cur, h->stream, false);
     h->cur ^= 1;
   }
@@ -1061,6 +1180,7 @@ int lbm_set_launch(lbm_t* h, int32_t threads_x, int32_t rows, int32_t prefetch_r
   h->pf = prefetch_rows;
   h->staged = 0;
   h->fused = false;
+  h->twostep = false;
   drop_graphs(h);
   return LBM_OK;
 }
@@ -1068,7 +1188,10 @@ int lbm_set_launch(lbm_t* h, int32_t threads_x, int32_t rows, int32_t prefetch_r
 int lbm_set_fused(lbm_t* h, int32_t enable) {
   if (!h) return fail(LBM_EINVAL, "lbm_set_fused: NULL handle");
   h->fused = enable != 0;
-  if (h->fused) h->staged = 0;
+  if (h->fused) {
+    h->staged = 0;
+    h->twostep = false;
+  }
   drop_graphs(h);
   return LBM_OK;
 }
@@ -1080,12 +1203,30 @@ int lbm_set_staged(lbm_t* h, int32_t stages) {
   if (stages != 0 && stages != 3 && stages != 4)
     return fail(LBM_EINVAL, "lbm_set_staged: stages=%d (0 = off, 3 or 4)", stages);
   h->staged = stages;
-  if (stages) h->fused = false;
+  if (stages) {
+    h->fused = false;
+    h->twostep = false;
+  }
   drop_graphs(h);
   return LBM_OK;
 }
 
 int32_t lbm_get_staged(const lbm_t* h) { return h ? h->staged : LBM_EINVAL; }
+
+int lbm_set_twostep(lbm_t* h, int32_t enable) {
+  if (!h) return fail(LBM_EINVAL, "lbm_set_twostep: NULL handle");
+  if (enable && !twostep_ok(h))
+    return fail(LBM_EINVAL, "lbm_set_twostep: needs f32, f16 or bf16 storage, no periodic axis and 8 x 8 nodes or more");
+  h->twostep = enable != 0;
+  if (h->twostep) {
+    h->staged = 0;
+    h->fused = false;
+  }
+  drop_graphs(h);
+  return LBM_OK;
+}
+
+int32_t lbm_get_twostep(const lbm_t* h) { return h ? (h->twostep ? 1 : 0) : LBM_EINVAL; }
 
 int lbm_status(lbm_t* h) {
   if (!h) return fail(LBM_EINVAL, "lbm_status: NULL handle");
@@ -1109,12 +1250,13 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
   if (!tune_path.empty()) {
     tune_key = lbm_internal_tune_key("domain", h->storage, h->collision, zshift(h).on, {h->nx, h->ny});
     lbmtune::Entry e;
-    double bx = 0, r = 0, pf = 0, st = -1, fz = -1, ms = 0;
+    double bx = 0, r = 0, pf = 0, st = -1, fz = -1, ts = -1, ms = 0;
     if (lbmtune::lookup(tune_path, tune_key, &e) && e.get("threads_x", &bx) && e.get("rows", &r) &&
-        e.get("prefetch_rows", &pf) && e.get("staged", &st) && e.get("fused", &fz) && e.get("ms_per_step", &ms) &&
-        (st == 0 || st == 3 || st == 4) && (fz == 0 || fz == 1) &&
-        lbm_set_launch(h, (int32_t)bx, (int32_t)r, (int32_t)pf) == LBM_OK &&
-        (st == 0 || lbm_set_staged(h, (int32_t)st) == LBM_OK) && (fz == 0 || lbm_set_fused(h, 1) == LBM_OK)) {
+        e.get("prefetch_rows", &pf) && e.get("staged", &st) && e.get("fused", &fz) && e.get("twostep", &ts) &&
+        e.get("ms_per_step", &ms) && (st == 0 || st == 3 || st == 4) && (fz == 0 || fz == 1) &&
+        (ts == 0 || ts == 1) && lbm_set_launch(h, (int32_t)bx, (int32_t)r, (int32_t)pf) == LBM_OK &&
+        (st == 0 || lbm_set_staged(h, (int32_t)st) == LBM_OK) && (fz == 0 || lbm_set_fused(h, 1) == LBM_OK) &&
+        (ts == 0 || lbm_set_twostep(h, 1) == LBM_OK)) {
       lbm_internal_tune_count(true);
       if (threads_x) *threads_x = h->bx;
       if (rows) *rows = h->rows;
@@ -1135,7 +1277,8 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
   const int reps = (int)std::max<long long>(4, std::min<long long>(64, (1LL << 28) / std::max(cells, 1LL)));
   float best = 1e30f;
   int best_bx = h->bx, best_rows = h->rows, best_pf = h->pf, best_staged = h->staged;
-  bool best_fused = h->fused;
+  bool best_fused = h->fused, best_twostep = false;
+  h->twostep = false;
   // whole steps as the graphs run them (NSBC kernel on the forked branch)
   auto time_steps = [&]() -> float {
     for (int k = 0; k < 2; ++k) enqueue_step(h, k & 1, h->stream, true);
@@ -1165,6 +1308,7 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
             best_pf = pf;
             best_staged = 0;
             best_fused = fz;
+            best_twostep = false;
           }
         }
   h->fused = false;
@@ -1178,7 +1322,32 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
       best = ms;
       best_staged = st;
       best_fused = false;
+      best_twostep = false;
     }
+  }
+  // the two-step kernel: two steps per launch
+  h->staged = 0;
+  if (twostep_ok(h)) {
+    h->twostep = true;
+    if (ensure_twostep(h) == LBM_OK) {
+      const int launches = std::max(2, reps / 2);
+      for (int k = 0; k < 2; ++k) enqueue_twostep(h, k & 1, h->stream);
+      cudaEventRecord(e0, h->stream);
+      for (int k = 0; k < launches; ++k) enqueue_twostep(h, k & 1, h->stream);
+      cudaEventRecord(e1, h->stream);
+      float ms = 1e30f;
+      if (cudaEventSynchronize(e1) == cudaSuccess) {
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 2.0f * launches;
+      }
+      if (ms < best) {
+        best = ms;
+        best_twostep = true;
+        best_staged = 0;
+        best_fused = false;
+      }
+    }
+    h->twostep = false;
   }
   rc = check_launch();
   h->bx = best_bx;
@@ -1186,6 +1355,7 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
   h->pf = best_pf;
   h->staged = best_staged;
   h->fused = best_fused && !best_staged;
+  h->twostep = best_twostep && !best_staged && !h->fused;
   drop_graphs(h);
   LBM_CUDA(cudaMemcpyAsync(h->buf[h->cur], backup, bb, cudaMemcpyDeviceToDevice, h->stream));
   LBM_CUDA(cudaFreeAsync(backup, h->stream));
@@ -1197,7 +1367,8 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
     lbm_internal_tune_count(false);
     lbmtune::Entry e{tune_key,
                      {{"threads_x", best_bx}, {"rows", best_rows}, {"prefetch_rows", best_pf},
-                      {"staged", h->staged}, {"fused", h->fused ? 1 : 0}, {"ms_per_step", best}}};
+                      {"staged", h->staged}, {"fused", h->fused ? 1 : 0}, {"twostep", h->twostep ? 1 : 0},
+                      {"ms_per_step", best}}};
     lbmtune::store(tune_path, e);  // a cache that cannot be written is only not reused
   }
   if (threads_x) *threads_x = best_bx;

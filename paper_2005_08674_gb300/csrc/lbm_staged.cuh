@@ -310,7 +310,9 @@ __global__ void __launch_bounds__(NC + 32, 4) batch_ws_kernel(const T* __restric
         valid[k] = n < w.z;
         node[k] = w.y + (valid[k] ? n : 0);
       }
-      lbmk::nsbc_nodes<T, MODEL, K, SHIFT>(A + d.off, B + d.off, g, q, r, node, valid, tid & 3);
+      lbmk::nsbc_nodes<T, MODEL, K, SHIFT>(lbmk::GlobalSrc<T>{A + d.off, g.plane, g.pitch},
+                                           lbmk::GlobalDst<T>{B + d.off, g.plane, g.pitch}, g, q, r, node, valid,
+                                           tid & 3);
     } else {
       collide_tile<T, NC, MODEL, TILE, SHIFT>(smem + s * 9 * SLOT, d, w, B, r);
     }

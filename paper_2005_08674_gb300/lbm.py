@@ -69,6 +69,8 @@ _SIGS = {
     "lbm_get_staged": (ctypes.c_int32, [_vp]),
     "lbm_set_fused": (ctypes.c_int, [_vp, _i32]),
     "lbm_get_fused": (ctypes.c_int32, [_vp]),
+    "lbm_set_twostep": (ctypes.c_int, [_vp, _i32]),
+    "lbm_get_twostep": (ctypes.c_int32, [_vp]),
     "lbm_status": (ctypes.c_int, [_vp]),
     "lbm_reduce_noalloc": (ctypes.c_int, [_vp, _vp, _vp, _vp, _i32, _dp]),
     "lbm_set_tune_cache": (ctypes.c_int, [ctypes.c_char_p]),
@@ -354,6 +356,14 @@ def lbm_get_fused(h) -> int:
     return int(_L.lbm_get_fused(h))
 
 
+def lbm_set_twostep(h, enable: bool):
+    return _check(_L.lbm_set_twostep(h, int(bool(enable))))
+
+
+def lbm_get_twostep(h) -> int:
+    return int(_L.lbm_get_twostep(h))
+
+
 def lbm_status(h):
     return _check(_L.lbm_status(h))
 
@@ -520,6 +530,15 @@ class Simulation:
     @property
     def fused(self) -> bool:
         return lbm_get_fused(self.h) == 1
+
+    def set_twostep(self, enable=True):
+        """Two steps per launch, the step in between kept in shared memory."""
+        lbm_set_twostep(self.h, enable)
+        return self
+
+    @property
+    def twostep(self) -> bool:
+        return lbm_get_twostep(self.h) == 1
 
     def status(self):
         """Raises LbmError(LBM_ETIMEOUT) if a bounded device-side wait gave up."""

@@ -1,8 +1,8 @@
 """Driver for the bounds-checked library (run in a child process with
 LBM_CHECKED=1 by test_checked_build_gpu.py; not collected by pytest).
 
-Steps every launch form of the single-domain (kernel pair, fused, staged)
-and batched paths on small, odd-sized domains (all storages, BGK and MRT,
+Steps every launch form of the single-domain (kernel pair, fused, staged,
+two-step where it applies) and batched paths on small, odd-sized domains (all storages, BGK and MRT,
 first- and second-order NSBC differences, periodic and velocity edges, far
 fields at rest and in a stream, i.e. the plain and shifted kernels) and
 prints one JSON line: whether the loaded library is the checked build, how
@@ -23,9 +23,9 @@ import oracle  # noqa: E402
 from paper_2005_08674_gb300 import inputs, lbm  # noqa: E402
 
 STEPS = 21
-SIZES = [(3, 3), (5, 7), (33, 17), (65, 4), (517, 4), (4, 129), (130, 66)]
+SIZES = [(3, 3), (5, 7), (33, 17), (65, 4), (517, 4), (4, 129), (130, 66), (9, 8), (300, 41)]
 LAUNCHES = [("pair", (64, 1, 0)), ("pair", (128, 2, 1)), ("pair", (256, 1, 3)), ("pair", (512, 8, 64)),
-            ("fused", (128, 1, 0)), ("fused", (64, 4, 3)), ("staged", 3), ("staged", 4)]
+            ("fused", (128, 1, 0)), ("fused", (64, 4, 3)), ("staged", 3), ("staged", 4), ("twostep", None)]
 BATCH_LAUNCHES = [(128, 1, -1, 0, 0, 0), (64, 1, 0, 0, 0, 0), (128, 2, 0, 1, 1, 0), (256, 4, 152, 0, 0, 0),
                   (64, 4, 7, 64, 1, 0), (128, 1, 0, 0, 1, 128), (128, 1, 0, 0, 1, 256), (256, 1, 0, 0, 1, 256),
                   (128, 4, -1, 1, 0, 0), (256, 1, -1, 0, 1, 0), (128, 3, 0, 0, 0, 128), (128, 4, 0, 2, 0, 128),
@@ -53,7 +53,11 @@ def main():
                 for i, kw in enumerate(kws):
                     with lbm.Simulation(nx, ny, 0.6, storage=storage, **kw) as s:
                         s.init(*fields)
-                        if kind == "staged":
+                        if kind == "twostep":
+                            if storage == "f64" or nx < 8 or ny < 8 or "edges" in kw:
+                                continue  # the two-step kernel does not serve these
+                            s.set_twostep(True)
+                        elif kind == "staged":
                             s.set_staged(arg)
                         else:
                             s.set_launch(*arg)
