@@ -268,21 +268,25 @@ int32_t lbm_get_staged(const lbm_t* h);
 int lbm_set_fused(lbm_t* h, int32_t enable);
 int32_t lbm_get_fused(const lbm_t* h);
 /* Two steps per launch (temporal blocking): each block of the two-step kernel
- * owns a strip of columns x a band of rows and streams down it with two rings
- * of rows in shared memory -- the state at step n, copied in from device
- * memory, and step n + 1, computed there and never written to device memory
- * -- and stores step n + 2.  Every node runs the same device arithmetic as the
+ * owns an output tile (120 x 8 nodes in f32, 240 x 8 in f16 / bf16), stages
+ * the state at step n over the tile and two nodes around it in shared memory
+ * by bulk copies, computes step n + 1 over the tile and one node around it
+ * into shared memory -- never writing it to device memory -- and stores step
+ * n + 2 over the tile.  Every node runs the same device arithmetic as the
  * single-step kernels and step n + 1 is rounded to the storage type as a
  * single step stores it, so the results are bit-identical to the kernel pair;
  * device-memory traffic per step is about half (one read and one write of the
- * state per two steps, plus a one-node halo per strip and two rows per band).
+ * state per two steps; the halos of neighbouring tiles come mostly from L2).
+ * A persistent grid (two blocks per SM) takes the tiles in turn, copying the
+ * next tile's state in while it computes the current one's second step.
  * lbm_step(n) runs n / 2 two-step launches (graphs of 8) and, for odd n, one
  * step of the kernel pair.  enable != 0 turns it on (and the staged and fused
  * kernels off); lbm_set_launch, lbm_set_staged and lbm_set_fused turn it off;
  * lbm_autotune times it against the other forms.  LBM_EINVAL when enabling it
  * on an f64 handle, a handle with a periodic axis or fewer than 8 x 8 nodes.
- * Shared memory per block: about 190 KB (one block per SM).  lbm_get_twostep:
- * 1 if on, 0 if off, LBM_EINVAL for NULL. */
+ * A bounded wait for the bulk copies that gives up makes lbm_status report
+ * LBM_ETIMEOUT.  Shared memory per block: about 101 KB (two blocks per SM).
+ * lbm_get_twostep: 1 if on, 0 if off, LBM_EINVAL for NULL. */
 int lbm_set_twostep(lbm_t* h, int32_t enable);
 int32_t lbm_get_twostep(const lbm_t* h);
 /* LBM_ETIMEOUT if a bounded wait of the staged kernel gave up (the state is

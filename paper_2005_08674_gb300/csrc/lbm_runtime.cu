@@ -125,9 +125,10 @@ struct lbm {
   // the NSBC quads in one launch per step
   bool fused = false;
   // two-step kernel (lbm_set_twostep): two steps per launch, the step in
-  // between kept in shared memory; its grid of strips x bands of rows
+  // between kept in shared memory; its tiles along x and along y, and the
+  // persistent grid (blocks launched) and the device's SM count
   bool twostep = false;
-  int ts_strips = 0, ts_bands = 0, ts_band = 0;
+  int ts_strips = 0, ts_bands = 0, ts_grid = 0, sms = 0;
   int4* d_items = nullptr;
   lbmk::InstDev* d_inst = nullptr;
   void* d_shift = nullptr;  // the far field's storage shift in the compute type (staged kernel)
@@ -342,38 +343,23 @@ void launch_staged(const lbm_t* h, const void* a, void* b, cudaStream_t s) {
   });
 }
 
-// Two-step kernel: grid and launch.  Strips of W columns; bands of rows
-// chosen so that the blocks (one per SM: the rings take ~190 KB of shared
-// memory) fill whole waves of the GPU where the band stays between 32 and 1024
-// rows, the fewest bands among equally good choices.
+// Two-step kernel: output tiles of TX x TY nodes (the last ones along each
+// axis shifted back to end at the domain's edge), taken in turn by a
+// persistent grid of as many blocks as fit on the device at once.
 template <typename T>
-void twostep_grid(lbm_t* h) {
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-  const int W = lbmk::TwoStep<T>::W;
-  h->ts_strips = (h->nx + W - 1) / W;
-  double best = 1e30;
-  const int lo = std::max(1, (h->ny + 1023) / 1024), hi = std::max(lo, (h->ny + 31) / 32);
-  for (int nb = lo; nb <= hi; ++nb) {
-    const int band = (h->ny + nb - 1) / nb;
-    const int blocks = h->ts_strips * ((h->ny + band - 1) / band);
-    const int waves = (blocks + sms - 1) / sms;
-    // time ~ waves x (band + 4 halo rows); a row costs the same in every wave
-    const double t = (double)waves * (band + 4);
-    if (t < best - 1e-9) {
-      best = t;
-      h->ts_band = band;
-    }
-  }
-  h->ts_bands = (h->ny + h->ts_band - 1) / h->ts_band;
+void twostep_grid(lbm_t* h, int per_sm) {
+  using TS = lbmk::TwoStep<T>;
+  h->ts_strips = (h->nx + TS::TX - 1) / TS::TX;
+  h->ts_bands = (h->ny + TS::TY - 1) / TS::TY;
+  h->ts_grid = std::max(1, std::min(h->ts_strips * h->ts_bands, per_sm * h->sms));
 }
 
 template <typename T, int MODEL, bool SHIFT>
 void launch_twostep_k(const lbm_t* h, const T* A, T* B, cudaStream_t s) {
   auto k = lbmk::twostep_kernel<T, MODEL, SHIFT>;
-  k<<<h->ts_strips * h->ts_bands, lbmk::kTwoStepThreads, lbmk::TwoStep<T>::kSmem, s>>>(
-      A, B, lbmk::Geom{h->nx, h->ny, h->pitch, h->plane}, h->nsbc, rates<typename lbmk::Store<T>::C>(h), h->ts_band,
-      h->ts_strips);
+  k<<<h->ts_grid, lbmk::kTwoStepThreads, lbmk::TwoStep<T>::kSmem, s>>>(
+      A, B, lbmk::Geom{h->nx, h->ny, h->pitch, h->plane}, h->nsbc, rates<typename lbmk::Store<T>::C>(h),
+      h->ts_strips, h->ts_strips * h->ts_bands, h->d_sched);
 }
 
 template <typename T>
@@ -396,15 +382,26 @@ bool twostep_ok(const lbm_t* h) {
 
 template <typename T>
 int twostep_prepare(lbm_t* h) {
-  twostep_grid<T>(h);
+  if (!h->d_sched) {  // the give-up flag of the bounded wait (lbm_status reads it)
+    LBM_CUDA(cudaMalloc(&h->d_sched, 4 * sizeof(int)));
+    LBM_CUDA(cudaMemset(h->d_sched, 0, 4 * sizeof(int)));
+  }
   const int smem = (int)lbmk::TwoStep<T>::kSmem;
   cudaError_t e = cudaSuccess;
+  int per_sm = 0, sms = 0;
   for (const void* k : {(const void*)lbmk::twostep_kernel<T, 0, false>, (const void*)lbmk::twostep_kernel<T, 0, true>,
                         (const void*)lbmk::twostep_kernel<T, 1, false>, (const void*)lbmk::twostep_kernel<T, 1, true>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  return e == cudaSuccess ? LBM_OK
-                          : fail(LBM_ECUDA, "two-step kernel: %d bytes of shared memory refused: %s", smem,
-                                 cudaGetErrorString(e));
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbmk::twostep_kernel<T, 1, true>,
+                                                      lbmk::kTwoStepThreads, smem);
+  if (e != cudaSuccess)
+    return fail(LBM_ECUDA, "two-step kernel: %d bytes of shared memory refused: %s", smem, cudaGetErrorString(e));
+  if (per_sm <= 0) return fail(LBM_ECUDA, "two-step kernel: no block fits on an SM");
+  h->sms = sms;
+  twostep_grid<T>(h, per_sm);
+  return LBM_OK;
 }
 
 template <typename F>
