@@ -144,20 +144,22 @@ def measured_peak_gbs():
 
 def kernel_source_sha() -> str:
     h = hashlib.sha256()
-    for name in ("lbm_kernels.cuh", "lbm_device.cuh", "lbm_staged.cuh"):
+    for name in ("lbm_kernels.cuh", "lbm_device.cuh", "lbm_staged.cuh", "lbm_twostep.cuh"):
         with open(os.path.join(ROOT, "paper_2005_08674_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def step_kernel(sim, nx, ny):
-    """(kernel description, traffic summary file stem, cells one launch updates)
-    of the kernel that carries the step: the staged kernel updates every node,
-    the two-step kernel every node twice, the bulk kernel the interior (the
-    NSBC kernel the perimeter, beside it)."""
+    """(kernel description, traffic summary file stem, nodes whose state one
+    timed launch reads and writes once) of the kernel that carries the step:
+    the staged kernel updates every node, the bulk kernel the interior (the
+    NSBC kernel the perimeter, beside it); a two-step pass moves every node's
+    state once for two steps (its events bracket its three launches)."""
     if sim.twostep:
-        return ("twostep_kernel (two steps per launch: strips of rows streamed through two rings in shared memory)",
-                "twostep_traffic", 2 * nx * ny)
+        return ("two-step pass: roll_kernel (steps n+1 and n+2 on nodes 2..n-3, warps rolling down 128-column "
+                "strips, step n+1 kept in registers) between two frame_kernel launches (step n+1 on the "
+                "width-3 frame into a frame buffer, step n+2 on the width-2 frame)", "twostep_traffic", nx * ny)
     if sim.staged:
         return ("batch_ws_kernel (staged step: interior tiles by bulk copies + NSBC chunks, "
                 f"{sim.staged} stages)", "staged_step_traffic", nx * ny)
@@ -451,10 +453,11 @@ def run_ours(args, rank, world, local_rank):
                          "dram_frac": traffic / (bulk_avg * 1e-3) / 1e9 / peak if traffic else None,
                          "kernel": kname,
                          "bytes_per_cell": BYTES_PER_CELL[args.storage], "cells_per_launch": kcells,
+                         "steps_per_launch": 2 if sim.twostep else 1,
                          "avg_launch_ms": bulk_avg, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "nsbc_avg_launch_ms": nsbc_avg if nn else None,
                          "timing": f"per-launch CUDA events over {kprof} steps after the timed region"},
-            "gpu_launches": (args.steps // 2 + 2 * (args.steps % 2) if sim.twostep else
+            "gpu_launches": (3 * (args.steps // 2) + 2 * (args.steps % 2) if sim.twostep else
                              (1 if sim.staged or sim.fused else 2) * args.steps),
             "clocks": clk,
         }

@@ -267,25 +267,23 @@ int32_t lbm_get_staged(const lbm_t* h);
  * NULL handle. */
 int lbm_set_fused(lbm_t* h, int32_t enable);
 int32_t lbm_get_fused(const lbm_t* h);
-/* Two steps per launch (temporal blocking): each block of the two-step kernel
- * owns an output tile (120 x 8 nodes in f32, 240 x 8 in f16 / bf16), stages
- * the state at step n over the tile and two nodes around it in shared memory
- * by bulk copies, computes step n + 1 over the tile and one node around it
- * into shared memory -- never writing it to device memory -- and stores step
- * n + 2 over the tile.  Every node runs the same device arithmetic as the
- * single-step kernels and step n + 1 is rounded to the storage type as a
- * single step stores it, so the results are bit-identical to the kernel pair;
- * device-memory traffic per step is about half (one read and one write of the
- * state per two steps; the halos of neighbouring tiles come mostly from L2).
- * A persistent grid (two blocks per SM) takes the tiles in turn, copying the
- * next tile's state in while it computes the current one's second step.
- * lbm_step(n) runs n / 2 two-step launches (graphs of 8) and, for odd n, one
- * step of the kernel pair.  enable != 0 turns it on (and the staged and fused
- * kernels off); lbm_set_launch, lbm_set_staged and lbm_set_fused turn it off;
- * lbm_autotune times it against the other forms.  LBM_EINVAL when enabling it
- * on an f64 handle, a handle with a periodic axis or fewer than 8 x 8 nodes.
- * A bounded wait for the bulk copies that gives up makes lbm_status report
- * LBM_ETIMEOUT.  Shared memory per block: about 101 KB (two blocks per SM).
+/* Two steps per pass (temporal blocking), in three launches: step n + 1 on
+ * the frame of nodes within distance 2 of an edge (the NSBC and the interior
+ * collision) into a small frame buffer; steps n + 1 and n + 2 on the nodes at
+ * distance 2 or more by a kernel whose warps each roll down a strip of 128
+ * columns, staging the state rows by bulk copies and keeping step n + 1 in
+ * registers; step n + 2 on the frame from the frame buffer.  Every node runs
+ * the same device arithmetic as the single-step kernels and step n + 1 is
+ * rounded to the storage type as a single step stores it, so the results are
+ * bit-identical to the kernel pair, while the state crosses device memory
+ * once per two steps.  lbm_step(n) runs n / 2 passes (graphs of 8 steps) and,
+ * for odd n, one step of the kernel pair.  enable != 0 turns it on (and the
+ * staged and fused kernels off); lbm_set_launch, lbm_set_staged and
+ * lbm_set_fused turn it off; lbm_autotune times it against the other forms.
+ * LBM_EINVAL when enabling it on an f64 handle, a handle with a periodic axis
+ * or fewer than 8 x 8 nodes.  A bounded wait for the bulk copies that gives
+ * up makes lbm_status report LBM_ETIMEOUT.  Device memory: a frame buffer of
+ * 9 x (6 (nx + ny) - 36) populations, allocated when first enabled.
  * lbm_get_twostep: 1 if on, 0 if off, LBM_EINVAL for NULL. */
 int lbm_set_twostep(lbm_t* h, int32_t enable);
 int32_t lbm_get_twostep(const lbm_t* h);

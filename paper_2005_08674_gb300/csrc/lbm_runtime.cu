@@ -124,11 +124,14 @@ struct lbm {
   // fused step kernel (lbm_set_fused): the bulk grid of the current shape and
   // the NSBC quads in one launch per step
   bool fused = false;
-  // two-step kernel (lbm_set_twostep): two steps per launch, the step in
-  // between kept in shared memory; its tiles along x and along y, and the
-  // persistent grid (blocks launched) and the device's SM count
+  // two-step pass (lbm_set_twostep): two steps per pass, the step in between
+  // kept on chip except on the frame of width 3 (in d_frame, fn nodes);
+  // the rolling kernel's strips, bands, rows per band, bands per wave,
+  // waves and persistent grid, and the device's SM count
   bool twostep = false;
-  int ts_strips = 0, ts_bands = 0, ts_grid = 0, sms = 0;
+  int ts_strips = 0, ts_bands = 0, ts_band = 0, ts_wave_bands = 0, ts_waves = 0, ts_grid = 0, sms = 0;
+  void* d_frame = nullptr;
+  int frame_fn = 0;
   int4* d_items = nullptr;
   lbmk::InstDev* d_inst = nullptr;
   void* d_shift = nullptr;  // the far field's storage shift in the compute type (staged kernel)
@@ -343,23 +346,45 @@ void launch_staged(const lbm_t* h, const void* a, void* b, cudaStream_t s) {
   });
 }
 
-// Two-step kernel: output tiles of TX x TY nodes (the last ones along each
-// axis shifted back to end at the domain's edge), taken in turn by a
-// persistent grid of as many blocks as fit on the device at once.
+// Two-step pass: the rolling kernel's items are strips of Roll::OUT output
+// columns times bands of ts_band rows, taken by a persistent grid of as many
+// blocks as fit on the device at once; each wave of items is all strips of
+// ts_wave_bands bands, and four waves give every resident warp about four
+// items.
 template <typename T>
 void twostep_grid(lbm_t* h, int per_sm) {
-  using TS = lbmk::TwoStep<T>;
-  h->ts_strips = (h->nx + TS::TX - 1) / TS::TX;
-  h->ts_bands = (h->ny + TS::TY - 1) / TS::TY;
-  h->ts_grid = std::max(1, std::min(h->ts_strips * h->ts_bands, per_sm * h->sms));
+  using R = lbmk::Roll<T>;
+  const int interior_x = h->nx - 4, interior_y = h->ny - 4;  // output nodes [2, n - 2)
+  h->ts_strips = (interior_x + R::OUT - 1) / R::OUT;
+  const int warps = std::max(1, per_sm * h->sms * R::WARPS);
+  const int per_wave = std::max(1, warps / h->ts_strips);  // bands side by side
+  const int want = std::max(1, std::min(4 * per_wave, interior_y));
+  h->ts_band = (interior_y + want - 1) / want;
+  h->ts_bands = (interior_y + h->ts_band - 1) / h->ts_band;
+  h->ts_wave_bands = std::min(per_wave, h->ts_bands);
+  h->ts_waves = (h->ts_bands + h->ts_wave_bands - 1) / h->ts_wave_bands;
+  const long long items = (long long)h->ts_waves * h->ts_wave_bands * h->ts_strips;
+  h->ts_grid = (int)std::max(1LL, std::min((items + R::WARPS - 1) / R::WARPS, (long long)per_sm * h->sms));
 }
 
 template <typename T, int MODEL, bool SHIFT>
 void launch_twostep_k(const lbm_t* h, const T* A, T* B, cudaStream_t s) {
-  auto k = lbmk::twostep_kernel<T, MODEL, SHIFT>;
-  k<<<h->ts_grid, lbmk::kTwoStepThreads, lbmk::TwoStep<T>::kSmem, s>>>(
-      A, B, lbmk::Geom{h->nx, h->ny, h->pitch, h->plane}, h->nsbc, rates<typename lbmk::Store<T>::C>(h),
-      h->ts_strips, h->ts_strips * h->ts_bands, h->d_sched);
+  using C = typename lbmk::Store<T>::C;
+  const lbmk::Geom g{h->nx, h->ny, h->pitch, h->plane};
+  const lbmk::Rates<C> r = rates<C>(h);
+  T* F = static_cast<T*>(h->d_frame);
+  const int perim = lbmk::ring_offset(h->nx, h->ny, 1);
+  auto frame_blocks = [&](int width) { return (4 * perim + lbmk::ring_offset(h->nx, h->ny, width) - perim + 127) / 128; };
+  // step n + 1 on the frame of width 3, A -> F
+  lbmk::frame_kernel<T, MODEL, SHIFT><<<frame_blocks(lbmk::kFrameWidth), 128, 0, s>>>(
+      lbmk::GlobalRawSrc<T>{A, h->plane, h->pitch}, lbmk::FrameDst<T>{F, h->nx, h->ny, h->frame_fn}, g, h->nsbc, r,
+      lbmk::kFrameWidth);
+  // steps n + 1 and n + 2 on the interior, A -> B
+  lbmk::roll_kernel<T, MODEL, SHIFT><<<h->ts_grid, lbmk::kRollThreads, lbmk::Roll<T>::kSmem, s>>>(
+      A, B, g, r, h->ts_strips, h->ts_band, h->ts_bands, h->ts_wave_bands, h->ts_waves, h->d_sched);
+  // step n + 2 on the frame of width 2, F -> B
+  lbmk::frame_kernel<T, MODEL, SHIFT><<<frame_blocks(2), 128, 0, s>>>(
+      lbmk::FrameSrc<T>{F, h->nx, h->ny, h->frame_fn}, lbmk::GlobalRawDst<T>{B, h->plane, h->pitch}, g, h->nsbc, r, 2);
 }
 
 template <typename T>
@@ -382,20 +407,24 @@ bool twostep_ok(const lbm_t* h) {
 
 template <typename T>
 int twostep_prepare(lbm_t* h) {
-  if (!h->d_sched) {  // the give-up flag of the bounded wait (lbm_status reads it)
+  if (!h->d_sched) {  // the give-up flag of the bounded waits (lbm_status reads it)
     LBM_CUDA(cudaMalloc(&h->d_sched, 4 * sizeof(int)));
     LBM_CUDA(cudaMemset(h->d_sched, 0, 4 * sizeof(int)));
   }
-  const int smem = (int)lbmk::TwoStep<T>::kSmem;
+  if (!h->d_frame) {
+    h->frame_fn = lbmk::ring_offset(h->nx, h->ny, lbmk::kFrameWidth);
+    LBM_CUDA(cudaMalloc(&h->d_frame, (size_t)9 * h->frame_fn * sizeof(T)));
+  }
+  const int smem = (int)lbmk::Roll<T>::kSmem;
   cudaError_t e = cudaSuccess;
   int per_sm = 0, sms = 0;
-  for (const void* k : {(const void*)lbmk::twostep_kernel<T, 0, false>, (const void*)lbmk::twostep_kernel<T, 0, true>,
-                        (const void*)lbmk::twostep_kernel<T, 1, false>, (const void*)lbmk::twostep_kernel<T, 1, true>})
+  for (const void* k : {(const void*)lbmk::roll_kernel<T, 0, false>, (const void*)lbmk::roll_kernel<T, 0, true>,
+                        (const void*)lbmk::roll_kernel<T, 1, false>, (const void*)lbmk::roll_kernel<T, 1, true>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbmk::twostep_kernel<T, 1, true>,
-                                                      lbmk::kTwoStepThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbmk::roll_kernel<T, 1, true>, lbmk::kRollThreads,
+                                                      smem);
   if (e != cudaSuccess)
     return fail(LBM_ECUDA, "two-step kernel: %d bytes of shared memory refused: %s", smem, cudaGetErrorString(e));
   if (per_sm <= 0) return fail(LBM_ECUDA, "two-step kernel: no block fits on an SM");
@@ -502,7 +531,7 @@ int ensure_twostep(lbm_t* h) {
   return rc;
 }
 
-// Two steps from buffer `from` to 1 - from in one launch.
+// Two steps from buffer `from` to 1 - from (three launches).
 void enqueue_twostep(const lbm_t* h, int from, cudaStream_t s) {
   dispatch(h->storage, [&](auto tag) {
     using T = decltype(tag);
@@ -597,8 +626,8 @@ int enqueue_step_profiled(lbm_t* h, int from) {
   return LBM_OK;
 }
 
-// Two steps in one launch with an event pair around it (counted as one bulk
-// launch; it carries two steps).
+// A two-step pass with an event pair around its three launches (counted as
+// one bulk launch; it carries two steps).
 int enqueue_twostep_profiled(lbm_t* h, int from) {
   cudaEvent_t e[2];
   int rc = profiled_pair(h, 0, e);
@@ -679,6 +708,7 @@ void lbm_destroy(lbm_t* h) {
   if (h->d_inst) cudaFree(h->d_inst);
   if (h->d_shift) cudaFree(h->d_shift);
   if (h->d_sched) cudaFree(h->d_sched);
+  if (h->d_frame) cudaFree(h->d_frame);
   if (h->cap) {
     cudaStreamDestroy(h->cap);
     cudaStreamDestroy(h->side);
