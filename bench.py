@@ -51,7 +51,7 @@ def parse():
                    help="'threads_x,rows[,prefetch]' (bulk + NSBC kernel pair), 'fused[:threads_x,rows,prefetch]' "
                         "(both in one launch), 'staged3' / 'staged4' or 'twostep' instead of autotuning")
     p.add_argument("--batched-only", action="store_true", help="time only the batched workload")
-    p.add_argument("--batch-launch", default="", help="batched launch 'threads_x,rows,blocks,prefetch,split'")
+    p.add_argument("--batch-launch", default="", help="batched launch 'threads_x,rows,blocks,prefetch,split[,tma_tile]' or 'twostep'")
     p.add_argument("--batch-count", type=int, default=256,
                    help="instances of the batched workload (--batched-only; fewer for profiling captures)")
     return p.parse_args()
@@ -275,7 +275,10 @@ def run_batched(lbm, ws, bfields, storage, steps, warmup, world, peak, launch=No
     bt = lbm.Batch(ws, storage=storage)
     for k, f in enumerate(bfields):
         bt.init(k, *f)
-    if launch:
+    if launch == "twostep":
+        tb = tr = tg = tp = ts = tt = None
+        bt.set_twostep(True)
+    elif launch:
         tb, tr, tg, tp, ts, tt = (list(launch) + [0, 0])[:6]
         bt.set_launch(tb, tr, tg, tp, ts, tt)
     else:
@@ -298,8 +301,9 @@ def run_batched(lbm, ws, bfields, storage, steps, warmup, world, peak, launch=No
            "sharding": (f"{world} ranks, instances split by nodes (lbm_partition_instances), no exchange; "
                         f"rank {rank} steps {len(ws)} instances, {bt.cells} nodes of {total_cells}")
            if world > 1 else "one rank, all instances",
-           "launch": {"threads_x": tb, "rows": tr, "blocks": tg, "prefetch_rows": tp, "split": ts,
-                      "tma_tile": tt},
+           "launch": ({"twostep": True} if bt.twostep else
+                      {"threads_x": tb, "rows": tr, "blocks": tg, "prefetch_rows": tp, "split": ts,
+                       "tma_tile": tt}),
            "unstable_nodes": bad, "what": batch_what(len(all_ws))}
     bt.close()
     del bt
@@ -340,7 +344,8 @@ def run_batched_only(args, rank, world, local_rank):
     ws = inputs.batch_instances(count=args.batch_count)
     bfields = [w.fields() for w in ws]
     peak, _ = measured_peak_gbs()
-    launch = [int(v) for v in args.batch_launch.split(",")] if args.batch_launch else None
+    launch = (args.batch_launch if args.batch_launch == "twostep" else
+              [int(v) for v in args.batch_launch.split(",")] if args.batch_launch else None)
     r = run_batched(lbm, ws, bfields, args.storage, args.steps, args.warmup, world, peak, launch, rank)
     if rank == 0:
         print(json.dumps({"metric": METRIC, "value": r["mlups"], "unit": UNIT, "n_gpus": world,

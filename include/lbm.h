@@ -431,9 +431,23 @@ int lbm_batch_unstable_nodes(lbm_batch_t* b, int32_t k, int64_t* count);
  * shape not compiled. */
 int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_t blocks, int32_t prefetch_rows,
                          int32_t split, int32_t tma_tile);
-/* Time every compiled tile shape, grid size, prefetch setting and split, and
- * the shared-memory path, on the batch's own state (restored afterwards,
- * through a temporary device copy from cudaMallocAsync) and keep the fastest. */
+/* Two steps per pass for every instance (the pass lbm_set_twostep describes,
+ * in three launches over all instances: rolling items in bands of at most
+ * 128 output rows, claimed by warps from a counter, largest instance first,
+ * and frame items of 128 threads; each instance's frame buffer after the
+ * last).  Bit-identical to two batched steps.  lbm_batch_step(n) runs n / 2
+ * passes (graphs of 16 steps) and, for odd n, one batched step of the launch
+ * shape set.  enable != 0 turns it on; lbm_batch_set_launch turns it off;
+ * lbm_batch_autotune times it against the other forms.  LBM_EINVAL when
+ * enabling it on f64 storage, with a periodic axis, or with an instance
+ * smaller than 8 x 8.  lbm_batch_get_twostep: 1 on, 0 off, LBM_EINVAL for
+ * NULL. */
+int lbm_batch_set_twostep(lbm_batch_t* b, int32_t enable);
+int32_t lbm_batch_get_twostep(const lbm_batch_t* b);
+/* Time every compiled tile shape, grid size, prefetch setting and split, the
+ * shared-memory paths and the two-step pass, on the batch's own state
+ * (restored afterwards, through a temporary device copy from
+ * cudaMallocAsync) and keep the fastest. */
 int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_t* blocks, int32_t* prefetch_rows,
                        int32_t* split, int32_t* tma_tile, double* ms_per_step);
 /* LBM_ETIMEOUT if a staged-tile wait of the shared-memory path gave up since

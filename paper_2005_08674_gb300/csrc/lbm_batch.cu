@@ -37,6 +37,7 @@
 #include "lbm_staged.cuh"
 #include "lbm_trace.h"
 #include "lbm_tune_cache.h"
+#include "lbm_twostep.cuh"
 
 int lbm_internal_fail(int code, const char* msg);
 // the autotuner cache of lbm_runtime.cu (lbm_set_tune_cache)
@@ -115,6 +116,15 @@ struct lbm_batch {
   int wave = 1;                        // resident blocks on the device for the current shape
   int tile = 128;                      // > 0: bulk tiles of this many vectors staged by bulk copies
   int* d_err = nullptr;                // [0] work counter, [1] blocks done, [2] a bounded wait gave up
+  // two-step passes (lbm_batch_set_twostep): the rolling kernel's items and
+  // grid, the frame launches' items (step n + 1 on the width-3 frames, step
+  // n + 2 on the width-2 frames) and the instances' frame buffers
+  bool twostep = false, ts_dirty = true;
+  int4* d_roll = nullptr;
+  int4* d_frame1 = nullptr;
+  int4* d_frame2 = nullptr;
+  void* d_frame = nullptr;
+  int n_roll = 0, n_frame1 = 0, n_frame2 = 0, roll_grid = 0;
   bool items_dirty = true;
   std::vector<char> initialised;
   int cur = 0;
@@ -594,6 +604,122 @@ int build_items(lbm_batch_t* b) {
   return LBM_OK;
 }
 
+// The two-step pass serves the batch: 16- or 32-bit storage, no periodic
+// axis, every instance 8 x 8 nodes or more.
+bool batch_twostep_ok(const lbm_batch_t* b) {
+  if (b->storage == LBM_F64 || b->nsbc.periodic_x || b->nsbc.periodic_y) return false;
+  for (const InstDev& d : b->inst)
+    if (d.nx < 8 || d.ny < 8) return false;
+  return true;
+}
+
+// Work lists of the two-step pass, largest instance first: rolling items in
+// bands of at most 128 output rows, all strips of a band side by side;
+// frame items of 128 threads; each instance's frame buffer after the last.
+int build_twostep(lbm_batch_t* b) {
+  if (!b->ts_dirty) return LBM_OK;
+  const int out = b->storage == LBM_F32 ? lbmk::Roll<float>::OUT : lbmk::Roll<__half>::OUT;
+  std::vector<int> order(b->count);
+  for (int k = 0; k < b->count; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int i, int j) {
+    return (long long)b->inst[i].nx * b->inst[i].ny > (long long)b->inst[j].nx * b->inst[j].ny;
+  });
+  std::vector<int4> roll, f1, f2;
+  long long foff = 0;
+  for (int k : order) {
+    const InstDev& d = b->inst[k];
+    const int strips = (d.nx - 4 + out - 1) / out, iy = d.ny - 4;
+    const int nb = (iy + 127) / 128, band = (iy + nb - 1) / nb;
+    for (int y = 2; y < d.ny - 2; y += band)
+      for (int j = 0; j < strips; ++j) roll.push_back(make_int4(k, j * out, y, std::min(y + band, d.ny - 2)));
+    if (foff > INT32_MAX - 9LL * lbmk::ring_offset(d.nx, d.ny, lbmk::kFrameWidth))
+      return bfail(LBM_EINVAL, "lbm_batch: frame buffers beyond 2^31 elements");
+    for (int t0 = 0; t0 < lbmk::frame_threads(d.nx, d.ny, lbmk::kFrameWidth); t0 += 128)
+      f1.push_back(make_int4(k, t0, (int)foff, 0));
+    for (int t0 = 0; t0 < lbmk::frame_threads(d.nx, d.ny, 2); t0 += 128) f2.push_back(make_int4(k, t0, (int)foff, 0));
+    foff += 9LL * lbmk::ring_offset(d.nx, d.ny, lbmk::kFrameWidth);
+  }
+  for (int4** p : {&b->d_roll, &b->d_frame1, &b->d_frame2}) {
+    cudaFree(*p);
+    *p = nullptr;
+  }
+  cudaFree(b->d_frame);
+  b->d_frame = nullptr;
+  BATCH_CUDA(cudaMalloc(&b->d_frame, (size_t)foff * b->elt));
+  BATCH_CUDA(cudaMalloc(&b->d_roll, roll.size() * sizeof(int4)));
+  BATCH_CUDA(cudaMalloc(&b->d_frame1, f1.size() * sizeof(int4)));
+  BATCH_CUDA(cudaMalloc(&b->d_frame2, f2.size() * sizeof(int4)));
+  BATCH_CUDA(cudaMemcpy(b->d_roll, roll.data(), roll.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  BATCH_CUDA(cudaMemcpy(b->d_frame1, f1.data(), f1.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  BATCH_CUDA(cudaMemcpy(b->d_frame2, f2.data(), f2.size() * sizeof(int4), cudaMemcpyHostToDevice));
+  b->n_roll = (int)roll.size();
+  b->n_frame1 = (int)f1.size();
+  b->n_frame2 = (int)f2.size();
+  // the rolling kernel's shared memory, and one resident wave of its blocks
+  int per_sm = 0, sms = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device);
+  bdispatch(b->storage, [&](auto tag) {
+    using T = decltype(tag);
+    if constexpr (!std::is_same<T, double>::value) {
+      const int smem = (int)lbmk::Roll<T>::kSmem;
+      for (const void* k :
+           {(const void*)lbmk::roll_batch_kernel<T, 0, false>, (const void*)lbmk::roll_batch_kernel<T, 0, true>,
+            (const void*)lbmk::roll_batch_kernel<T, 1, false>, (const void*)lbmk::roll_batch_kernel<T, 1, true>})
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbmk::roll_batch_kernel<T, 1, true>,
+                                                          lbmk::kRollThreads, smem);
+    }
+  });
+  if (e != cudaSuccess) return bfail(LBM_ECUDA, "lbm_batch: two-step kernel setup: %s", cudaGetErrorString(e));
+  if (per_sm <= 0) return bfail(LBM_ECUDA, "lbm_batch: no two-step block fits on an SM");
+  const int warps = lbmk::Roll<float>::WARPS;
+  b->roll_grid = std::max(1, std::min(per_sm * sms, (b->n_roll + warps - 1) / warps));
+  b->ts_dirty = false;
+  return LBM_OK;
+}
+
+// Two steps from pool `from` to 1 - from: three launches.
+void enqueue_batch_twostep(const lbm_batch_t* b, int from, cudaStream_t s) {
+  bdispatch(b->storage, [&](auto tag) {
+    using T = decltype(tag);
+    if constexpr (!std::is_same<T, double>::value) {
+      using C = typename lbmk::Store<T>::C;
+      const T* A = static_cast<const T*>(b->pool[from]);
+      T* B = static_cast<T*>(b->pool[1 - from]);
+      T* F = static_cast<T*>(b->d_frame);
+      const auto* zs = static_cast<const lbmk::Shift<C>*>(b->d_shift);
+      with_shift(b->shift, [&](auto zc) {
+        constexpr bool Z = decltype(zc)::value;
+        // the frame launches on the side stream, beside the rolling kernel
+        // (whose warps claim items, so blocks that start late take fewer)
+        cudaStream_t fs = b->side ? b->side : s;
+        auto go = [&](auto mc) {
+          constexpr int M = decltype(mc)::value;
+          if (fs != s) {
+            cudaEventRecord(b->ev_fork, s);
+            cudaStreamWaitEvent(fs, b->ev_fork, 0);
+          }
+          lbmk::frame_batch_kernel<T, M, Z, true><<<b->n_frame1, 128, 0, fs>>>(A, B, F, b->d_inst, zs, b->d_frame1,
+                                                                               b->nsbc, b->s_e, b->s_eps, b->s_q);
+          lbmk::roll_batch_kernel<T, M, Z><<<b->roll_grid, lbmk::kRollThreads, lbmk::Roll<T>::kSmem, s>>>(
+              A, B, b->d_inst, zs, b->d_roll, b->n_roll, b->s_e, b->s_eps, b->s_q, b->d_err);
+          lbmk::frame_batch_kernel<T, M, Z, false><<<b->n_frame2, 128, 0, fs>>>(A, B, F, b->d_inst, zs, b->d_frame2,
+                                                                                b->nsbc, b->s_e, b->s_eps, b->s_q);
+          if (fs != s) {
+            cudaEventRecord(b->ev_join, fs);
+            cudaStreamWaitEvent(s, b->ev_join, 0);
+          }
+        };
+        if (b->collision == 1)
+          go(std::integral_constant<int, 1>{});
+        else
+          go(std::integral_constant<int, 0>{});
+      });
+    }
+  });
+}
+
 int ensure_batch_memory(lbm_batch_t* b) {
   if (!b->bound) {
     const size_t pb = lbm_batch_buffer_bytes(b);
@@ -734,6 +860,10 @@ void lbm_batch_destroy(lbm_batch_t* b) {
   cudaFree(b->d_shift);
   cudaFree(b->d_items);
   cudaFree(b->d_err);
+  cudaFree(b->d_roll);
+  cudaFree(b->d_frame1);
+  cudaFree(b->d_frame2);
+  cudaFree(b->d_frame);
   if (b->cap) cudaStreamDestroy(b->cap);
   if (b->side) cudaStreamDestroy(b->side);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
@@ -867,12 +997,20 @@ int lbm_batch_step(lbm_batch_t* b, int32_t n) {
   if (rc) return rc;
   rc = ensure_batch_streams(b);
   if (rc) return rc;
+  const bool two = b->twostep && batch_twostep_ok(b);
+  if (two) {
+    rc = build_twostep(b);
+    if (rc) return rc;
+  }
   int left = n;
   if (left >= kBatchGraphSteps) {
     if (!b->graph[b->cur]) {
       cudaGraph_t g = nullptr;
       BATCH_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
-      for (int s = 0; s < kBatchGraphSteps; ++s) enqueue_batch_step(b, (b->cur + s) & 1, b->cap);
+      if (two)  // kBatchGraphSteps / 2 passes: an even number of pool swaps
+        for (int s = 0; s < kBatchGraphSteps / 2; ++s) enqueue_batch_twostep(b, (b->cur + s) & 1, b->cap);
+      else
+        for (int s = 0; s < kBatchGraphSteps; ++s) enqueue_batch_step(b, (b->cur + s) & 1, b->cap);
       cudaError_t e = cudaStreamEndCapture(b->cap, &g);
       if (e != cudaSuccess) return bfail(LBM_ECUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
       e = cudaGraphInstantiate(&b->graph[b->cur], g, 0);
@@ -883,6 +1021,10 @@ int lbm_batch_step(lbm_batch_t* b, int32_t n) {
       BATCH_CUDA(cudaGraphLaunch(b->graph[b->cur], b->stream));
       left -= kBatchGraphSteps;
     }
+  }
+  for (; two && left >= 2; left -= 2) {
+    enqueue_batch_twostep(b, b->cur, b->stream);
+    b->cur ^= 1;
   }
   for (; left > 0; --left) {
     enqueue_batch_step(b, b->cur, b->stream);
@@ -967,10 +1109,23 @@ int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_
   b->pf = prefetch_rows;
   b->split = tma_tile == 0 && split != 0;
   b->tile = tma_tile;
+  b->twostep = false;
   b->items_dirty = true;
   drop_batch_graphs(b);
   return LBM_OK;
 }
+
+int lbm_batch_set_twostep(lbm_batch_t* b, int32_t enable) {
+  if (!b) return bfail(LBM_EINVAL, "lbm_batch_set_twostep: NULL handle");
+  if (enable && !batch_twostep_ok(b))
+    return bfail(LBM_EINVAL, "lbm_batch_set_twostep: needs f32, f16 or bf16 storage, no periodic axis and every "
+                             "instance 8 x 8 nodes or more");
+  b->twostep = enable != 0;
+  drop_batch_graphs(b);
+  return LBM_OK;
+}
+
+int32_t lbm_batch_get_twostep(const lbm_batch_t* b) { return b ? (b->twostep ? 1 : 0) : LBM_EINVAL; }
 
 int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_t* blocks, int32_t* prefetch_rows,
                        int32_t* split, int32_t* tma_tile, double* ms_per_step) {
@@ -990,8 +1145,11 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
     const char* names[7] = {"threads_x", "rows", "blocks", "prefetch_rows", "split", "tma_tile", "ms_per_step"};
     bool ok = lbmtune::lookup(tune_path, tune_key, &e);
     for (int k = 0; ok && k < 7; ++k) ok = e.get(names[k], &v[k]);
+    double ts = 0.0;
+    ok = ok && e.get("twostep", &ts);
     if (ok && lbm_batch_set_launch(b, (int32_t)v[0], (int32_t)v[1], (int32_t)v[2], (int32_t)v[3], (int32_t)v[4],
-                                   (int32_t)v[5]) == LBM_OK) {
+                                   (int32_t)v[5]) == LBM_OK &&
+        (ts == 0.0 || lbm_batch_set_twostep(b, 1) == LBM_OK)) {
       lbm_internal_tune_count(true);
       if (threads_x) *threads_x = b->bx;
       if (rows) *rows = b->rows;
@@ -1014,7 +1172,8 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
   const int reps = (int)std::max<long long>(4, std::min<long long>(32, (1LL << 28) / std::max(b->cells, 1LL)));
   float best = 1e30f;
   int bb = b->bx, br = b->rows, bk = b->blocks, bp = b->pf, bt = b->tile;
-  bool bs = b->split;
+  bool bs = b->split, bts = false;
+  b->twostep = false;
   int rc = LBM_OK;
   auto time_it = [&]() -> float {
     for (int s = 0; s < 2; ++s) enqueue_batch_step(b, s & 1, b->stream);
@@ -1029,6 +1188,7 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
   auto keep = [&](float ms) {
     if (ms < best) {
       best = ms;
+      bts = false;
       bb = b->bx;
       br = b->rows;
       bk = b->blocks;
@@ -1086,6 +1246,26 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
       if (rc) break;
       keep(time_it());
     }
+  // two-step passes (their odd steps, if any, take the best single step)
+  if (!rc && batch_twostep_ok(b)) {
+    rc = build_twostep(b);
+    if (!rc) {
+      for (int s = 0; s < 2; ++s) enqueue_batch_twostep(b, s & 1, b->stream);
+      cudaEventRecord(e0, b->stream);
+      const int passes = std::max(2, reps / 2);
+      for (int s = 0; s < passes; ++s) enqueue_batch_twostep(b, s & 1, b->stream);
+      cudaEventRecord(e1, b->stream);
+      float ms = 1e30f;
+      if (cudaEventSynchronize(e1) == cudaSuccess) {
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= 2.0f * passes;
+      }
+      if (ms < best) {
+        best = ms;
+        bts = true;
+      }
+    }
+  }
   if (!rc) rc = batch_check_launch();
   b->bx = bb;
   b->rows = br;
@@ -1093,7 +1273,9 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
   b->pf = bp;
   b->split = bs;
   b->tile = bt;
+  b->twostep = bts;
   b->items_dirty = true;
+  drop_batch_graphs(b);
   int rc2 = build_items(b);
   BATCH_CUDA(cudaMemcpyAsync(b->pool[b->cur], backup, pb, cudaMemcpyDeviceToDevice, b->stream));
   BATCH_CUDA(cudaFreeAsync(backup, b->stream));
@@ -1106,7 +1288,7 @@ int lbm_batch_autotune(lbm_batch_t* b, int32_t* threads_x, int32_t* rows, int32_
     lbm_internal_tune_count(false);
     lbmtune::Entry e{tune_key,
                      {{"threads_x", bb}, {"rows", br}, {"blocks", bk}, {"prefetch_rows", bp}, {"split", bs ? 1 : 0},
-                      {"tma_tile", bt}, {"ms_per_step", best}}};
+                      {"tma_tile", bt}, {"twostep", bts ? 1 : 0}, {"ms_per_step", best}}};
     lbmtune::store(tune_path, e);  // a cache that cannot be written is only not reused
   }
   if (threads_x) *threads_x = bb;

@@ -373,18 +373,29 @@ void launch_twostep_k(const lbm_t* h, const T* A, T* B, cudaStream_t s) {
   const lbmk::Geom g{h->nx, h->ny, h->pitch, h->plane};
   const lbmk::Rates<C> r = rates<C>(h);
   T* F = static_cast<T*>(h->d_frame);
-  const int perim = lbmk::ring_offset(h->nx, h->ny, 1);
-  auto frame_blocks = [&](int width) { return (4 * perim + lbmk::ring_offset(h->nx, h->ny, width) - perim + 127) / 128; };
+  auto frame_blocks = [&](int width) { return (lbmk::frame_threads(h->nx, h->ny, width) + 127) / 128; };
+  // the frame launches on the side stream, beside the rolling kernel (they
+  // read A or F and write F or B's nodes at distance 0 and 1, the rolling
+  // kernel reads A and writes B's nodes at distance 2 or more)
+  cudaStream_t fs = h->side ? h->side : s;
+  if (fs != s) {
+    cudaEventRecord(h->ev_fork, s);
+    cudaStreamWaitEvent(fs, h->ev_fork, 0);
+  }
   // step n + 1 on the frame of width 3, A -> F
-  lbmk::frame_kernel<T, MODEL, SHIFT><<<frame_blocks(lbmk::kFrameWidth), 128, 0, s>>>(
+  lbmk::frame_kernel<T, MODEL, SHIFT><<<frame_blocks(lbmk::kFrameWidth), 128, 0, fs>>>(
       lbmk::GlobalRawSrc<T>{A, h->plane, h->pitch}, lbmk::FrameDst<T>{F, h->nx, h->ny, h->frame_fn}, g, h->nsbc, r,
       lbmk::kFrameWidth);
   // steps n + 1 and n + 2 on the interior, A -> B
   lbmk::roll_kernel<T, MODEL, SHIFT><<<h->ts_grid, lbmk::kRollThreads, lbmk::Roll<T>::kSmem, s>>>(
       A, B, g, r, h->ts_strips, h->ts_band, h->ts_bands, h->ts_wave_bands, h->ts_waves, h->d_sched);
   // step n + 2 on the frame of width 2, F -> B
-  lbmk::frame_kernel<T, MODEL, SHIFT><<<frame_blocks(2), 128, 0, s>>>(
+  lbmk::frame_kernel<T, MODEL, SHIFT><<<frame_blocks(2), 128, 0, fs>>>(
       lbmk::FrameSrc<T>{F, h->nx, h->ny, h->frame_fn}, lbmk::GlobalRawDst<T>{B, h->plane, h->pitch}, g, h->nsbc, r, 2);
+  if (fs != s) {
+    cudaEventRecord(h->ev_join, fs);
+    cudaStreamWaitEvent(s, h->ev_join, 0);
+  }
 }
 
 template <typename T>

@@ -9,7 +9,7 @@
 //   roll_kernel (A -> B): step n + 2 on the nodes at distance 2 or more.
 //       Each warp owns a strip of 32 x 4 columns and rolls down a band of
 //       rows: it stages the state rows by bulk copies in a private ring of
-//       four rows in shared memory, computes step n + 1 of each row (the
+//       three or four rows in shared memory, computes step n + 1 of each row (the
 //       interior collision only: every node it needs there is at distance 1
 //       or more) and keeps the populations that step n + 2 pulls from it in
 //       registers, rounded to the storage type as a single step stores them.
@@ -31,7 +31,7 @@ namespace lbmk {
 // ---------------------------------------------------------------------------
 // The frame of width w: nodes with d = min(x, y, nx-1-x, ny-1-y) < w.  Ring d
 // is the perimeter of the (nx - 2d) x (ny - 2d) domain at offset (d, d),
-// walked in perimeter_node's order; the rings are stored one after another.
+// walked in perimeter_node's order; ring_offset(d) nodes lie in rings below d.
 // ---------------------------------------------------------------------------
 __host__ __device__ inline int ring_offset(int nx, int ny, int d) {
   return d * (2 * nx + 2 * ny - 4) - 4 * d * (d - 1);
@@ -42,16 +42,15 @@ __host__ __device__ inline int ring_offset(int nx, int ny, int d) {
 // collision pulls from rings 0..2.
 constexpr int kFrameWidth = 3;
 
-// Perimeter index (perimeter_node's order) of edge node (x, y).
-__device__ __forceinline__ int perimeter_index(int x, int y, int nx, int ny) {
-  if (y == 0) return x;
-  if (y == ny - 1) return nx + x;
-  return 2 * nx + (x == 0 ? y - 1 : (ny - 2) + (y - 1));
-}
-
+// Element of frame node (x, y) (distance below kFrameWidth = w) in a plane
+// of the frame buffer: rows 0 .. w-1 (nx each), rows ny-w .. ny-1, then per
+// middle row y = w .. ny-w-1 its columns 0 .. w-1 and nx-w .. nx-1; the
+// plane holds ring_offset(nx, ny, w) = 2 w (nx + ny - 2 w) elements.
 __device__ __forceinline__ int frame_index(int x, int y, int nx, int ny) {
-  const int d = min(min(x, y), min(nx - 1 - x, ny - 1 - y));
-  return ring_offset(nx, ny, d) + perimeter_index(x - d, y - d, nx - 2 * d, ny - 2 * d);
+  constexpr int w = kFrameWidth;
+  if (y < w) return y * nx + x;
+  if (y >= ny - w) return (y - ny + 2 * w) * nx + x;
+  return 2 * w * nx + (y - w) * 2 * w + (x < w ? x : x - nx + 2 * w);
 }
 
 // Population i of frame node (x, y) in the frame buffer f (planes of fn
@@ -110,16 +109,16 @@ struct GlobalRawDst {
   }
 };
 
-// One step on the frame of width `width`: threads 0 .. 4 P - 1 (P perimeter
-// nodes) run the NSBC quads, the next ones one interior node of rings
-// 1 .. width - 1 each, pulled and collided in stored units like the interior
-// kernels.
+// Thread t's share of one step on the frame of width `width`: threads
+// 0 .. 4 P - 1 (P perimeter nodes) run the NSBC quads (a quad's four lanes
+// are consecutive threads of one warp), the next ones one interior node of
+// rings 1 .. width - 1 each, pulled and collided in stored units like the
+// interior kernels.
 template <typename T, int MODEL, bool SHIFT, typename Src, typename Dst>
-__global__ void __launch_bounds__(128) frame_kernel(Src src, Dst dst, Geom g, Nsbc p, Rates<typename Store<T>::C> r,
-                                                    int width) {
+__device__ __forceinline__ void frame_node(const Src& src, const Dst& dst, const Geom& g, const Nsbc& p,
+                                           const Rates<typename Store<T>::C>& r, int width, int t) {
   using S = Store<T>;
   using C = typename S::C;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const int perim = ring_offset(g.nx, g.ny, 1);
   if (t < 4 * perim) {  // 4 P is a multiple of 4: a quad stays together
     const int node[1] = {t >> 2};
@@ -146,6 +145,18 @@ __global__ void __launch_bounds__(128) frame_kernel(Src src, Dst dst, Geom g, Ns
   for (int i = 0; i < 9; ++i) dst.st_raw(i, x, y, h[i]);
 }
 
+// Threads on the frame of width `width`: 4 per perimeter node, 1 per node of
+// rings 1 .. width - 1.
+__host__ __device__ inline int frame_threads(int nx, int ny, int width) {
+  return 3 * ring_offset(nx, ny, 1) + ring_offset(nx, ny, width);
+}
+
+template <typename T, int MODEL, bool SHIFT, typename Src, typename Dst>
+__global__ void __launch_bounds__(128) frame_kernel(Src src, Dst dst, Geom g, Nsbc p, Rates<typename Store<T>::C> r,
+                                                    int width) {
+  frame_node<T, MODEL, SHIFT>(src, dst, g, p, r, width, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // The rolling interior kernel.
 // ---------------------------------------------------------------------------
@@ -156,7 +167,10 @@ struct Roll {
   // the strip, step n + 2 on 2 .. W - 3; strips start OUT apart, a multiple
   // of 16 bytes for the copies
   static constexpr int OUT = sizeof(T) == 4 ? W - 4 : W - 8;
-  static constexpr int DEPTH = 4;  // ring rows: three read, one in flight
+  // ring rows: three read while the next DEPTH - 3 are in flight (f32: the
+  // three alone -- the next row is staged as soon as the oldest is read --
+  // so that four blocks fit in shared memory)
+  static constexpr int DEPTH = sizeof(T) == 4 ? 3 : 4;
   static constexpr int ROWE = 9 * W;
   static constexpr int WARPS = 4;  // independent warps per block
   static constexpr size_t kSmem = (size_t)WARPS * DEPTH * ROWE * sizeof(T);
@@ -211,6 +225,127 @@ __device__ __forceinline__ void roll_stage(const T* __restrict__ A, const Geom& 
   if (ok) bulk_copy_g2s(dst + lane * R::W, src, bytes, bar);
 }
 
+// One work item of the rolling kernel: steps n + 1 and n + 2 of output rows
+// [Ya, Yb) x columns X0 + 2 .. X0 + 2 + OUT (clipped to [2, nx - 2)) of the
+// domain g, rolling down state rows Ya - 2 .. Yb + 1 through this warp's
+// ring (rows `ring`, barriers `bar`, their parities in `phase`).  All lanes
+// of the warp call it.  false: a wait gave up (err[2] is set).
+template <typename T, int MODEL, bool SHIFT>
+__device__ __forceinline__ bool roll_item(const T* __restrict__ A, T* __restrict__ B, const Geom& g,
+                                          const Rates<typename Store<T>::C>& r, int X0, int Ya, int Yb, T* ring,
+                                          uint64_t* bar, uint32_t& phase, int lane, int* __restrict__ err) {
+  using R = Roll<T>;
+  using S = Store<T>;
+  using C = typename S::C;
+  const int s0 = Ya - 2, s1 = Yb + 1;  // state rows read: s0 .. s1
+  __syncwarp();                        // the previous item's reads of the ring are done
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  for (int s = s0; s <= min(s0 + R::DEPTH - 1, s1); ++s)
+    roll_stage<T>(A, g, X0, s, ring + (s - s0) * R::ROWE, &bar[s - s0], lane);
+  // step n + 1 populations carried from row to row, already pulled along x:
+  // ip = row q - 1's c_y = +1 ones, i0 / ip2 = row q's c_y = 0 / +1 ones
+  C ip[3][4], i0[3][4], ip2[3][4];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) ip[a][k] = i0[a][k] = ip2[a][k] = C(0);
+  for (int s = s0, slot = 0; s <= s1; ++s, slot = slot + 1 == R::DEPTH ? 0 : slot + 1) {
+    {
+      const bool done = mbar_wait(&bar[slot], (phase >> slot) & 1u);
+      if (!__all_sync(0xffffffffu, done)) {
+        if (lane == 0) atomicExch(&err[2], 1);
+        return false;
+      }
+      phase ^= 1u << slot;
+    }
+    if (s < s0 + 2) continue;
+    // step n + 1 of row s - 1 from state rows s - 2, s - 1, s
+    const int slot_m1 = slot == 0 ? R::DEPTH - 1 : slot - 1;
+    const int slot_m2 = slot_m1 == 0 ? R::DEPTH - 1 : slot_m1 - 1;
+    C h[9][4];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int row = cy(i) > 0 ? slot_m2 : (cy(i) == 0 ? slot_m1 : slot);
+      roll_lds<T>(ring + row * R::ROWE + i * R::W + 4 * lane, h[i]);
+      shift_x(cx(i), h[i]);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      C n[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) n[i] = h[i][k];
+      collide<MODEL, SHIFT>(n, r, C(S::kScale));
+#pragma unroll
+      for (int i = 0; i < 9; ++i) h[i][k] = C(T(n[i]));  // rounded as a single step stores it
+    }
+    // row s - 2 is read: stage row s + DEPTH - 2 in its place
+    __syncwarp();
+    if (s + R::DEPTH - 2 <= s1) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      roll_stage<T>(A, g, X0, s + R::DEPTH - 2, ring + slot_m2 * R::ROWE, &bar[slot_m2], lane);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) shift_x(cx(i), h[i]);
+    // step n + 2 of row q = s - 2 (rows Ya .. Yb - 1) from step n + 1 rows q - 1, q, q + 1
+    const int q = s - 2;
+    if (q >= Ya) {
+      C o[9][4];
+#pragma unroll
+      for (int i = 0, a = 0, b = 0; i < 9; ++i) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o[i][k] = cy(i) > 0 ? ip[a][k] : (cy(i) == 0 ? i0[b][k] : h[i][k]);
+        a += cy(i) > 0;
+        b += cy(i) == 0;
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        C n[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) n[i] = o[i][k];
+        collide<MODEL, SHIFT>(n, r, C(S::kScale));
+#pragma unroll
+        for (int i = 0; i < 9; ++i) o[i][k] = n[i];
+      }
+      const int x0 = X0 + 4 * lane;
+      const int lo = max(max(2, X0 + 2), x0), hi = min(min(g.nx - 2, X0 + 2 + R::OUT), x0 + 4);
+      T* row = B + (long long)q * g.pitch + x0;
+      if (lo == x0 && hi == x0 + 4) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          if constexpr (sizeof(T) == 4)
+            S::st(row + i * g.plane, o[i]);
+          else
+            S::stp(row + i * g.plane, o[i]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (x0 + k >= lo && x0 + k < hi) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) S::st1r(row + i * g.plane + k, o[i][k]);
+          }
+      }
+    }
+    // carry: row s - 1 is the next q's row q
+#pragma unroll
+    for (int i = 0, a = 0, b = 0; i < 9; ++i) {
+      if (cy(i) > 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          ip[a][k] = ip2[a][k];
+          ip2[a][k] = h[i][k];
+        }
+      } else if (cy(i) == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) i0[b][k] = h[i][k];
+      }
+      a += cy(i) > 0;
+      b += cy(i) == 0;
+    }
+  }
+  return true;
+}
+
 // Two steps, A (step n) -> B (step n + 2), on nodes [2, nx - 2) x [2, ny - 2).
 // Work item = (strip, band): strip j reads columns X0 = j OUT .. X0 + W and
 // stores X0 + 2 .. X0 + 2 + OUT; band b stores rows 2 + b band .. + band.
@@ -222,12 +357,10 @@ __device__ __forceinline__ void roll_stage(const T* __restrict__ A, const Geom& 
 // (four rows staged again) on rows band b read just before.  A wait that
 // gives up sets err[2] and the warp returns.
 template <typename T, int MODEL, bool SHIFT>
-__global__ void __launch_bounds__(kRollThreads, sizeof(T) == 4 ? 3 : 4)
+__global__ void __launch_bounds__(kRollThreads, 4)
     roll_kernel(const T* __restrict__ A, T* __restrict__ B, Geom g, Rates<typename Store<T>::C> r, int n_strips,
                 int band, int n_bands, int bands_per_wave, int n_waves, int* __restrict__ err) {
   using R = Roll<T>;
-  using S = Store<T>;
-  using C = typename S::C;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[R::WARPS][R::DEPTH];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -249,111 +382,93 @@ __global__ void __launch_bounds__(kRollThreads, sizeof(T) == 4 ? 3 : 4)
     if (b >= n_bands) continue;
     const int X0 = strip * R::OUT;
     const int Ya = 2 + b * band, Yb = min(Ya + band, g.ny - 2);
-    const int s0 = Ya - 2, s1 = Yb + 1;  // state rows read: s0 .. s1
-    __syncwarp();                        // the previous item's reads of the ring are done
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    for (int s = s0; s <= min(s0 + R::DEPTH - 1, s1); ++s)
-      roll_stage<T>(A, g, X0, s, ring + (s - s0) * R::ROWE, &bar[s - s0], lane);
-    // step n + 1 populations carried from row to row, already pulled along x:
-    // ip = row q - 1's c_y = +1 ones, i0 / ip2 = row q's c_y = 0 / +1 ones
-    C ip[3][4], i0[3][4], ip2[3][4];
+    if (!roll_item<T, MODEL, SHIFT>(A, B, g, r, X0, Ya, Yb, ring, bar, phase, lane, err)) return;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The same pass over many independent instances (the batched mode): the
+// instance table, per-instance storage shifts and relaxation rates as the
+// batched single step takes them, so the bits are those of two batched steps.
+// ---------------------------------------------------------------------------
+// Rates and NSBC parameters of instance d, as the batched step forms them.
+template <typename C, bool SHIFT>
+__device__ __forceinline__ Rates<C> instance_rates(const InstDev& d, const Shift<C>* __restrict__ shifts, int k,
+                                                   double s_e, double s_eps, double s_q) {
+  Rates<C> r{C(d.omega), C(s_e), C(s_eps), C(s_q), {}};
+  if constexpr (SHIFT) r.z = shifts[k];
+  return r;
+}
+
+// Frame work: item j = {instance k, first frame thread t0 of this block (a
+// multiple of 128), element offset of the instance's frame buffer (9 planes
+// of ring_offset(nx, ny, 3) elements), 0}; one block of 128 threads per item.
+// TO_FRAME: step n + 1 from pool A into the frame buffers F (width 3); else
+// step n + 2 from F into pool B (width 2).
+template <typename T, int MODEL, bool SHIFT, bool TO_FRAME>
+__global__ void __launch_bounds__(128) frame_batch_kernel(const T* __restrict__ A, T* __restrict__ B, T* __restrict__ F,
+                                                          const InstDev* __restrict__ inst,
+                                                          const Shift<typename Store<T>::C>* __restrict__ shifts,
+                                                          const int4* __restrict__ items, Nsbc p, double s_e,
+                                                          double s_eps, double s_q) {
+  using C = typename Store<T>::C;
+  const int4 w = items[blockIdx.x];
+  const InstDev d = inst[w.x];
+  const Rates<C> r = instance_rates<C, SHIFT>(d, shifts, w.x, s_e, s_eps, s_q);
+  Nsbc q = p;
+  q.m0[0] = d.m0[0];
+  q.m0[1] = d.m0[1];
+  q.m0[2] = d.m0[2];
+  const Geom g{d.nx, d.ny, d.pitch, d.plane};
+  const int fn = ring_offset(d.nx, d.ny, kFrameWidth);
+  const int t = w.y + threadIdx.x;
+  if constexpr (TO_FRAME)
+    frame_node<T, MODEL, SHIFT>(GlobalRawSrc<T>{A + d.off, d.plane, d.pitch}, FrameDst<T>{F + w.z, d.nx, d.ny, fn}, g,
+                                q, r, kFrameWidth, t);
+  else
+    frame_node<T, MODEL, SHIFT>(FrameSrc<T>{F + w.z, d.nx, d.ny, fn}, GlobalRawDst<T>{B + d.off, d.plane, d.pitch}, g,
+                                q, r, 2, t);
+}
+
+// Rolling work: item j = {instance k, strip start X0, output rows Ya, Yb}.
+// Warps claim items from a counter (sched[0]; the last warp to finish resets
+// it and sched[1]); items come largest instance first, all strips of a band
+// side by side.  A wait that gives up sets sched[2] and the warp returns.
+template <typename T, int MODEL, bool SHIFT>
+__global__ void __launch_bounds__(kRollThreads, 4)
+    roll_batch_kernel(const T* __restrict__ A, T* __restrict__ B, const InstDev* __restrict__ inst,
+                      const Shift<typename Store<T>::C>* __restrict__ shifts, const int4* __restrict__ items,
+                      int n_items, double s_e, double s_eps, double s_q, int* __restrict__ sched) {
+  using R = Roll<T>;
+  using C = typename Store<T>::C;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bars[R::WARPS][R::DEPTH];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  T* ring = reinterpret_cast<T*>(smem_raw) + warp * R::DEPTH * R::ROWE;
+  uint64_t* bar = bars[warp];
+  if (lane == 0) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int k = 0; k < 4; ++k) ip[a][k] = i0[a][k] = ip2[a][k] = C(0);
-    for (int s = s0; s <= s1; ++s) {
-      const int slot = (s - s0) & (R::DEPTH - 1);
-      {
-        const bool done = mbar_wait(&bar[slot], (phase >> slot) & 1u);
-        if (!__all_sync(0xffffffffu, done)) {
-          if (lane == 0) atomicExch(&err[2], 1);
-          return;
-        }
-        phase ^= 1u << slot;
-      }
-      if (s < s0 + 2) continue;
-      // step n + 1 of row s - 1 from state rows s - 2, s - 1, s
-      C h[9][4];
-#pragma unroll
-      for (int i = 0; i < 9; ++i) {
-        const int row = (s - 1 - cy(i) - s0) & (R::DEPTH - 1);
-        roll_lds<T>(ring + row * R::ROWE + i * R::W + 4 * lane, h[i]);
-        shift_x(cx(i), h[i]);
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        C n[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) n[i] = h[i][k];
-        collide<MODEL, SHIFT>(n, r, C(S::kScale));
-#pragma unroll
-        for (int i = 0; i < 9; ++i) h[i][k] = C(T(n[i]));  // rounded as a single step stores it
-      }
-      // row s - 2 is read: stage row s + 2 in its place
-      __syncwarp();
-      if (s + 2 <= s1) {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        const int j = (s + 2 - s0) & (R::DEPTH - 1);
-        roll_stage<T>(A, g, X0, s + 2, ring + j * R::ROWE, &bar[j], lane);
-      }
-#pragma unroll
-      for (int i = 0; i < 9; ++i) shift_x(cx(i), h[i]);
-      // step n + 2 of row q = s - 2 (rows Ya .. Yb - 1) from step n + 1 rows q - 1, q, q + 1
-      const int q = s - 2;
-      if (q >= Ya) {
-        C o[9][4];
-#pragma unroll
-        for (int i = 0, a = 0, b = 0; i < 9; ++i) {
-#pragma unroll
-          for (int k = 0; k < 4; ++k) o[i][k] = cy(i) > 0 ? ip[a][k] : (cy(i) == 0 ? i0[b][k] : h[i][k]);
-          a += cy(i) > 0;
-          b += cy(i) == 0;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          C n[9];
-#pragma unroll
-          for (int i = 0; i < 9; ++i) n[i] = o[i][k];
-          collide<MODEL, SHIFT>(n, r, C(S::kScale));
-#pragma unroll
-          for (int i = 0; i < 9; ++i) o[i][k] = n[i];
-        }
-        const int x0 = X0 + 4 * lane;
-        const int lo = max(max(2, X0 + 2), x0), hi = min(min(g.nx - 2, X0 + 2 + R::OUT), x0 + 4);
-        T* row = B + (long long)q * g.pitch + x0;
-        if (lo == x0 && hi == x0 + 4) {
-#pragma unroll
-          for (int i = 0; i < 9; ++i) {
-            if constexpr (sizeof(T) == 4)
-              S::st(row + i * g.plane, o[i]);
-            else
-              S::stp(row + i * g.plane, o[i]);
-          }
-        } else {
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            if (x0 + k >= lo && x0 + k < hi) {
-#pragma unroll
-              for (int i = 0; i < 9; ++i) S::st1r(row + i * g.plane + k, o[i][k]);
-            }
-        }
-      }
-      // carry: row s - 1 is the next q's row q
-#pragma unroll
-      for (int i = 0, a = 0, b = 0; i < 9; ++i) {
-        if (cy(i) > 0) {
-#pragma unroll
-          for (int k = 0; k < 4; ++k) {
-            ip[a][k] = ip2[a][k];
-            ip2[a][k] = h[i][k];
-          }
-        } else if (cy(i) == 0) {
-#pragma unroll
-          for (int k = 0; k < 4; ++k) i0[b][k] = h[i][k];
-        }
-        a += cy(i) > 0;
-        b += cy(i) == 0;
-      }
+    for (int j = 0; j < R::DEPTH; ++j) mbar_init(&bar[j], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  uint32_t phase = 0u;
+  for (;;) {
+    int c = 0;
+    if (lane == 0) c = atomicAdd(&sched[0], 1);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c >= n_items) break;
+    const int4 w = items[c];
+    const InstDev d = inst[w.x];
+    const Rates<C> r = instance_rates<C, SHIFT>(d, shifts, w.x, s_e, s_eps, s_q);
+    const Geom g{d.nx, d.ny, d.pitch, d.plane};
+    if (!roll_item<T, MODEL, SHIFT>(A + d.off, B + d.off, g, r, w.y, w.z, w.w, ring, bar, phase, lane, sched)) return;
+  }
+  if (lane == 0) {
+    __threadfence();
+    if (atomicAdd(&sched[1], 1) == (int)gridDim.x * R::WARPS - 1) {
+      sched[0] = 0;
+      sched[1] = 0;
     }
   }
 }

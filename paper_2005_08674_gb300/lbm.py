@@ -94,6 +94,8 @@ _SIGS = {
     "lbm_batch_unstable_nodes": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(ctypes.c_int64)]),
     "lbm_batch_set_launch": (ctypes.c_int, [_vp, _i32, _i32, _i32, _i32, _i32, _i32]),
     "lbm_batch_autotune": (ctypes.c_int, [_vp, _i32p, _i32p, _i32p, _i32p, _i32p, _i32p, _dp]),
+    "lbm_batch_set_twostep": (ctypes.c_int, [_vp, _i32]),
+    "lbm_batch_get_twostep": (ctypes.c_int32, [_vp]),
     "lbm_batch_status": (ctypes.c_int, [_vp]),
     "lbm_wait_selftest": (ctypes.c_int, [ctypes.c_int64]),
     "lbm_partition_instances": (ctypes.c_int, [_i32, ctypes.POINTER(ctypes.c_int64), _i32, _i32p]),
@@ -646,6 +648,14 @@ def lbm_batch_status(b):
     return _check(_L.lbm_batch_status(b))
 
 
+def lbm_batch_set_twostep(b, enable: bool):
+    return _check(_L.lbm_batch_set_twostep(b, int(bool(enable))))
+
+
+def lbm_batch_get_twostep(b) -> int:
+    return int(_L.lbm_batch_get_twostep(b))
+
+
 def lbm_partition_instances(cells, ranks: int):
     """Rank of each instance for a node-balanced split over `ranks` (see lbm.h)."""
     n = len(cells)
@@ -736,3 +746,12 @@ class Batch:
 
     def status(self):
         return lbm_batch_status(self.b)
+
+    def set_twostep(self, enable=True):
+        """Two steps per pass for every instance (see lbm_batch_set_twostep)."""
+        lbm_batch_set_twostep(self.b, enable)
+        return self
+
+    @property
+    def twostep(self) -> bool:
+        return lbm_batch_get_twostep(self.b) == 1
