@@ -13,6 +13,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "lbm_check.cuh"
 
 namespace lbmk {
@@ -393,6 +395,50 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ float div_rho(float a, float rho) { return __fdividef(a, rho); }
 __device__ __forceinline__ double div_rho(double a, double rho) { return a / rho; }
 
+// The interior collision's arithmetic, every operation rounded on its own
+// (none fused by the compiler), on one node (float, double) or on two nodes
+// at once (float2: the paired FP32 instructions of sm_100 and later, whose
+// components round exactly as the scalar __fadd_rn / __fmul_rn / __fmaf_rn
+// do).  The same sequence of operations therefore gives the same bits for a
+// node whether it is collided alone or beside another.
+__device__ __forceinline__ float v_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double v_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float2 v_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float v_neg(float a) { return -a; }
+__device__ __forceinline__ double v_neg(double a) { return -a; }
+__device__ __forceinline__ float2 v_neg(float2 a) { return make_float2(-a.x, -a.y); }
+template <typename V>
+__device__ __forceinline__ V v_sub(V a, V b) {
+  return v_add(a, v_neg(b));  // a - b = a + (-b), rounded once
+}
+__device__ __forceinline__ float v_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double v_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float2 v_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float v_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double v_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float2 v_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+template <typename V, typename C>
+__device__ __forceinline__ V v_splat(C c) {
+  if constexpr (std::is_same<V, float2>::value)
+    return make_float2(c, c);
+  else
+    return V(c);
+}
+__device__ __forceinline__ float v_div_rho(float a, float rho) { return div_rho(a, rho); }
+__device__ __forceinline__ double v_div_rho(double a, double rho) { return div_rho(a, rho); }
+__device__ __forceinline__ float2 v_div_rho(float a, float2 rho) {
+  return make_float2(div_rho(a, rho.x), div_rho(a, rho.y));
+}
+// the moments' sums (as moments() forms them) in this arithmetic
+template <typename V>
+__device__ __forceinline__ void v_moments(const V (&h)[9], V& drho, V& jx, V& jy) {
+  drho = v_add(v_add(v_add(v_add(h[0], h[1]), v_add(h[2], h[3])), v_add(v_add(h[4], h[5]), v_add(h[6], h[7]))),
+               h[8]);
+  const V a = v_sub(h[5], h[6]);
+  jx = v_add(v_add(v_sub(h[1], h[2]), a), v_sub(h[8], h[7]));
+  jy = v_add(v_add(v_sub(h[3], h[4]), a), v_sub(h[7], h[8]));
+}
+
 // Equilibrium in deviations from the far field: E_i = f_i^eq(rho, u) -
 // f_i^eq(rho0, u0) (Eq. feq_1 at two states, cs^2 = 1/3) times the weight
 // scale ws, from d = rho - rho0, v = u - u0 and the momentum deviation
@@ -410,49 +456,52 @@ __device__ __forceinline__ double div_rho(double a, double rho) { return a / rho
 // BGK relaxation puts back is the node's own to the rounding of each term.
 // For a far field at rest (SHIFT false: rho0 = 1, u0 = 0, P_i(u0) = 1) this
 // is w_i (d + 3 c_i.J + rho (4.5 (c_i.u)^2 - 1.5 u.u)).
-template <bool SHIFT, typename C>
-__device__ __forceinline__ void equilibrium_dev(C d, C vx, C vy, C jx, C jy, const Shift<C>& z, C (&e)[9],
+template <bool SHIFT, typename V, typename C>
+__device__ __forceinline__ void equilibrium_dev(V d, V vx, V vy, V jx, V jy, const Shift<C>& z, V (&e)[9],
                                                 C ws = C(1)) {
-  // every multiply-add is explicit, so that the shifted form with a zero
-  // shift (rho0 = 1, u0 = 0, P_i(u0) = 1) rounds exactly like the plain one
-  C rho, sx, sy;
+  // every operation is rounded on its own (v_add / v_mul / v_fma), so that
+  // the shifted form with a zero shift (rho0 = 1, u0 = 0, P_i(u0) = 1) rounds
+  // exactly like the plain one, and two nodes at once like one at a time
+  V rho, sx, sy;
   if constexpr (SHIFT) {
-    rho = z.rho0 + d;
-    sx = fma_rn(C(2), z.u0[0], vx);
-    sy = fma_rn(C(2), z.u0[1], vy);
+    rho = v_add(v_splat<V>(z.rho0), d);
+    sx = v_fma(v_splat<V>(C(2)), v_splat<V>(z.u0[0]), vx);
+    sy = v_fma(v_splat<V>(C(2)), v_splat<V>(z.u0[1]), vy);
   } else {
-    rho = C(1) + d;
+    rho = v_add(v_splat<V>(C(1)), d);
     sx = vx;
     sy = vy;
   }
-  C dp[9];  // d P_i(u0)
+  V dp[9];  // d P_i(u0)
 #pragma unroll
-  for (int i = 0; i < 9; ++i) dp[i] = SHIFT ? mul_rn(d, z.p0[i]) : d;
-  const C vs = C(1.5) * fma_rn(vx, sx, mul_rn(vy, sy));
-  const C w0 = wt<C>(0) * ws, wa = wt<C>(1) * ws, wd = wt<C>(5) * ws;
-  e[0] = w0 * fma_rn(-rho, vs, dp[0]);
+  for (int i = 0; i < 9; ++i) dp[i] = SHIFT ? v_mul(d, v_splat<V>(z.p0[i])) : d;
+  const V vs = v_mul(v_splat<V>(C(1.5)), v_fma(vx, sx, v_mul(vy, sy)));
+  const V nvs = v_neg(vs);
+  const V w0 = v_splat<V>(wt<C>(0) * ws), wa = v_splat<V>(wt<C>(1) * ws), wd = v_splat<V>(wt<C>(5) * ws);
+  const V c45 = v_splat<V>(C(4.5)), c3 = v_splat<V>(C(3));
+  e[0] = v_mul(w0, v_fma(v_neg(rho), vs, dp[0]));
   // axis directions: c.v = +-vx, +-vy
   {
-    const C q = fma_rn(C(4.5) * vx, sx, -vs), b = C(3) * jx;
-    e[1] = wa * (fma_rn(rho, q, dp[1]) + b);
-    e[2] = wa * (fma_rn(rho, q, dp[2]) - b);
+    const V q = v_fma(v_mul(c45, vx), sx, nvs), b = v_mul(c3, jx);
+    e[1] = v_mul(wa, v_add(v_fma(rho, q, dp[1]), b));
+    e[2] = v_mul(wa, v_sub(v_fma(rho, q, dp[2]), b));
   }
   {
-    const C q = fma_rn(C(4.5) * vy, sy, -vs), b = C(3) * jy;
-    e[3] = wa * (fma_rn(rho, q, dp[3]) + b);
-    e[4] = wa * (fma_rn(rho, q, dp[4]) - b);
+    const V q = v_fma(v_mul(c45, vy), sy, nvs), b = v_mul(c3, jy);
+    e[3] = v_mul(wa, v_add(v_fma(rho, q, dp[3]), b));
+    e[4] = v_mul(wa, v_sub(v_fma(rho, q, dp[4]), b));
   }
   {
-    const C cv = vx + vy, cs = sx + sy;  // c_5 = -c_6 = (1, 1)
-    const C q = fma_rn(C(4.5) * cv, cs, -vs), b = C(3) * (jx + jy);
-    e[5] = wd * (fma_rn(rho, q, dp[5]) + b);
-    e[6] = wd * (fma_rn(rho, q, dp[6]) - b);
+    const V cv = v_add(vx, vy), cs = v_add(sx, sy);  // c_5 = -c_6 = (1, 1)
+    const V q = v_fma(v_mul(c45, cv), cs, nvs), b = v_mul(c3, v_add(jx, jy));
+    e[5] = v_mul(wd, v_add(v_fma(rho, q, dp[5]), b));
+    e[6] = v_mul(wd, v_sub(v_fma(rho, q, dp[6]), b));
   }
   {
-    const C cv = vy - vx, cs = sy - sx;  // c_7 = -c_8 = (-1, 1)
-    const C q = fma_rn(C(4.5) * cv, cs, -vs), b = C(3) * (jy - jx);
-    e[7] = wd * (fma_rn(rho, q, dp[7]) + b);
-    e[8] = wd * (fma_rn(rho, q, dp[8]) - b);
+    const V cv = v_sub(vy, vx), cs = v_sub(sy, sx);  // c_7 = -c_8 = (-1, 1)
+    const V q = v_fma(v_mul(c45, cv), cs, nvs), b = v_mul(c3, v_sub(jy, jx));
+    e[7] = v_mul(wd, v_add(v_fma(rho, q, dp[7]), b));
+    e[8] = v_mul(wd, v_sub(v_fma(rho, q, dp[8]), b));
   }
 }
 
@@ -466,26 +515,29 @@ __device__ __forceinline__ void equilibrium_dev(C d, C vx, C vy, C jx, C jy, con
 // the stream's equilibrium is ever rounded.  The relaxation is one explicitly
 // rounded fused multiply-add per population in both forms, and the shifted
 // form with a zero shift gives the same bits as the plain one.
-template <bool SHIFT, typename C>
-__device__ __forceinline__ void collide_bgk(C (&h)[9], const Rates<C>& r, C s = C(1)) {
+template <bool SHIFT, typename V, typename C>
+__device__ __forceinline__ void collide_bgk(V (&h)[9], const Rates<C>& r, C s = C(1)) {
   const C omega = r.omega;
-  C sd, sjx, sjy;
-  moments(h, sd, sjx, sjy);
+  V sd, sjx, sjy;
+  v_moments(h, sd, sjx, sjy);
   const C is = C(1) / s;
-  const C d = sd * is;  // rho - rho0
-  C e[9];
+  const V vis = v_splat<V>(is);
+  const V d = v_mul(sd, vis);  // rho - rho0
+  V e[9];
   if constexpr (SHIFT) {
     // J = rho (u - u0) = sum c h - d u0 and v = J / rho, from small quantities only
-    const C inv = div_rho(is, r.z.rho0 + d);
-    const C jx = fma_rn(-sd, r.z.u0[0], sjx), jy = fma_rn(-sd, r.z.u0[1], sjy);
-    equilibrium_dev<true>(d, jx * inv, jy * inv, jx * is, jy * is, r.z, e, s * omega);
+    const V inv = v_div_rho(is, v_add(v_splat<V>(r.z.rho0), d));
+    const V nsd = v_neg(sd);
+    const V jx = v_fma(nsd, v_splat<V>(r.z.u0[0]), sjx), jy = v_fma(nsd, v_splat<V>(r.z.u0[1]), sjy);
+    equilibrium_dev<true>(d, v_mul(jx, inv), v_mul(jy, inv), v_mul(jx, vis), v_mul(jy, vis), r.z, e, s * omega);
   } else {
-    const C inv = div_rho(is, C(1) + d);
-    equilibrium_dev<false>(d, sjx * inv, sjy * inv, sjx * is, sjy * is, r.z, e, s * omega);
+    const V inv = v_div_rho(is, v_add(v_splat<V>(C(1)), d));
+    equilibrium_dev<false>(d, v_mul(sjx, inv), v_mul(sjy, inv), v_mul(sjx, vis), v_mul(sjy, vis), r.z, e,
+                           s * omega);
   }
-  const C keep = C(1) - omega;
+  const V keep = v_splat<V>(C(1) - omega);
 #pragma unroll
-  for (int i = 0; i < 9; ++i) h[i] = fma_rn(keep, h[i], e[i]);
+  for (int i = 0; i < 9; ++i) h[i] = v_fma(keep, h[i], e[i]);
 }
 
 // ---------------------------------------------------------------------------
@@ -551,6 +603,40 @@ __device__ __forceinline__ void collide(C (&h)[9], const Rates<C>& r, C s = C(1)
     collide_mrt<SHIFT>(h, r, s);
   else
     collide_bgk<SHIFT>(h, r, s);
+}
+
+// The collision of N nodes held as h[i][k] (population i of node k): with
+// PAIRED, in float BGK, two nodes per paired instruction (half the
+// arithmetic instructions, at the price of register pairs: worth it where
+// the kernel is bound by instruction issue and has registers to spare),
+// otherwise one after another; the bits of each node are those of collide()
+// on it alone either way.
+template <int MODEL, bool SHIFT, bool PAIRED, typename C, int N>
+__device__ __forceinline__ void collide_nodes(C (&h)[9][N], const Rates<C>& r, C s = C(1)) {
+  if constexpr (PAIRED && MODEL == 0 && std::is_same<C, float>::value && N % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < N; k += 2) {
+      float2 p[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) p[i] = make_float2(h[i][k], h[i][k + 1]);
+      collide_bgk<SHIFT>(p, r, s);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        h[i][k] = p[i].x;
+        h[i][k + 1] = p[i].y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      C n[9];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) n[i] = h[i][k];
+      collide<MODEL, SHIFT>(n, r, s);
+#pragma unroll
+      for (int i = 0; i < 9; ++i) h[i][k] = n[i];
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -108,20 +108,17 @@ __device__ __forceinline__ void bulk_row(const T* __restrict__ A, T* __restrict_
     C o[9][V];
 #pragma unroll
     for (int k = 0; k < V; ++k) {
-      C h[9];
-      h[0] = v[0][k];
-      h[1] = k == 0 ? l1 : v[1][k - 1];
-      h[2] = k == V - 1 ? r2 : v[2][k + 1];
-      h[3] = v[3][k];
-      h[4] = v[4][k];
-      h[5] = k == 0 ? l5 : v[5][k - 1];
-      h[6] = k == V - 1 ? r6 : v[6][k + 1];
-      h[7] = k == V - 1 ? r7 : v[7][k + 1];
-      h[8] = k == 0 ? l8 : v[8][k - 1];
-      collide<MODEL, SHIFT>(h, rates, C(S::kScale));  // in stored units
-#pragma unroll
-      for (int i = 0; i < 9; ++i) o[i][k] = h[i];
+      o[0][k] = v[0][k];
+      o[1][k] = k == 0 ? l1 : v[1][k - 1];
+      o[2][k] = k == V - 1 ? r2 : v[2][k + 1];
+      o[3][k] = v[3][k];
+      o[4][k] = v[4][k];
+      o[5][k] = k == 0 ? l5 : v[5][k - 1];
+      o[6][k] = k == V - 1 ? r6 : v[6][k + 1];
+      o[7][k] = k == V - 1 ? r7 : v[7][k + 1];
+      o[8][k] = k == 0 ? l8 : v[8][k - 1];
     }
+    collide_nodes<MODEL, SHIFT, false>(o, rates, C(S::kScale));  // in stored units
     if (active) {
       if (x0 >= 1 && x0 + V <= g.nx - 1) {
 #pragma unroll

@@ -170,20 +170,17 @@ __device__ __forceinline__ void collide_tile(const unsigned char* sl, const Inst
     C o[9][CPT];
 #pragma unroll
     for (int kk = 0; kk < CPT; ++kk) {
-      C h[9];
-      h[0] = v[0][kk];
-      h[1] = kk == 0 ? lf[1] : v[1][kk - 1];
-      h[2] = kk == CPT - 1 ? rt[2] : v[2][kk + 1];
-      h[3] = v[3][kk];
-      h[4] = v[4][kk];
-      h[5] = kk == 0 ? lf[5] : v[5][kk - 1];
-      h[6] = kk == CPT - 1 ? rt[6] : v[6][kk + 1];
-      h[7] = kk == CPT - 1 ? rt[7] : v[7][kk + 1];
-      h[8] = kk == 0 ? lf[8] : v[8][kk - 1];
-      lbmk::collide<MODEL, SHIFT>(h, r, C(S::kScale));
-#pragma unroll
-      for (int i = 0; i < 9; ++i) o[i][kk] = h[i];
+      o[0][kk] = v[0][kk];
+      o[1][kk] = kk == 0 ? lf[1] : v[1][kk - 1];
+      o[2][kk] = kk == CPT - 1 ? rt[2] : v[2][kk + 1];
+      o[3][kk] = v[3][kk];
+      o[4][kk] = v[4][kk];
+      o[5][kk] = kk == 0 ? lf[5] : v[5][kk - 1];
+      o[6][kk] = kk == CPT - 1 ? rt[6] : v[6][kk + 1];
+      o[7][kk] = kk == CPT - 1 ? rt[7] : v[7][kk + 1];
+      o[8][kk] = kk == 0 ? lf[8] : v[8][kk - 1];
     }
+    lbmk::collide_nodes<MODEL, SHIFT, false>(o, r, C(S::kScale));
     const long long r0 = (long long)y * d.pitch + x0;
     if (x0 >= 1 && x0 + CPT <= d.nx - 1) {
 #pragma unroll

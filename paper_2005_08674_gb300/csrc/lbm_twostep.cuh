@@ -173,6 +173,9 @@ struct Roll {
   static constexpr int DEPTH = sizeof(T) == 4 ? 3 : 4;
   static constexpr int ROWE = 9 * W;
   static constexpr int WARPS = 4;  // independent warps per block
+  // paired FP32 collisions for 16-bit storage, whose kernel is bound by
+  // instruction issue; f32 has no registers to spare for them
+  static constexpr bool PAIRED = sizeof(T) == 2;
   static constexpr size_t kSmem = (size_t)WARPS * DEPTH * ROWE * sizeof(T);
 };
 constexpr int kRollThreads = 32 * 4;
@@ -269,15 +272,11 @@ __device__ __forceinline__ bool roll_item(const T* __restrict__ A, T* __restrict
       roll_lds<T>(ring + row * R::ROWE + i * R::W + 4 * lane, h[i]);
       shift_x(cx(i), h[i]);
     }
+    collide_nodes<MODEL, SHIFT, R::PAIRED>(h, r, C(S::kScale));
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      C n[9];
+    for (int i = 0; i < 9; ++i)
 #pragma unroll
-      for (int i = 0; i < 9; ++i) n[i] = h[i][k];
-      collide<MODEL, SHIFT>(n, r, C(S::kScale));
-#pragma unroll
-      for (int i = 0; i < 9; ++i) h[i][k] = C(T(n[i]));  // rounded as a single step stores it
-    }
+      for (int k = 0; k < 4; ++k) h[i][k] = C(T(h[i][k]));  // rounded as a single step stores it
     // row s - 2 is read: stage row s + DEPTH - 2 in its place
     __syncwarp();
     if (s + R::DEPTH - 2 <= s1) {
@@ -297,15 +296,7 @@ __device__ __forceinline__ bool roll_item(const T* __restrict__ A, T* __restrict
         a += cy(i) > 0;
         b += cy(i) == 0;
       }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        C n[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) n[i] = o[i][k];
-        collide<MODEL, SHIFT>(n, r, C(S::kScale));
-#pragma unroll
-        for (int i = 0; i < 9; ++i) o[i][k] = n[i];
-      }
+      collide_nodes<MODEL, SHIFT, R::PAIRED>(o, r, C(S::kScale));
       const int x0 = X0 + 4 * lane;
       const int lo = max(max(2, X0 + 2), x0), hi = min(min(g.nx - 2, X0 + 2 + R::OUT), x0 + 4);
       T* row = B + (long long)q * g.pitch + x0;
