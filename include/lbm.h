@@ -276,7 +276,7 @@ int32_t lbm_get_fused(const lbm_t* h);
  * the same device arithmetic as the single-step kernels and step n + 1 is
  * rounded to the storage type as a single step stores it, so the results are
  * bit-identical to the kernel pair, while the state crosses device memory
- * once per two steps.  lbm_step(n) runs n / 2 passes (graphs of 8 steps) and,
+ * once per two steps.  lbm_step(n) runs n / 2 passes (graphs of 16 steps) and,
  * for odd n, one step of the kernel pair.  enable != 0 turns it on (and the
  * staged and fused kernels off); lbm_set_launch, lbm_set_staged and
  * lbm_set_fused turn it off; lbm_autotune times it against the other forms.

@@ -1328,6 +1328,30 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
     cudaEventElapsedTime(&ms, e0, e1);
     return ms / reps;
   };
+  // small domains: steps as lbm_step replays them (captured graphs of
+  // kGraphSteps steps), since there the gaps between launches are part of
+  // what is being chosen (timed one by one, a form with fewer launches per
+  // step looks better than it runs)
+  const bool use_graph = cells <= (1LL << 22);
+  auto time_graph = [&]() -> float {
+    drop_graphs(h);
+    if (h->staged && ensure_staged(h) != LBM_OK) return 1e30f;
+    if (h->twostep && ensure_twostep(h) != LBM_OK) return 1e30f;
+    if (capture_graph(h, 0) != LBM_OK) return 1e30f;
+    const int n = std::max(1, reps / kGraphSteps);
+    cudaGraphLaunch(h->graph[0], h->stream);
+    cudaEventRecord(e0, h->stream);
+    for (int k = 0; k < n; ++k) cudaGraphLaunch(h->graph[0], h->stream);
+    cudaEventRecord(e1, h->stream);
+    float ms = 1e30f;
+    if (cudaEventSynchronize(e1) == cudaSuccess) {
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= (float)(n * kGraphSteps);
+    }
+    drop_graphs(h);
+    return ms;
+  };
+  auto time_form = [&]() -> float { return use_graph ? time_graph() : time_steps(); };
   h->staged = 0;
   for (int bx : kShapesBX)
     for (int r : kShapesRows)
@@ -1338,7 +1362,7 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
           h->rows = r;
           h->pf = pf;
           h->fused = fz;
-          const float ms = time_steps();
+          const float ms = time_form();
           if (ms < best) {
             best = ms;
             best_bx = bx;
@@ -1355,7 +1379,7 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
     h->staged = st;
     drop_graphs(h);
     if (ensure_staged(h) != LBM_OK) break;
-    const float ms = time_steps();
+    const float ms = time_form();
     if (ms < best) {
       best = ms;
       best_staged = st;
@@ -1368,15 +1392,19 @@ int lbm_autotune(lbm_t* h, int32_t* threads_x, int32_t* rows, int32_t* prefetch_
   if (twostep_ok(h)) {
     h->twostep = true;
     if (ensure_twostep(h) == LBM_OK) {
-      const int launches = std::max(2, reps / 2);
-      for (int k = 0; k < 2; ++k) enqueue_twostep(h, k & 1, h->stream);
-      cudaEventRecord(e0, h->stream);
-      for (int k = 0; k < launches; ++k) enqueue_twostep(h, k & 1, h->stream);
-      cudaEventRecord(e1, h->stream);
       float ms = 1e30f;
-      if (cudaEventSynchronize(e1) == cudaSuccess) {
-        cudaEventElapsedTime(&ms, e0, e1);
-        ms /= 2.0f * launches;
+      if (use_graph) {
+        ms = time_graph();
+      } else {
+        const int launches = std::max(2, reps / 2);
+        for (int k = 0; k < 2; ++k) enqueue_twostep(h, k & 1, h->stream);
+        cudaEventRecord(e0, h->stream);
+        for (int k = 0; k < launches; ++k) enqueue_twostep(h, k & 1, h->stream);
+        cudaEventRecord(e1, h->stream);
+        if (cudaEventSynchronize(e1) == cudaSuccess) {
+          cudaEventElapsedTime(&ms, e0, e1);
+          ms /= 2.0f * launches;
+        }
       }
       if (ms < best) {
         best = ms;

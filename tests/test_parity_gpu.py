@@ -12,7 +12,9 @@ depends only on nodes within distance k, and a window edge that is not a
 domain edge disturbs nodes at most k + 2 away from it (the boundary stencil
 reaches two nodes inwards), so nodes deeper than that are exact.
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -52,6 +54,16 @@ def max_err(a, b):
     return max(float(np.abs(x - y).max()) for x, y in zip(a, b))
 
 
+def record(case, storage, err):
+    """With LBM_RESULTS_DIR set, append the case's largest |error| in rho and u
+    to parity_errors.jsonl there (the error table of the precision report)."""
+    out = os.environ.get("LBM_RESULTS_DIR")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, "parity_errors.jsonl"), "a") as f:
+            f.write(json.dumps({"case": case, "storage": storage, "max_abs_err": err}) + "\n")
+
+
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 @pytest.mark.parametrize("steps", [250, 1000])
 def test_pulse_200(lbm, storage, steps):
@@ -62,6 +74,7 @@ def test_pulse_200(lbm, storage, steps):
     got = gpu_run(lbm, w, storage, steps)
     assert np.abs(ref[0] - 1).max() > 1e-7
     err = max_err(got, ref)
+    record(f"pulse-200, {steps} steps", storage, err)
     assert err <= TOL[storage], err
     # relative to the size of the disturbance, too
     assert err <= 1e-3 * np.abs(ref[0] - 1).max() or storage == "f64", err
@@ -77,6 +90,7 @@ def test_vortex_in_stream(lbm, storage, nsbc):
     ref = oracle_run(w, 300, **nsbc)
     got = gpu_run(lbm, w, storage, 300, **nsbc)
     err = max_err(got, ref)
+    record(f"BGK vortex in a Ma 0.1 stream, 160x120, 300 steps, {nsbc}", storage, err)
     assert err <= TOL[storage], err
 
 
@@ -310,6 +324,7 @@ def test_mrt_vortex_in_stream(lbm, storage, rates):
     ref = oracle_run(w, 300, beta=0.05, collision="mrt", mrt_rates=_oracle_mrt_rates(rates, w.tau))
     got = gpu_run(lbm, w, storage, 300, beta=0.05, collision="mrt", mrt_rates=rates)
     err = max_err(got, ref)
+    record(f"MRT {rates} vortex in a Ma 0.1 stream, 160x120, 300 steps", storage, err)
     assert err <= TOL[storage], err
 
 
@@ -324,6 +339,7 @@ def test_vortex_400_mrt_4000_steps(lbm):
     assert all(np.isfinite(a).all() for a in ref)
     got = gpu_run(lbm, w, "f32", 4000, collision="mrt", mrt_rates=rates)
     err = max_err(got, ref)
+    record("vortex-400, MRT, 4000 steps", "f32", err)
     assert err <= TOL["f32"], err
 
 
@@ -382,6 +398,7 @@ def test_paper_vortex_setup_f32(lbm):
                      mrt_rates=_oracle_mrt_rates(PAPER_VORTEX_RATES, tau))
     got = gpu_run(lbm, w, "f32", 1200, edges=[("velocity", u0, 0.0), "nsbc", "periodic", "periodic"],
                   collision="mrt", mrt_rates=PAPER_VORTEX_RATES)
+    record("Sec. 7 vortex set-up, 128^2, 1200 steps", "f32", max_err(got, ref))
     assert max_err(got, ref) <= TOL["f32"]
 
 
