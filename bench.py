@@ -155,11 +155,11 @@ def step_kernel(sim, nx, ny):
     timed launch reads and writes once) of the kernel that carries the step:
     the staged kernel updates every node, the bulk kernel the interior (the
     NSBC kernel the perimeter, beside it); a two-step pass moves every node's
-    state once for two steps (its events bracket its three launches)."""
+    state once for two steps (one launch)."""
     if sim.twostep:
-        return ("two-step pass: roll_kernel (steps n+1 and n+2 on nodes 2..n-3, warps rolling down 128-column "
-                "strips, step n+1 kept in registers) between two frame_kernel launches (step n+1 on the "
-                "width-3 frame into a frame buffer, step n+2 on the width-2 frame)", "twostep_traffic", nx * ny)
+        return ("two-step pass: pass_kernel, one launch per two steps (step n+1 on the width-3 frame into a "
+                "frame buffer, steps n+1 and n+2 on nodes 2..n-3 by warps rolling down 128-column strips with "
+                "step n+1 in registers, step n+2 on the width-2 frame)", "twostep_traffic", nx * ny)
     if sim.staged:
         return ("batch_ws_kernel (staged step: interior tiles by bulk copies + NSBC chunks, "
                 f"{sim.staged} stages)", "staged_step_traffic", nx * ny)
@@ -462,7 +462,7 @@ def run_ours(args, rank, world, local_rank):
                          "avg_launch_ms": bulk_avg, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                          "nsbc_avg_launch_ms": nsbc_avg if nn else None,
                          "timing": f"per-launch CUDA events over {kprof} steps after the timed region"},
-            "gpu_launches": (3 * (args.steps // 2) + 2 * (args.steps % 2) if sim.twostep else
+            "gpu_launches": (args.steps // 2 + 2 * (args.steps % 2) if sim.twostep else
                              (1 if sim.staged or sim.fused else 2) * args.steps),
             "clocks": clk,
         }

@@ -267,24 +267,26 @@ int32_t lbm_get_staged(const lbm_t* h);
  * NULL handle. */
 int lbm_set_fused(lbm_t* h, int32_t enable);
 int32_t lbm_get_fused(const lbm_t* h);
-/* Two steps per pass (temporal blocking), in three launches: step n + 1 on
- * the frame of nodes within distance 2 of an edge (the NSBC and the interior
- * collision) into a small frame buffer; steps n + 1 and n + 2 on the nodes at
- * distance 2 or more by a kernel whose warps each roll down a strip of 128
- * columns, staging the state rows by bulk copies and keeping step n + 1 in
- * registers; step n + 2 on the frame from the frame buffer.  Every node runs
- * the same device arithmetic as the single-step kernels and step n + 1 is
- * rounded to the storage type as a single step stores it, so the results are
- * bit-identical to the kernel pair, while the state crosses device memory
- * once per two steps.  lbm_step(n) runs n / 2 passes (graphs of 16 steps) and,
- * for odd n, one step of the kernel pair.  enable != 0 turns it on (and the
- * staged and fused kernels off); lbm_set_launch, lbm_set_staged and
- * lbm_set_fused turn it off; lbm_autotune times it against the other forms.
- * LBM_EINVAL when enabling it on an f64 handle, a handle with a periodic axis
- * or fewer than 8 x 8 nodes.  A bounded wait for the bulk copies that gives
- * up makes lbm_status report LBM_ETIMEOUT.  Device memory: a frame buffer of
- * 9 x (6 (nx + ny) - 36) populations, allocated when first enabled.
- * lbm_get_twostep: 1 if on, 0 if off, LBM_EINVAL for NULL. */
+/* Two steps per pass (temporal blocking), in one launch whose warps take, in
+ * turn, three kinds of work: step n + 1 on the frame of nodes within
+ * distance 2 of an edge (the NSBC and the interior collision) into a small
+ * frame buffer; steps n + 1 and n + 2 on the nodes at distance 2 or more,
+ * each warp rolling down a strip of 128 columns, staging the state rows by
+ * bulk copies and keeping step n + 1 in registers; and, once all of the first
+ * kind is done (a bounded wait on a counter), step n + 2 on the frame from
+ * the frame buffer.  Every node runs the same device arithmetic as the
+ * single-step kernels and step n + 1 is rounded to the storage type as a
+ * single step stores it, so the results are bit-identical to the kernel
+ * pair, while the state crosses device memory once per two steps.
+ * lbm_step(n) runs n / 2 passes (graphs of 16 steps) and, for odd n, one
+ * step of the kernel pair.  enable != 0 turns it on (and the staged and fused
+ * kernels off); lbm_set_launch, lbm_set_staged and lbm_set_fused turn it off;
+ * lbm_autotune times it against the other forms.  LBM_EINVAL when enabling
+ * it on an f64 handle, a handle with a periodic axis or fewer than 8 x 8
+ * nodes.  A bounded wait that gives up makes lbm_status report LBM_ETIMEOUT.
+ * Device memory: a frame buffer of 9 x (6 (nx + ny) - 36) populations,
+ * allocated when first enabled.  lbm_get_twostep: 1 if on, 0 if off,
+ * LBM_EINVAL for NULL. */
 int lbm_set_twostep(lbm_t* h, int32_t enable);
 int32_t lbm_get_twostep(const lbm_t* h);
 /* LBM_ETIMEOUT if a bounded wait of the staged kernel gave up (the state is
@@ -432,10 +434,11 @@ int lbm_batch_unstable_nodes(lbm_batch_t* b, int32_t k, int64_t* count);
 int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_t blocks, int32_t prefetch_rows,
                          int32_t split, int32_t tma_tile);
 /* Two steps per pass for every instance (the pass lbm_set_twostep describes,
- * in three launches over all instances: rolling items in bands of at most
- * 128 output rows, claimed by warps from a counter, largest instance first,
- * and frame items of 128 threads; each instance's frame buffer after the
- * last).  Bit-identical to two batched steps.  lbm_batch_step(n) runs n / 2
+ * here in three launches over all instances: step n + 1 on every frame, the
+ * rolling items in bands of at most 128 output rows, claimed by warps from a
+ * counter, largest instance first, beside the frame launches on a side
+ * stream, then step n + 2 on every frame; each instance's frame buffer after
+ * the last).  Bit-identical to two batched steps.  lbm_batch_step(n) runs n / 2
  * passes (graphs of 16 steps) and, for odd n, one batched step of the launch
  * shape set.  enable != 0 turns it on; lbm_batch_set_launch turns it off;
  * lbm_batch_autotune times it against the other forms.  LBM_EINVAL when

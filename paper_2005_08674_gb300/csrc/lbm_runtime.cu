@@ -346,11 +346,11 @@ void launch_staged(const lbm_t* h, const void* a, void* b, cudaStream_t s) {
   });
 }
 
-// Two-step pass: the rolling kernel's items are strips of Roll::OUT output
-// columns times bands of ts_band rows, taken by a persistent grid of as many
-// blocks as fit on the device at once; each wave of items is all strips of
-// ts_wave_bands bands, and four waves give every resident warp about four
-// items.
+// Two-step pass: the rolling items are strips of Roll::OUT output columns
+// times bands of ts_band rows, taken with the frame chunks by a persistent
+// grid of as many blocks as fit on the device at once; each wave of items is
+// all strips of ts_wave_bands bands, and four waves give every resident warp
+// about four items.
 template <typename T>
 void twostep_grid(lbm_t* h, int per_sm) {
   using R = lbmk::Roll<T>;
@@ -363,8 +363,7 @@ void twostep_grid(lbm_t* h, int per_sm) {
   h->ts_bands = (interior_y + h->ts_band - 1) / h->ts_band;
   h->ts_wave_bands = std::min(per_wave, h->ts_bands);
   h->ts_waves = (h->ts_bands + h->ts_wave_bands - 1) / h->ts_wave_bands;
-  const long long items = (long long)h->ts_waves * h->ts_wave_bands * h->ts_strips;
-  h->ts_grid = (int)std::max(1LL, std::min((items + R::WARPS - 1) / R::WARPS, (long long)per_sm * h->sms));
+  h->ts_grid = std::max(1, per_sm * h->sms);  // frame chunks as well as rolling items: every resident warp
 }
 
 template <typename T, int MODEL, bool SHIFT>
@@ -372,30 +371,13 @@ void launch_twostep_k(const lbm_t* h, const T* A, T* B, cudaStream_t s) {
   using C = typename lbmk::Store<T>::C;
   const lbmk::Geom g{h->nx, h->ny, h->pitch, h->plane};
   const lbmk::Rates<C> r = rates<C>(h);
-  T* F = static_cast<T*>(h->d_frame);
-  auto frame_blocks = [&](int width) { return (lbmk::frame_threads(h->nx, h->ny, width) + 127) / 128; };
-  // the frame launches on the side stream, beside the rolling kernel (they
-  // read A or F and write F or B's nodes at distance 0 and 1, the rolling
-  // kernel reads A and writes B's nodes at distance 2 or more)
-  cudaStream_t fs = h->side ? h->side : s;
-  if (fs != s) {
-    cudaEventRecord(h->ev_fork, s);
-    cudaStreamWaitEvent(fs, h->ev_fork, 0);
-  }
-  // step n + 1 on the frame of width 3, A -> F
-  lbmk::frame_kernel<T, MODEL, SHIFT><<<frame_blocks(lbmk::kFrameWidth), 128, 0, fs>>>(
-      lbmk::GlobalRawSrc<T>{A, h->plane, h->pitch}, lbmk::FrameDst<T>{F, h->nx, h->ny, h->frame_fn}, g, h->nsbc, r,
-      lbmk::kFrameWidth);
-  // steps n + 1 and n + 2 on the interior, A -> B
-  lbmk::roll_kernel<T, MODEL, SHIFT><<<h->ts_grid, lbmk::kRollThreads, lbmk::Roll<T>::kSmem, s>>>(
-      A, B, g, r, h->ts_strips, h->ts_band, h->ts_bands, h->ts_wave_bands, h->ts_waves, h->d_sched);
-  // step n + 2 on the frame of width 2, F -> B
-  lbmk::frame_kernel<T, MODEL, SHIFT><<<frame_blocks(2), 128, 0, fs>>>(
-      lbmk::FrameSrc<T>{F, h->nx, h->ny, h->frame_fn}, lbmk::GlobalRawDst<T>{B, h->plane, h->pitch}, g, h->nsbc, r, 2);
-  if (fs != s) {
-    cudaEventRecord(h->ev_join, fs);
-    cudaStreamWaitEvent(s, h->ev_join, 0);
-  }
+  // one launch: the frame chunks of step n + 1, the rolling items, the frame
+  // chunks of step n + 2 (32 frame threads per chunk)
+  const int n_f1 = (lbmk::frame_threads(h->nx, h->ny, lbmk::kFrameWidth) + 31) / 32;
+  const int n_f3 = (lbmk::frame_threads(h->nx, h->ny, 2) + 31) / 32;
+  lbmk::pass_kernel<T, MODEL, SHIFT><<<h->ts_grid, lbmk::kRollThreads, lbmk::Roll<T>::kSmem, s>>>(
+      A, B, static_cast<T*>(h->d_frame), g, h->nsbc, r, h->ts_strips, h->ts_band, h->ts_bands, h->ts_wave_bands,
+      h->ts_waves, n_f1, n_f3, h->d_sched);
 }
 
 template <typename T>
@@ -429,12 +411,12 @@ int twostep_prepare(lbm_t* h) {
   const int smem = (int)lbmk::Roll<T>::kSmem;
   cudaError_t e = cudaSuccess;
   int per_sm = 0, sms = 0;
-  for (const void* k : {(const void*)lbmk::roll_kernel<T, 0, false>, (const void*)lbmk::roll_kernel<T, 0, true>,
-                        (const void*)lbmk::roll_kernel<T, 1, false>, (const void*)lbmk::roll_kernel<T, 1, true>})
+  for (const void* k : {(const void*)lbmk::pass_kernel<T, 0, false>, (const void*)lbmk::pass_kernel<T, 0, true>,
+                        (const void*)lbmk::pass_kernel<T, 1, false>, (const void*)lbmk::pass_kernel<T, 1, true>})
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbmk::roll_kernel<T, 1, true>, lbmk::kRollThreads,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, lbmk::pass_kernel<T, 1, true>, lbmk::kRollThreads,
                                                       smem);
   if (e != cudaSuccess)
     return fail(LBM_ECUDA, "two-step kernel: %d bytes of shared memory refused: %s", smem, cudaGetErrorString(e));

@@ -1,26 +1,31 @@
 // lbm_twostep.cuh -- two time steps per pass over one domain (temporal
-// blocking), in three launches that together give the bits of two single
-// steps:
+// blocking), in one launch whose warps claim three kinds of work from a
+// counter, in this order, and together give the bits of two single steps:
 //
-//   frame_kernel (width 3, A -> F): step n + 1 on the frame of nodes whose
+//   first-frame chunks (A -> F): step n + 1 on the frame of nodes whose
 //       distance to the nearest edge is below 3 -- the NSBC (Sec. 5) on the
 //       perimeter, the interior collision on rings 1 and 2 -- into a compact
 //       frame buffer F (a few MB);
-//   roll_kernel (A -> B): step n + 2 on the nodes at distance 2 or more.
-//       Each warp owns a strip of 32 x 4 columns and rolls down a band of
-//       rows: it stages the state rows by bulk copies in a private ring of
-//       three or four rows in shared memory, computes step n + 1 of each row (the
-//       interior collision only: every node it needs there is at distance 1
-//       or more) and keeps the populations that step n + 2 pulls from it in
-//       registers, rounded to the storage type as a single step stores them.
-//       The intermediate step never reaches device memory, and the warps
-//       never wait for one another;
-//   frame_kernel (width 2, F -> B): step n + 2 on the nodes at distance 0
-//       and 1, from the frame buffer.
+//   rolling items (A -> B): steps n + 1 and n + 2 on the nodes at distance
+//       2 or more.  The warp owns a strip of 32 x 4 columns and rolls down a
+//       band of rows: it stages the state rows by bulk copies in a private
+//       ring of three or four rows in shared memory, computes step n + 1 of
+//       each row (the interior collision only: every node it needs there is
+//       at distance 1 or more) and keeps the populations that step n + 2
+//       pulls from it in registers, rounded to the storage type as a single
+//       step stores them.  The intermediate step never reaches device memory;
+//   second-frame chunks (F -> B): step n + 2 on the nodes at distance 0 and
+//       1, from the frame buffer, each after a bounded wait until every
+//       first-frame chunk is done.
 //
 // Device-memory traffic per two steps: one read and one write of the state
 // (the strips' overlapping columns and the bands' four overlapping rows are
 // read again, mostly from L2) plus the frame buffer.
+//
+// The batched form (many instances) runs the same three kinds of work as
+// three launches instead -- the frames' thousands of NSBC quads are latency-
+// bound and want more resident warps than the rolling kernel leaves; in one
+// launch the 256-instance batch ran 20 % slower.
 #pragma once
 
 #include "lbm_kernels.cuh"
@@ -61,7 +66,9 @@ struct FrameSrc {
   const T* __restrict__ f;
   int nx, ny, fn;
   __device__ __forceinline__ typename Store<T>::C raw(int i, int x, int y) const {
-    return Store<T>::ld1s(f + (long long)i * fn + frame_index(x, y, nx, ny));
+    // through L2: other warps of the same launch wrote it
+    const T v = __ldcg(f + (long long)i * fn + frame_index(x, y, nx, ny));
+    return Store<T>::ld1s(&v);
   }
   __device__ __forceinline__ typename Store<T>::C ld(int i, int x, int y) const {
     using S = Store<T>;
@@ -149,12 +156,6 @@ __device__ __forceinline__ void frame_node(const Src& src, const Dst& dst, const
 // rings 1 .. width - 1.
 __host__ __device__ inline int frame_threads(int nx, int ny, int width) {
   return 3 * ring_offset(nx, ny, 1) + ring_offset(nx, ny, width);
-}
-
-template <typename T, int MODEL, bool SHIFT, typename Src, typename Dst>
-__global__ void __launch_bounds__(128) frame_kernel(Src src, Dst dst, Geom g, Nsbc p, Rates<typename Store<T>::C> r,
-                                                    int width) {
-  frame_node<T, MODEL, SHIFT>(src, dst, g, p, r, width, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -337,20 +338,59 @@ __device__ __forceinline__ bool roll_item(const T* __restrict__ A, T* __restrict
   return true;
 }
 
-// Two steps, A (step n) -> B (step n + 2), on nodes [2, nx - 2) x [2, ny - 2).
-// Work item = (strip, band): strip j reads columns X0 = j OUT .. X0 + W and
-// stores X0 + 2 .. X0 + 2 + OUT; band b stores rows 2 + b band .. + band.
-// Every warp takes items gw, gw + total warps, ... in an order that keeps
-// the reads of shared lines close in time, so that the second read comes
-// from L2: all strips of a band side by side (neighbouring strips share the
-// cache lines at their ends), and the bands in waves -- wave k holds bands
-// k, k + n_waves, k + 2 n_waves, ... -- so that band b + 1 restarts its roll
-// (four rows staged again) on rows band b read just before.  A wait that
-// gives up sets err[2] and the warp returns.
+// Bounded wait until the counter *c reaches `want` (acquire: what the
+// producers wrote before their release increments is visible after it);
+// false once `budget` SM clock cycles have passed.
+__device__ __forceinline__ bool wait_count(const int* c, int want, long long budget = kTmaWaitCycles) {
+  const long long t0 = clock64();
+  do {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+    if (v >= want) return true;
+    __nanosleep(100);
+  } while (clock64() - t0 < budget);
+  return false;
+}
+
+// Frame work of one warp: 32 consecutive frame threads of frame_node (a
+// multiple of 32 from the first, so quads stay whole).  FIRST: step n + 1 on
+// the width-3 frame into F, then a release increment of *done; else step
+// n + 2 on the width-2 frame from F.
+template <typename T, int MODEL, bool SHIFT, bool FIRST>
+__device__ __forceinline__ void frame_chunk(const T* __restrict__ A, T* __restrict__ B, T* __restrict__ F,
+                                            const Geom& g, const Nsbc& p, const Rates<typename Store<T>::C>& r,
+                                            int t0, int lane, int* done) {
+  const int fn = ring_offset(g.nx, g.ny, kFrameWidth);
+  if constexpr (FIRST) {
+    frame_node<T, MODEL, SHIFT>(GlobalRawSrc<T>{A, g.plane, g.pitch}, FrameDst<T>{F, g.nx, g.ny, fn}, g, p, r,
+                                kFrameWidth, t0 + lane);
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicAdd(done, 1);
+  } else {
+    frame_node<T, MODEL, SHIFT>(FrameSrc<T>{F, g.nx, g.ny, fn}, GlobalRawDst<T>{B, g.plane, g.pitch}, g, p, r, 2,
+                                t0 + lane);
+  }
+}
+
+// The whole pass in one launch, A (step n) -> B (step n + 2), F the frame
+// buffer.  Warps claim work from a counter (sched[0]) in this order: n_f1
+// chunks of step n + 1 on the width-3 frame; the rolling items; n_f3 chunks
+// of step n + 2 on the width-2 frame, each of which first waits (bounded)
+// until all n_f1 first chunks are done (sched[3]).  Every claimed first chunk
+// belongs to a running warp that waits on nothing, so the wait always ends.
+// Rolling item j = (strip, band): strip X0 = strip OUT reads columns X0 ..
+// X0 + W and stores X0 + 2 .. X0 + 2 + OUT; band b stores rows 2 + b band ..
+// + band; items come as all strips of a band side by side, the bands in
+// waves (wave k: bands k, k + n_waves, ...), so that the lines neighbouring
+// strips share and the rows a band restarts on are read from L2.  The last
+// warp out resets the counters.  A wait that gives up sets sched[2] and the
+// warp returns.
 template <typename T, int MODEL, bool SHIFT>
 __global__ void __launch_bounds__(kRollThreads, 4)
-    roll_kernel(const T* __restrict__ A, T* __restrict__ B, Geom g, Rates<typename Store<T>::C> r, int n_strips,
-                int band, int n_bands, int bands_per_wave, int n_waves, int* __restrict__ err) {
+    pass_kernel(const T* __restrict__ A, T* __restrict__ B, T* __restrict__ F, Geom g, Nsbc p,
+                Rates<typename Store<T>::C> r, int n_strips, int band, int n_bands, int bands_per_wave, int n_waves,
+                int n_f1, int n_f3, int* __restrict__ sched) {
   using R = Roll<T>;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[R::WARPS][R::DEPTH];
@@ -364,16 +404,42 @@ __global__ void __launch_bounds__(kRollThreads, 4)
   }
   __syncwarp();
   uint32_t phase = 0u;  // bit j: parity of the next completion of bar[j]
-  const int per_wave = bands_per_wave * n_strips, n_items = n_waves * per_wave;
-  const int nw = gridDim.x * R::WARPS;
-  for (int item = blockIdx.x * R::WARPS + warp; item < n_items; item += nw) {
-    const int wave = item / per_wave, rem = item - wave * per_wave;
-    const int m = rem / n_strips, strip = rem - m * n_strips;
-    const int b = m * n_waves + wave;
-    if (b >= n_bands) continue;
-    const int X0 = strip * R::OUT;
-    const int Ya = 2 + b * band, Yb = min(Ya + band, g.ny - 2);
-    if (!roll_item<T, MODEL, SHIFT>(A, B, g, r, X0, Ya, Yb, ring, bar, phase, lane, err)) return;
+  const int per_wave = bands_per_wave * n_strips, n_roll = n_waves * per_wave;
+  const int n_items = n_f1 + n_roll + n_f3;
+  for (;;) {
+    int c = 0;
+    if (lane == 0) c = atomicAdd(&sched[0], 1);
+    c = __shfl_sync(0xffffffffu, c, 0);
+    if (c >= n_items) break;
+    if (c < n_f1) {
+      frame_chunk<T, MODEL, SHIFT, true>(A, B, F, g, p, r, c * 32, lane, &sched[3]);
+    } else if (c < n_f1 + n_roll) {
+      const int item = c - n_f1;
+      const int wave = item / per_wave, rem = item - wave * per_wave;
+      const int m = rem / n_strips, strip = rem - m * n_strips;
+      const int b = m * n_waves + wave;
+      if (b >= n_bands) continue;
+      const int Ya = 2 + b * band, Yb = min(Ya + band, g.ny - 2);
+      if (!roll_item<T, MODEL, SHIFT>(A, B, g, r, strip * R::OUT, Ya, Yb, ring, bar, phase, lane, sched)) return;
+    } else {
+      bool ok = true;
+      if (lane == 0) ok = wait_count(&sched[3], n_f1);
+      if (!__shfl_sync(0xffffffffu, ok, 0)) {
+        if (lane == 0) atomicExch(&sched[2], 1);
+        return;
+      }
+      __syncwarp();
+      frame_chunk<T, MODEL, SHIFT, false>(A, B, F, g, p, r, (c - n_f1 - n_roll) * 32, lane, nullptr);
+    }
+  }
+  if (lane == 0) {
+    __threadfence();
+    if (atomicAdd(&sched[1], 1) == (int)gridDim.x * R::WARPS - 1) {
+      sched[0] = 0;
+      sched[3] = 0;
+      __threadfence();
+      sched[1] = 0;
+    }
   }
 }
 
