@@ -349,8 +349,13 @@ void launch_staged(const lbm_t* h, const void* a, void* b, cudaStream_t s) {
 // Two-step pass: the rolling items are strips of Roll::OUT output columns
 // times bands of ts_band rows, taken with the frame chunks by a persistent
 // grid of as many blocks as fit on the device at once; each wave of items is
-// all strips of ts_wave_bands bands, and four waves give every resident warp
-// about four items.
+// all strips of ts_wave_bands bands.  Bands of 16 rows (a restart costs four
+// staged and two computed rows) unless the domain gives every resident warp
+// more than 16 (f32) or 8 (16-bit) items: measured on pulse-2048 / 4096 /
+// 8192, f32 bands of 16 gave 128k / 147k / 162k MLUPS against 58-100k /
+// 111-147k / 157-160k for bands of 24-48, and 16-bit storage, bound by
+// instruction issue, gains from the longer bands at 8192^2 (29 rows: 207k
+// against 198k for 16).
 template <typename T>
 void twostep_grid(lbm_t* h, int per_sm) {
   using R = lbmk::Roll<T>;
@@ -358,8 +363,9 @@ void twostep_grid(lbm_t* h, int per_sm) {
   h->ts_strips = (interior_x + R::OUT - 1) / R::OUT;
   const int warps = std::max(1, per_sm * h->sms * R::WARPS);
   const int per_wave = std::max(1, warps / h->ts_strips);  // bands side by side
-  const int want = std::max(1, std::min(4 * per_wave, interior_y));
-  h->ts_band = (interior_y + want - 1) / want;
+  const int items_per_warp = sizeof(T) == 4 ? 16 : 8;
+  const int want = std::max(1, std::min(items_per_warp * per_wave, interior_y));
+  h->ts_band = std::max(std::min(16, interior_y), (interior_y + want - 1) / want);
   h->ts_bands = (interior_y + h->ts_band - 1) / h->ts_band;
   h->ts_wave_bands = std::min(per_wave, h->ts_bands);
   h->ts_waves = (h->ts_bands + h->ts_wave_bands - 1) / h->ts_wave_bands;
