@@ -435,7 +435,7 @@ int lbm_batch_set_launch(lbm_batch_t* b, int32_t threads_x, int32_t rows, int32_
                          int32_t split, int32_t tma_tile);
 /* Two steps per pass for every instance (the pass lbm_set_twostep describes,
  * here in three launches over all instances: step n + 1 on every frame, the
- * rolling items in bands of at most 128 output rows, claimed by warps from a
+ * rolling items in bands of at most 64 output rows, claimed by warps from a
  * counter, largest instance first, beside the frame launches on a side
  * stream, then step n + 2 on every frame; each instance's frame buffer after
  * the last).  Bit-identical to two batched steps.  lbm_batch_step(n) runs n / 2

@@ -614,7 +614,7 @@ bool batch_twostep_ok(const lbm_batch_t* b) {
 }
 
 // Work lists of the two-step pass, largest instance first: rolling items in
-// bands of at most 128 output rows, all strips of a band side by side;
+// bands of at most 64 output rows, all strips of a band side by side;
 // frame items of 128 threads; each instance's frame buffer after the last.
 int build_twostep(lbm_batch_t* b) {
   if (!b->ts_dirty) return LBM_OK;
@@ -629,7 +629,10 @@ int build_twostep(lbm_batch_t* b) {
   for (int k : order) {
     const InstDev& d = b->inst[k];
     const int strips = (d.nx - 4 + out - 1) / out, iy = d.ny - 4;
-    const int nb = (iy + 127) / 128, band = (iy + nb - 1) / nb;
+    // bands of at most 64 rows: more, smaller items balance the warps better
+    // (measured on the 256-instance batch, band caps 128 / 64 / 32 / 16:
+    // f32 115k / 123k / 124k / 122k MLUPS, f16 144k / 149k / 149k / 144k)
+    const int nb = (iy + 63) / 64, band = (iy + nb - 1) / nb;
     for (int y = 2; y < d.ny - 2; y += band)
       for (int j = 0; j < strips; ++j) roll.push_back(make_int4(k, j * out, y, std::min(y + band, d.ny - 2)));
     if (foff > INT32_MAX - 9LL * lbmk::ring_offset(d.nx, d.ny, lbmk::kFrameWidth))
