@@ -469,12 +469,14 @@ int lbm_batch_status(lbm_batch_t* b);
  * arrays or a negative node count. */
 int lbm_partition_instances(int32_t count, const int64_t* cells, int32_t ranks, int32_t* rank_of);
 
-/* Failure-detection check of the bounded device-side wait used by the
- * shared-memory path: one block waits on an mbarrier that nothing arrives
- * on, gives up after budget_cycles SM clock cycles (at most 4e9), and
- * returns normally.  Returns LBM_ETIMEOUT when the wait gave up (the
- * expected outcome), LBM_OK if it did not, LBM_ECUDA on a CUDA error.
- * Allocates and frees one int of device memory; synchronises. */
+/* Failure-detection check of the bounded device-side waits: one block waits
+ * on an mbarrier that nothing arrives on (the waits of the shared-memory
+ * paths), then on a device counter that nothing increments (the two-step
+ * pass's wait for its first-frame chunks); each gives up after budget_cycles
+ * SM clock cycles (at most 4e9), and the kernel returns normally.  Returns
+ * LBM_ETIMEOUT when both waits gave up (the expected outcome), LBM_OK if
+ * either did not, LBM_ECUDA on a CUDA error.  Allocates and frees two ints of
+ * device memory; synchronises. */
 int lbm_wait_selftest(int64_t budget_cycles);
 
 /* Per-launch timing.  While enabled, lbm_step launches every step directly

@@ -233,16 +233,22 @@ __global__ void __launch_bounds__(BX) batch_step_kernel(const T* __restrict__ A,
 // next tile is in flight while the current one is collided, so the bytes in
 // flight are bounded by shared memory, not by registers.
 // ---------------------------------------------------------------------------
-// A wait on a barrier nothing ever arrives on: it must give up after its
-// budget and report it through *flag (the kernel then returns normally).
-__global__ void wait_selftest_kernel(long long budget, int* flag) {
+// A wait on a barrier nothing ever arrives on, then a wait on a counter
+// nothing ever increments (the two-step pass's wait for its first-frame
+// chunks): each must give up after its budget; *flag = 1 if both did (the
+// kernel then returns normally), 2 otherwise.
+__global__ void wait_selftest_kernel(long long budget, int* flag, const int* counter) {
   __shared__ __align__(8) uint64_t bar;
   if (threadIdx.x == 0) {
     mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (threadIdx.x == 0) *flag = mbar_wait(&bar, 0u, budget) ? 2 : 1;
+  if (threadIdx.x == 0) {
+    const bool a = mbar_wait(&bar, 0u, budget);
+    const bool b = lbmk::wait_count(counter, 1, budget);
+    *flag = (!a && !b) ? 1 : 2;
+  }
 }
 
 // The whole step of every instance in ONE persistent launch: blocks take
@@ -1329,12 +1335,12 @@ int lbm_partition_instances(int32_t count, const int64_t* cells, int32_t ranks, 
 int lbm_wait_selftest(int64_t budget_cycles) {
   if (budget_cycles <= 0 || budget_cycles > 4000000000LL)
     return bfail(LBM_EINVAL, "lbm_wait_selftest: budget %lld outside (0, 4e9] cycles", (long long)budget_cycles);
-  int* d = nullptr;
-  BATCH_CUDA(cudaMalloc(&d, sizeof(int)));
-  cudaError_t e = cudaMemset(d, 0, sizeof(int));
+  int* d = nullptr;  // [0] the flag, [1] a counter that stays 0
+  BATCH_CUDA(cudaMalloc(&d, 2 * sizeof(int)));
+  cudaError_t e = cudaMemset(d, 0, 2 * sizeof(int));
   int h = 0;
   if (e == cudaSuccess) {
-    wait_selftest_kernel<<<1, 32>>>(budget_cycles, d);
+    wait_selftest_kernel<<<1, 32>>>(budget_cycles, d, d + 1);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof h, cudaMemcpyDeviceToHost);
