@@ -530,7 +530,7 @@ int ensure_twostep(lbm_t* h) {
   return rc;
 }
 
-// Two steps from buffer `from` to 1 - from (three launches).
+// Two steps from buffer `from` to 1 - from (one launch of the pass kernel).
 void enqueue_twostep(const lbm_t* h, int from, cudaStream_t s) {
   dispatch(h->storage, [&](auto tag) {
     using T = decltype(tag);
@@ -625,8 +625,8 @@ int enqueue_step_profiled(lbm_t* h, int from) {
   return LBM_OK;
 }
 
-// A two-step pass with an event pair around its three launches (counted as
-// one bulk launch; it carries two steps).
+// A two-step pass with an event pair around its launch (counted as one bulk
+// launch; it carries two steps).
 int enqueue_twostep_profiled(lbm_t* h, int from) {
   cudaEvent_t e[2];
   int rc = profiled_pair(h, 0, e);

@@ -534,7 +534,7 @@ class Simulation:
         return lbm_get_fused(self.h) == 1
 
     def set_twostep(self, enable=True):
-        """Two steps per launch, the step in between kept in shared memory."""
+        """Two steps per launch, the step in between kept on chip (see lbm_set_twostep)."""
         lbm_set_twostep(self.h, enable)
         return self
 

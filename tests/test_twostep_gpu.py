@@ -1,5 +1,5 @@
-"""Two-step kernel (two time steps per launch, the step in between kept in
-shared memory): it runs the same device arithmetic as the single-step
+"""Two-step pass (two time steps per launch, the step in between kept on
+chip except on the frame): it runs the same device arithmetic as the single-step
 kernels and rounds the intermediate step to the storage type as a single step
 stores it, so every run must be bit-identical to the kernel pair's -- over
 ragged sizes (one strip and many, bands of rows, narrow last strips), every
