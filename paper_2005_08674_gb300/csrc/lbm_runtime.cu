@@ -355,7 +355,8 @@ void launch_staged(const lbm_t* h, const void* a, void* b, cudaStream_t s) {
 // 8192, f32 bands of 16 gave 128k / 147k / 162k MLUPS against 58-100k /
 // 111-147k / 157-160k for bands of 24-48, and 16-bit storage, bound by
 // instruction issue, gains from the longer bands at 8192^2 (29 rows: 207k
-// against 198k for 16).
+// against 198k for 16).  Items that would fill one wave of warps and a bit
+// of a second are cut to one wave instead (f32 at 2048^2: 102k -> 128k).
 template <typename T>
 void twostep_grid(lbm_t* h, int per_sm) {
   using R = lbmk::Roll<T>;
@@ -366,6 +367,9 @@ void twostep_grid(lbm_t* h, int per_sm) {
   const int items_per_warp = sizeof(T) == 4 ? 16 : 8;
   const int want = std::max(1, std::min(items_per_warp * per_wave, interior_y));
   h->ts_band = std::max(std::min(16, interior_y), (interior_y + want - 1) / want);
+  const long long items = (long long)h->ts_strips * ((interior_y + h->ts_band - 1) / h->ts_band);
+  if (items > warps && items < 2LL * warps && per_wave * h->ts_strips <= warps)
+    h->ts_band = std::max(h->ts_band, (interior_y + per_wave - 1) / per_wave);
   h->ts_bands = (interior_y + h->ts_band - 1) / h->ts_band;
   h->ts_wave_bands = std::min(per_wave, h->ts_bands);
   h->ts_waves = (h->ts_bands + h->ts_wave_bands - 1) / h->ts_wave_bands;

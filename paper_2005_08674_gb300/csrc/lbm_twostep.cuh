@@ -168,10 +168,10 @@ struct Roll {
   // the strip, step n + 2 on 2 .. W - 3; strips start OUT apart, a multiple
   // of 16 bytes for the copies
   static constexpr int OUT = sizeof(T) == 4 ? W - 4 : W - 8;
-  // ring rows: three read while the next DEPTH - 3 are in flight (f32: the
-  // three alone -- the next row is staged as soon as the oldest is read --
-  // so that four blocks fit in shared memory)
-  static constexpr int DEPTH = sizeof(T) == 4 ? 3 : 4;
+  // ring rows: three read while the fourth is in flight (f32 then fits
+  // three blocks per SM, 16-bit storage four)
+  static constexpr int DEPTH = 4;
+  static constexpr int BLOCKS = sizeof(T) == 4 ? 3 : 4;  // resident blocks per SM
   static constexpr int ROWE = 9 * W;
   static constexpr int WARPS = 4;  // independent warps per block
   // paired FP32 collisions for 16-bit storage, whose kernel is bound by
@@ -387,7 +387,7 @@ __device__ __forceinline__ void frame_chunk(const T* __restrict__ A, T* __restri
 // warp out resets the counters.  A wait that gives up sets sched[2] and the
 // warp returns.
 template <typename T, int MODEL, bool SHIFT>
-__global__ void __launch_bounds__(kRollThreads, 4)
+__global__ void __launch_bounds__(kRollThreads, Roll<T>::BLOCKS)
     pass_kernel(const T* __restrict__ A, T* __restrict__ B, T* __restrict__ F, Geom g, Nsbc p,
                 Rates<typename Store<T>::C> r, int n_strips, int band, int n_bands, int bands_per_wave, int n_waves,
                 int n_f1, int n_f3, int* __restrict__ sched) {
@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(128) frame_batch_kernel(const T* __restrict__ 
 // it and sched[1]); items come largest instance first, all strips of a band
 // side by side.  A wait that gives up sets sched[2] and the warp returns.
 template <typename T, int MODEL, bool SHIFT>
-__global__ void __launch_bounds__(kRollThreads, 4)
+__global__ void __launch_bounds__(kRollThreads, Roll<T>::BLOCKS)
     roll_batch_kernel(const T* __restrict__ A, T* __restrict__ B, const InstDev* __restrict__ inst,
                       const Shift<typename Store<T>::C>* __restrict__ shifts, const int4* __restrict__ items,
                       int n_items, double s_e, double s_eps, double s_q, int* __restrict__ sched) {
